@@ -1,0 +1,81 @@
+"""Independent checks ("pins") for the oracle: textbook routines that reach the
+product by a different road than the oracle's ordered map.
+
+* ``box_convolution``: direct N-dimensional convolution of dense coefficient
+  boxes (the product of polynomials is the convolution of their coefficient
+  arrays; Laurent exponents are shifted into the box first).
+* ``eval_mod_p`` / ``eval_mod_m31``: evaluation at a point modulo a prime
+  (Schwartz-Zippel: distinct polynomials agree at a random point with
+  probability <= degree / p).
+* ``eval_pseries``: evaluation of a Poisson series at real x and angles y.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+M61 = (1 << 61) - 1
+M31 = (1 << 31) - 1
+
+
+def box_convolution(f, g):
+    """{exponent tuple: coefficient} of f*g by dense N-d convolution (nonzeros only)."""
+    v = f.exps.shape[0]
+    fmin, gmin = f.exps.min(axis=1), g.exps.min(axis=1)
+    fdim = f.exps.max(axis=1) - fmin + 1
+    gdim = g.exps.max(axis=1) - gmin + 1
+    dt = f.coef.dtype
+    G = np.zeros(tuple(gdim), dtype=dt)
+    G[tuple(g.exps - gmin[:, None])] = g.coef
+    out = np.zeros(tuple(fdim + gdim - 1), dtype=dt)
+    fpos = (f.exps - fmin[:, None]).T
+    for p, c in zip(fpos, f.coef):
+        sl = tuple(slice(int(p[k]), int(p[k]) + int(gdim[k])) for k in range(v))
+        out[sl] += c * G
+    nz = np.nonzero(out)
+    base = fmin + gmin
+    keys = np.stack(nz, axis=1) + base
+    return {tuple(int(x) for x in k): out[i] for k, i in zip(keys, zip(*nz))}
+
+
+def as_dict(exps: np.ndarray, coef: np.ndarray):
+    return {tuple(int(x) for x in exps[:, i]): coef[i] for i in range(coef.shape[0])}
+
+
+def eval_mod_p(exps: np.ndarray, coef: np.ndarray, point, p: int = M61) -> int:
+    """sum_i coef_i * prod_k x_k^e_ik mod p, exact (Python integers)."""
+    inv = [pow(int(x), p - 2, p) for x in point]
+    total = 0
+    for i in range(coef.shape[0]):
+        t = int(coef[i]) % p
+        for k, x in enumerate(point):
+            e = int(exps[k, i])
+            t = t * (pow(int(x), e, p) if e >= 0 else pow(inv[k], -e, p)) % p
+        total = (total + t) % p
+    return total
+
+
+def eval_mod_m31(exps: np.ndarray, coef: np.ndarray, point) -> int:
+    """Vectorised evaluation modulo 2^31 - 1 (every product fits in 62 bits)."""
+    p = M31
+    acc = (coef.astype(np.int64) % p).astype(np.uint64)
+    for k, x in enumerate(point):
+        e = exps[k].astype(np.int64)
+        lo, hi = int(e.min()), int(e.max())
+        xi = pow(int(x), p - 2, p)
+        table = np.array([pow(int(x), t, p) if t >= 0 else pow(xi, -t, p)
+                          for t in range(lo, hi + 1)], dtype=np.uint64)
+        acc = (acc * table[e - lo]) % np.uint64(p)
+    # sum in chunks to stay below 2^64
+    s = 0
+    for c in np.array_split(acc, max(1, acc.shape[0] // (1 << 20))):
+        s = (s + int(c.sum())) % p
+    return s
+
+
+def eval_pseries(s, x: np.ndarray, y: np.ndarray):
+    """(value, magnitude) of a Poisson series at x (real, > 0) and angles y."""
+    mono = np.prod(x[:, None] ** s.exps.astype(np.float64), axis=0)
+    phase = (s.trig.astype(np.float64) * y[:, None]).sum(axis=0)
+    trig = np.where(s.kind == 0, np.cos(phase), np.sin(phase))
+    terms = s.coef * mono * trig
+    return float(terms.sum()), float(np.abs(s.coef * mono).sum())

@@ -1,0 +1,290 @@
+"""Pins for the oracle: its results checked against what the mathematics fixes,
+never against itself.  CPU only.
+
+Every pin is a function returning a list of failure messages, so the planted
+mistake test at the end can check that each deliberate error in the oracle is
+caught by at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from pins import (M61, as_dict, box_convolution, eval_mod_m31, eval_mod_p,
+                  eval_pseries)
+from workloads import (PSeries, Poly, Rng, dense_total_degree, random_poly,
+                       random_pseries, total_degree_tuples, workload_cfg1,
+                       workload_cfg2, workload_cfg3)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+NT = max(1, min(16, os.cpu_count() or 1))
+
+
+# ---------------------------------------------------------------------------
+# pins as functions (plant = which oracle build to check)
+# ---------------------------------------------------------------------------
+
+def pin_bruteforce(plant=0):
+    """Small random Laurent polynomials: oracle == dense N-d convolution."""
+    errs = []
+    cases = [(1, 12, -5, 6), (2, 40, -3, 4), (3, 60, [-2, 0, -4], [3, 4, 1]),
+             (3, 80, 0, 5)]
+    for s, (v, n, lo, hi) in enumerate(cases):
+        for dt in ("i64", "f64"):
+            f = random_poly(v, n, lo, hi, 100 + s, dt)
+            g = random_poly(v, n + 7, lo, hi, 200 + s, dt)
+            r = oracle.poly_mul(f, g, plant=plant)
+            got = as_dict(r.exps, r.coef)
+            want = box_convolution(f, g)
+            if dt == "i64":
+                if got != {k: int(x) for k, x in want.items()}:
+                    errs.append(f"bruteforce mismatch v={v} {dt}")
+            else:
+                keys = set(got) | set(want)
+                bad = [k for k in keys
+                       if abs(got.get(k, 0.0) - want.get(k, 0.0)) > 1e-12 * 16 * n]
+                if bad:
+                    errs.append(f"bruteforce mismatch v={v} {dt}: {len(bad)} keys")
+    return errs
+
+
+def pin_werner(plant=0):
+    """Single-term Poisson products against the product-to-sum identities (Eq. 6, with 1/2)."""
+    errs = []
+    C, D = 2.0, 3.0
+    # (f trig, f kind, g trig, g kind, expected [(trig, kind, coef)]) with 2 trig vars.
+    # x exponents: f has x^-1, g has x^3; the product always carries x^2.
+    cases = [
+        ((1, 1), 0, (0, 1), 0, [((1, 0), 0, 3.0), ((1, 2), 0, 3.0)]),           # cos cos
+        ((1, 1), 0, (0, 1), 1, [((1, 2), 1, 3.0), ((1, 0), 1, -3.0)]),          # cos sin
+        ((1, 1), 1, (0, 1), 0, [((1, 2), 1, 3.0), ((1, 0), 1, 3.0)]),           # sin cos
+        ((1, 1), 1, (0, 1), 1, [((1, 0), 0, 3.0), ((1, 2), 0, -3.0)]),          # sin sin
+        ((0, 1), 0, (1, 1), 0, [((1, 0), 0, 3.0), ((1, 2), 0, 3.0)]),           # a-b negated, cos
+        ((0, 1), 1, (1, 1), 0, [((1, 2), 1, 3.0), ((1, 0), 1, -3.0)]),          # a-b negated, sin
+        ((0, 1), 0, (1, 1), 1, [((1, 2), 1, 3.0), ((1, 0), 1, 3.0)]),           # cos sin, negated
+        ((1, 0), 0, (0, 1), 0, [((-1, 1), 0, 3.0), ((1, 1), 0, 3.0)]),          # (1,-1) -> (-1,1)
+        ((1, 0), 1, (0, 1), 0, [((1, 1), 1, 3.0), ((-1, 1), 1, -3.0)]),         # sin of (1,-1)
+        ((1, 0), 1, (1, 0), 0, [((2, 0), 1, 3.0)]),                             # sin 0 dropped
+        ((1, 0), 1, (1, 0), 1, [((0, 0), 0, 3.0), ((2, 0), 0, -3.0)]),          # cos 0 kept
+        ((1, 0), 0, (1, 0), 0, [((0, 0), 0, 3.0), ((2, 0), 0, 3.0)]),
+        ((1, 1), 0, (0, 0), 0, [((1, 1), 0, 6.0)]),                             # t_g = 0: C*D
+        ((1, 0), 1, (0, 0), 0, [((1, 0), 1, 6.0)]),
+    ]
+    for tf, kf, tg, kg, want in cases:
+        f = PSeries(np.array([[-1]], np.int32), np.array(tf, np.int32)[:, None],
+                    np.array([kf], np.uint8), np.array([C]))
+        g = PSeries(np.array([[3]], np.int32), np.array(tg, np.int32)[:, None],
+                    np.array([kg], np.uint8), np.array([D]))
+        r = oracle.poisson_mul(f, g, plant=plant)
+        got = sorted((tuple(int(x) for x in r.trig[:, i]), int(r.kind[i]), float(r.coef[i]))
+                     for i in range(r.coef.shape[0]))
+        if sorted(want) != got or (r.coef.shape[0] and not (r.exps == 2).all()):
+            errs.append(f"werner {tf},{kf} x {tg},{kg}: got {got}, want {sorted(want)}")
+    return errs
+
+
+def pin_random_angles(plant=0):
+    """F(x, y) * G(x, y) == H(x, y) at random real x and angles y."""
+    errs = []
+    rng = Rng(77)
+    for s, (np_, nt, n) in enumerate([(1, 1, 20), (2, 3, 60), (3, 4, 150)]):
+        f = random_pseries(np_, nt, n, 3, 4, 300 + s)
+        g = random_pseries(np_, nt, n + 11, 3, 4, 400 + s)
+        h = oracle.poisson_mul(f, g, plant=plant)
+        H = PSeries(h.exps, h.trig, h.kind, h.coef)
+        for _ in range(4):
+            x = 0.5 + rng.uniform(np_)
+            y = 2 * math.pi * rng.uniform(nt)
+            fv, fm = eval_pseries(f, x, y)
+            gv, gm = eval_pseries(g, x, y)
+            hv, _ = eval_pseries(H, x, y)
+            if abs(fv * gv - hv) > 1e-12 * fm * gm:
+                errs.append(f"random angles np={np_} nt={nt}: {fv * gv} vs {hv}")
+    return errs
+
+
+def pin_canonical(plant=0):
+    """Every output multiplier vector is canonical and no sine of the zero vector survives."""
+    errs = []
+    f = random_pseries(2, 3, 80, 2, 3, 501)
+    g = random_pseries(2, 3, 90, 2, 3, 502)
+    h = oracle.poisson_mul(f, g, plant=plant)
+    for i in range(h.coef.shape[0]):
+        t = h.trig[:, i]
+        nz = np.nonzero(t)[0]
+        if nz.size == 0:
+            if h.kind[i] == 1:
+                errs.append("sine of the zero vector in the output")
+        elif t[nz[-1]] <= 0:
+            errs.append(f"non-canonical output vector {t.tolist()}")
+            break
+    return errs
+
+
+def pin_mod_p(plant=0):
+    """h(x) == f(x) g(x) mod 2^61 - 1 at random points (Laurent: inverses)."""
+    errs = []
+    for s, (v, n, lo, hi) in enumerate([(2, 50, -6, 6), (4, 120, [-3, 0, -1, -8], [5, 9, 2, 0])]):
+        f = random_poly(v, n, lo, hi, 600 + s)
+        g = random_poly(v, n, lo, hi, 700 + s)
+        h = oracle.poly_mul(f, g, plant=plant)
+        rng = Rng(800 + s)
+        for _ in range(3):
+            pt = [int(x) for x in rng.ints(2, M61 - 1, v)]
+            lhs = eval_mod_p(h.exps, h.coef, pt)
+            rhs = eval_mod_p(f.exps, f.coef, pt) * eval_mod_p(g.exps, g.coef, pt) % M61
+            if lhs != rhs:
+                errs.append(f"mod-p evaluation mismatch v={v}")
+                break
+    return errs
+
+
+# ---------------------------------------------------------------------------
+# the pins, run on the oracle
+# ---------------------------------------------------------------------------
+
+def test_generator_counts_match_paper():
+    for line in open(os.path.join(GOLDEN, "paper_counts.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        _, v, D, n = line.split()
+        assert total_degree_tuples(int(v), int(D)).shape[0] == int(n)
+        assert math.comb(int(v) + int(D), int(v)) == int(n)
+
+
+def test_oracle_bruteforce():
+    assert pin_bruteforce() == []
+
+
+def test_oracle_werner_single_terms():
+    assert pin_werner() == []
+
+
+def test_oracle_random_angles():
+    assert pin_random_angles() == []
+
+
+def test_oracle_canonical_output():
+    assert pin_canonical() == []
+
+
+def test_oracle_mod_p_small():
+    assert pin_mod_p() == []
+
+
+def test_oracle_cfg1_bruteforce():
+    f, g = workload_cfg1()
+    r = oracle.poly_mul(f, g)
+    want = box_convolution(f, g)
+    assert as_dict(r.exps, r.coef) == {k: int(x) for k, x in want.items()}
+    assert r.coef.shape[0] == math.comb(4 + 20, 4) == 10626
+    assert not r.overflow
+
+
+@pytest.mark.parametrize("v,D", [(1, 7), (2, 5), (3, 4), (4, 3), (5, 2)])
+def test_oracle_closed_form_count(v, D):
+    """Product of two dense total-degree-D polynomials has C(v + 2D, v) terms."""
+    f = dense_total_degree(v, D, 1, 9, 900 + v)
+    g = dense_total_degree(v, D, 1, 9, 950 + v)
+    r = oracle.poly_mul(f, g)
+    assert r.coef.shape[0] == math.comb(v + 2 * D, v)
+    assert (r.exps.sum(axis=0) <= 2 * D).all() and (r.exps >= 0).all()
+
+
+def test_oracle_cfg2_count_and_eval():
+    f, g = workload_cfg2()
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    assert r.coef.shape[0] == math.comb(4 + 40, 4) == 135751
+    assert not r.overflow
+    rng = Rng(2024)
+    for _ in range(3):
+        pt = [int(x) for x in rng.ints(2, (1 << 31) - 2, 4)]
+        assert eval_mod_m31(r.exps, r.coef, pt) == \
+            eval_mod_m31(f.exps, f.coef, pt) * eval_mod_m31(g.exps, g.coef, pt) % ((1 << 31) - 1)
+
+
+def test_oracle_cfg3_support_and_eval():
+    """MP-sparse structure: the key set is exactly the set of pairwise exponent sums."""
+    f, g = workload_cfg3()
+    r = oracle.poly_mul(f, g, nthreads=NT, keep_zero=True)
+    assert not r.overflow
+    hi = (f.exps.max(axis=1) + g.exps.max(axis=1) + 1).astype(np.int64)
+    sums = []
+    for ch in np.array_split(np.arange(f.n), 16):
+        s = f.exps[:, ch][:, :, None].astype(np.int64) + g.exps[:, None, :]
+        sums.append(np.unique(np.ravel_multi_index(tuple(s.reshape(5, -1)), tuple(hi))))
+    support = np.unique(np.concatenate(sums))
+    got = np.ravel_multi_index(tuple(r.exps.astype(np.int64)), tuple(hi))
+    assert got.shape[0] == support.shape[0] == 5821335
+    assert np.array_equal(np.sort(got), support)
+    rng = Rng(3003)
+    for _ in range(3):
+        pt = [int(x) for x in rng.ints(2, (1 << 31) - 2, 5)]
+        assert eval_mod_m31(r.exps, r.coef, pt) == \
+            eval_mod_m31(f.exps, f.coef, pt) * eval_mod_m31(g.exps, g.coef, pt) % ((1 << 31) - 1)
+
+
+def test_oracle_int64_wraps_and_flags_overflow():
+    big = (1 << 62) + 12345
+    f = Poly(np.array([[0, 1]], np.int32), np.array([big, 3], np.int64))
+    g = Poly(np.array([[0, 1]], np.int32), np.array([7, big], np.int64))
+    r = oracle.poly_mul(f, g)
+    assert r.overflow
+    exact = {0: big * 7, 1: big * big + 3 * 7, 2: 3 * big}
+    for i in range(r.coef.shape[0]):
+        e = int(r.exps[0, i])
+        w = exact[e] % (1 << 64)
+        w = w - (1 << 64) if w >= (1 << 63) else w
+        assert int(r.coef[i]) == w
+
+
+def test_oracle_threads_and_shards_agree():
+    f = random_poly(3, 400, -5, 5, 11)
+    g = random_poly(3, 300, -5, 5, 12)
+    a = oracle.poly_mul(f, g, nthreads=1)
+    b = oracle.poly_mul(f, g, nthreads=4)
+    assert np.array_equal(a.exps, b.exps) and np.array_equal(a.coef, b.coef)
+    parts = [oracle.poly_mul(f, g, shard=(3, s)) for s in range(3)]
+    merged = {}
+    for p in parts:
+        d = as_dict(p.exps, p.coef)
+        assert not (set(d) & set(merged))
+        merged.update(d)
+    assert merged == as_dict(a.exps, a.coef)
+    keys = a.exps.T.copy()
+    sh = oracle.shard_of_keys(keys, 3)
+    for s in range(3):
+        assert set(as_dict(a.exps[:, sh == s], a.coef[sh == s])) == set(as_dict(parts[s].exps, parts[s].coef))
+    assert oracle.key_hash(keys[0]) % 3 == sh[0]
+
+
+def test_oracle_pseries_shards_and_mass():
+    f = random_pseries(2, 2, 120, 2, 3, 21)
+    g = random_pseries(2, 2, 110, 2, 3, 22)
+    full = oracle.poisson_mul(f, g, nthreads=3)
+    assert (full.mass >= np.abs(full.coef) * (1 - 1e-15)).all()
+    n = sum(oracle.poisson_mul(f, g, shard=(4, s)).coef.shape[0] for s in range(4))
+    assert n == full.coef.shape[0]
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes: each must be caught by some pin
+# ---------------------------------------------------------------------------
+
+PLANTS = {
+    1: "product-to-sum halves dropped",
+    2: "wrong sign in cos*sin",
+    3: "difference taken as g - f",
+    4: "canonical sign from the lowest-index multiplier",
+    5: "last term of g skipped",
+    6: "first exponent of f used twice",
+}
+
+
+@pytest.mark.parametrize("plant", sorted(PLANTS))
+def test_planted_mistake_is_caught(plant):
+    caught = (pin_werner(plant) + pin_canonical(plant) + pin_random_angles(plant)
+              + pin_bruteforce(plant) + pin_mod_p(plant))
+    assert caught, f"planted mistake {plant} ({PLANTS[plant]}) escaped every pin"
