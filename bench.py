@@ -1,0 +1,378 @@
+"""Benchmark: term-products per second of sparse polynomial multiplication on GB300.
+
+One step = one call of the library's poly_mul on the dense-path workload
+(two 4-variable polynomials with every monomial of total degree <= 20, 10626
+terms each, int64 coefficients in [-2^20, 2^20]; 112,911,876 term-products,
+135,751 output terms): range scan, host plan, Kronecker encode, sort, dense
+block planning, shared-memory accumulation, compaction and decode of the
+product into device buffers.  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (a 256 MB write) between timed steps.
+
+The line also carries the hash path (Monagan-Pearce sparse structure) and the
+Poisson path as secondary measurements under "paths".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own replica of the workload (independent
+products, no collective on the data path): "scaling": "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "M term-products/s (dense path, moderately sparse workload)"
+UNIT = "M term-products/s"
+WORKLOAD = ("dense path: f, g = all 4-variable monomials of total degree <= 20 "
+            "(10626 terms each), int64 coefficients uniform in [-2^20, 2^20], seeds 2001/2002")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-paths", action="store_true", help="skip the secondary hash/Poisson lines")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def cpu_baseline(f, g, budget_s: float = 12.0):
+    import oracle
+    from workloads import Poly
+    cores = os.cpu_count() or 1
+    m = 64
+    fs = Poly(np.ascontiguousarray(f.exps[:, :m]), f.coef[:m].copy())
+    t = time.perf_counter()
+    oracle.poly_mul(fs, g, nthreads=cores)
+    dt = max(time.perf_counter() - t, 1e-3)
+    m = int(min(f.n, max(cores, m * budget_s / dt)))
+    fs = Poly(np.ascontiguousarray(f.exps[:, :m]), f.coef[:m].copy())
+    t = time.perf_counter()
+    oracle.poly_mul(fs, g, nthreads=cores)
+    dt = time.perf_counter() - t
+    tp = m * g.n
+    return {"value": tp / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {m} of {f.n} f terms x all {g.n} g terms of the workload "
+                      f"({tp} term-products, {dt:.1f} s, std::map oracle, {cores} threads)"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from workloads import workload_cfg2
+    f, g = workload_cfg2()
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+        cb = cpu_baseline(f, g, budget_s=per_step)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import ctypes
+    import paper_1004_4548_gb300 as kron
+    from paper_1004_4548_gb300 import binding as B
+    from workloads import workload_cfg2, workload_cfg3, workload_cfg4, PSeries
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    ctx = kron.Context(local)
+    L = ctx.L
+
+    f, g = workload_cfg2()
+    tp = f.n * g.n
+    fe, fc = torch.from_numpy(f.exps).to(dev), torch.from_numpy(f.coef).to(dev)
+    ge, gc = torch.from_numpy(g.exps).to(dev), torch.from_numpy(g.coef).to(dev)
+    F = B.kr_poly(4, f.n, fe.data_ptr(), fc.data_ptr(), B.KR_I64)
+    G = B.kr_poly(4, g.n, ge.data_ptr(), gc.data_ptr(), B.KR_I64)
+    # output buffers sized by a first call
+    ex0, cf0, _, _ = kron.poly_mul(fe, fc, ge, gc, ctx=ctx)
+    nout = int(cf0.shape[0])
+    oe = torch.empty((4, nout), dtype=torch.int32, device=dev)
+    oc = torch.empty((nout,), dtype=torch.int64, device=dev)
+    H = B.kr_poly_out(4, nout, 0, oe.data_ptr(), oc.data_ptr(), None)
+    O = B.kr_opts()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        st = L.poly_mul(ctx.h, ctypes.byref(F), ctypes.byref(G), ctypes.byref(H), ctypes.byref(O), sp)
+        if st != 0:
+            raise RuntimeError(f"poly_mul failed: {st} {L.kr_last_error(ctx.h).decode()}")
+
+    ctx.set_profiling(True)
+    for _ in range(max(3, args.warmup)):
+        step()
+    assert int(H.nterms) == nout
+    # ---- timed region
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    accum_ms = []
+    l0 = ctx.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        accum_ms.extend(ms for name, ms in ctx.stages() if name == "dense_accum")
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * tp / (ms * 1e-3) / 1e6
+    stages = ctx.stages()
+
+    # ---- roofline of the dominant kernel (dense accumulation)
+    peak_smem = kron.kr_probe_smem_atomic_rate(local, False, 5)
+    acc_ms = statistics.mean(accum_ms) if accum_ms else float("nan")
+    achieved = tp / (acc_ms * 1e-3) / 1e9   # G shared-memory updates (term-products) per second
+    roof = {"bound": "alu", "kernel": "k_dense_accum",
+            "achieved": achieved, "peak": peak_smem / 1e9, "unit": "G smem-atomic-adds/s",
+            "frac": achieved / (peak_smem / 1e9) if peak_smem > 0 else None,
+            "peak_source": "measured: kr_probe_smem_atomic_rate (conflict-free 64-bit shared-memory "
+                           "atomic adds, all SMs, best of 5)",
+            "kernel_ms": acc_ms, "algorithmic_units_per_launch": tp,
+            "traffic": None}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hfe = torch.from_numpy(f.exps).pin_memory(); hfc = torch.from_numpy(f.coef).pin_memory()
+    hge = torch.from_numpy(g.exps).pin_memory(); hgc = torch.from_numpy(g.coef).pin_memory()
+    hoe = torch.empty((4, nout), dtype=torch.int32).pin_memory()
+    hoc = torch.empty((nout,), dtype=torch.int64).pin_memory()
+    Fh = B.kr_poly(4, f.n, hfe.data_ptr(), hfc.data_ptr(), B.KR_I64)
+    Gh = B.kr_poly(4, g.n, hge.data_ptr(), hgc.data_ptr(), B.KR_I64)
+    Hh = B.kr_poly_out(4, nout, 0, hoe.data_ptr(), hoc.data_ptr(), None)
+    ctx.set_profiling(False)
+
+    def step_host():
+        st = L.poly_mul(ctx.h, ctypes.byref(Fh), ctypes.byref(Gh), ctypes.byref(Hh), ctypes.byref(O), sp)
+        if st != 0:
+            raise RuntimeError(f"poly_mul (host buffers) failed: {st}")
+
+    for _ in range(3):
+        step_host()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step_host()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    assert np.array_equal(hoc.numpy(), oc.cpu().numpy()), "host-buffer result differs"
+    e2e = {"value": world * tp / (statistics.mean(e2e_ms) * 1e-3) / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(f.exps.nbytes + f.coef.nbytes + g.exps.nbytes + g.coef.nbytes),
+           "d2h_bytes_per_step": int(hoe.numel() * 4 + hoc.numel() * 8),
+           "ms_per_step": statistics.mean(e2e_ms)}
+
+    # ---- secondary paths
+    paths = {}
+    if not args.no_paths:
+        ctx.set_profiling(True)
+        paths["hash_cfg3"] = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert",
+                                       max(3, args.steps // 2))
+        f4, g4 = workload_cfg4()
+        paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3)
+        ctx.set_profiling(False)
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "term_products": tp, "output_terms": nout,
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": roof,
+                "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk,
+                "stages_ms_last_step": {k: round(v, 4) for k, v in stages},
+                "wall_s_timed": wall,
+                "sm_cycles_per_term_product": (clk["sm_mhz"] * 1e6 * ms * 1e-3 / tp * 152)
+                if clk.get("sm_mhz") else None,
+                "paths": paths}
+        line["cpu_baseline"] = cpu_baseline(f, g)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def time_poly(kron, ctx, f, g, dev, stream, flush, kernel, steps):
+    import torch
+    fe, fc = torch.from_numpy(f.exps).to(dev), torch.from_numpy(f.coef).to(dev)
+    ge, gc = torch.from_numpy(g.exps).to(dev), torch.from_numpy(g.coef).to(dev)
+    for _ in range(2):
+        ex, cf, _, _ = kron.poly_mul(fe, fc, ge, gc, ctx=ctx)
+    times, kt = [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ex, cf, _, _ = kron.poly_mul(fe, fc, ge, gc, ctx=ctx)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        kt.extend(ms for n, ms in ctx.stages() if n == kernel)
+    tp = f.n * g.n
+    ms = statistics.mean(times)
+    kms = statistics.mean(kt)
+    return {"value": tp / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "term_products": tp,
+            "output_terms": int(cf.shape[0]), "kernel": kernel, "kernel_ms": kms,
+            "kernel_rate": tp / (kms * 1e-3) / 1e6, "stages_ms_last_step": dict(ctx.stages())}
+
+
+def time_pseries(kron, ctx, f, g, dev, stream, flush, steps):
+    import torch
+    from workloads import PSeries
+    F = PSeries(*(torch.from_numpy(x).to(dev) for x in (f.exps, f.trig, f.kind, f.coef)))
+    G = PSeries(*(torch.from_numpy(x).to(dev) for x in (g.exps, g.trig, g.kind, g.coef)))
+    out = kron.poisson_mul(F, G, ctx=ctx)
+    times, kt = [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = kron.poisson_mul(F, G, ctx=ctx, capacity=int(out[3].shape[0]))
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+        kt.extend(ms for n, ms in ctx.stages() if n == "hash_insert")
+    tp = f.n * g.n
+    ms = statistics.mean(times)
+    kms = statistics.mean(kt)
+    return {"value": tp / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "term_products": tp,
+            "output_terms": int(out[3].shape[0]), "kernel": "hash_insert", "kernel_ms": kms,
+            "kernel_rate": tp / (kms * 1e-3) / 1e6,
+            "hbm_algorithmic_GBps": tp * 48 / (kms * 1e-3) / 1e9,
+            "stages_ms_last_step": dict(ctx.stages())}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * kron.h - C ABI of libkron: multiplication of sparse multivariate Laurent
+ * polynomials and Poisson series on NVIDIA GB300 (sm_103a).
+ *
+ * Method (Biscani, "Multiplication of sparse Laurent polynomials and Poisson
+ * series on modern hardware architectures"):
+ *   1. Kronecker substitution (Sec. 2, Table 1, Table 2 and the coding
+ *      equations that follow it): every exponent vector e in a box
+ *      [e_min, e_max] maps to the integer code c . e - chi, with widths
+ *      w_k = 1 + e_k,max - e_k,min, coding vector c = (1, w_0, w_0 w_1, ...)
+ *      and chi = c . e_min.  Variable 0 is the least significant.  The map is
+ *      additive, so a product of monomials is a sum of codes.
+ *   2. Schoolbook product of the coded univariate polynomials (Sec. 3), with
+ *      accumulation either into a dense array indexed by code (moderately
+ *      sparse products, Sec. 3.1) or into a hash table keyed by code (highly
+ *      sparse products, Sec. 3.2).
+ *   3. Poisson series (Sec. 1, Eq. 1): each pair of terms expands, by the
+ *      product-to-sum formulas of Eq. 6, into a term at the sum and a term at
+ *      the difference of the trigonometric multiplier vectors.  Eq. 6 is
+ *      printed without the factor 1/2 of the trigonometric identities; this
+ *      library applies it (cos a cos b = 1/2 cos(a-b) + 1/2 cos(a+b), ...).
+ *
+ * Conventions shared by every entry point
+ *   - Term arrays are "structure of arrays": exponents of a series with v
+ *     variables and n terms are an int32 array [v][n] (row k holds variable k
+ *     of every term, row stride n, or the output capacity for outputs).
+ *   - Pointers may address device memory or host memory (pageable or pinned);
+ *     the library detects which with cudaPointerGetAttributes and stages host
+ *     data through device scratch.  The caller owns every buffer it passes.
+ *   - Every call is issued on the given stream.  Calls that return a term count
+ *     synchronise that stream before returning; device outputs are complete
+ *     when the call returns KR_OK only after a later synchronisation of the
+ *     stream (the output decode is the last work queued).
+ *   - Canonical output: terms sorted by ascending code (reverse lexicographic
+ *     exponent order, variable 0 least significant; Poisson keys ordered by
+ *     kind (cos < sin), then trig multipliers, then exponents), no zero
+ *     coefficients.  int64 coefficients use wrapping arithmetic modulo 2^64.
+ *   - Trig canonical form: a multiplier vector is canonical when its
+ *     highest-index nonzero entry is positive.  Inputs must be canonical and a
+ *     sine may not have the zero vector (KR_ERR_INVALID otherwise).  Results
+ *     are canonicalised: cos(-x) = cos x, sin(-x) = -sin x, sin 0 = 0.
+ *   - No C++ exception crosses this interface.  A context is not thread safe:
+ *     use one context per host thread.
+ */
+#ifndef KRON_H
+#define KRON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KR_MAXV 16            /* max variables: poly vars + trig vars */
+
+typedef enum {
+  KR_OK = 0,
+  KR_ERR_INVALID = 1,    /* bad argument, mismatched shapes, non-canonical trig input */
+  KR_ERR_RANGE = 2,      /* an exponent lies outside the declared coding box */
+  KR_ERR_OVERFLOW = 3,   /* the code range exceeds 2^63 - 1 (no coding exists) */
+  KR_ERR_DUP = 4,        /* an input series repeats a term key */
+  KR_ERR_OOM = 5,        /* device or pinned-host allocation failed */
+  KR_ERR_CAPACITY = 6,   /* output buffers too small; required count returned */
+  KR_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
+  KR_ERR_CUDA = 8,       /* a CUDA runtime call failed; see kr_last_error */
+  KR_ERR_TABLE_FULL = 9  /* hash table full after every allowed regrowth */
+} kr_status;
+
+typedef enum { KR_I64 = 0, KR_F64 = 1 } kr_coef_t;
+
+typedef enum { KR_PATH_AUTO = 0, KR_PATH_DENSE = 1, KR_PATH_HASH = 2 } kr_path;
+
+typedef struct CUstream_st* kr_stream;   /* same type as cudaStream_t; NULL = default */
+typedef struct kr_ctx kr_ctx;
+
+/* A sparse polynomial (Sec. 3.1, "sparse distributed" representation). */
+typedef struct {
+  int32_t nvars;         /* 1 .. KR_MAXV */
+  int64_t nterms;        /* >= 0 */
+  const int32_t* exps;   /* [nvars][nterms] */
+  const void* coef;      /* int64_t or double [nterms] */
+  kr_coef_t type;
+} kr_poly;
+
+/* Product buffers.  capacity: terms the buffers hold.  nterms: set on return
+ * (also on KR_ERR_CAPACITY, to the count required).  exps and codes may be
+ * NULL.  omin / omax: the product's coding box, set on return, for
+ * kron_decode of the codes. */
+typedef struct {
+  int32_t nvars;
+  int64_t capacity;
+  int64_t nterms;
+  int32_t* exps;         /* [nvars][capacity] */
+  void* coef;            /* [capacity], type of the inputs */
+  int64_t* codes;        /* [capacity] Kronecker codes (c . e - chi), or NULL */
+  int32_t omin[KR_MAXV];
+  int32_t omax[KR_MAXV];
+} kr_poly_out;
+
+/* A Poisson series (Eq. 1): sum of C x^a cos|sin(j . y). */
+typedef struct {
+  int32_t npoly;         /* polynomial variables, >= 0 */
+  int32_t ntrig;         /* trig variables, >= 1; npoly + ntrig <= KR_MAXV */
+  int64_t nterms;
+  const int32_t* exps;   /* [npoly][nterms] */
+  const int32_t* trig;   /* [ntrig][nterms], canonical */
+  const uint8_t* kind;   /* [nterms], 0 = cos, 1 = sin */
+  const double* coef;    /* [nterms] */
+} kr_pseries;
+
+typedef struct {
+  int32_t npoly, ntrig;
+  int64_t capacity;
+  int64_t nterms;
+  int32_t* exps;         /* [npoly][capacity] or NULL */
+  int32_t* trig;         /* [ntrig][capacity] or NULL */
+  uint8_t* kind;         /* [capacity] or NULL */
+  double* coef;          /* [capacity] */
+  int64_t* codes;        /* [capacity] combined keys ((kind*T2 + |t|)*Wp + p), or NULL */
+} kr_pseries_out;
+
+/* Tuning knobs.  A NULL kr_opts pointer, or a zero field, means "default". */
+typedef struct {
+  int32_t path;          /* kr_path; AUTO picks by density (Sec. 3.2) */
+  int32_t block_slots;   /* dense path: output codes per block (shared-memory slice) */
+  double load_factor;    /* hash path: target table load factor, (0, 0.9] */
+  int32_t probe_limit;   /* hash path: windows probed before TABLE_FULL */
+  int32_t unsorted;      /* hash path: 1 = leave the output in table order */
+  int32_t max_regrow;    /* hash path: regrowths after TABLE_FULL (x4 each, the last one
+                            to the term-product bound); 0 = 4, <0 = none */
+  int64_t table_slots;   /* hash path: initial table slots (power of two), 0 = sized
+                            from the term-product bound and load_factor */
+} kr_opts;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a context bound to CUDA device `device` (scratch arena, pinned
+ * staging, status words).  Returns KR_ERR_CUDA / KR_ERR_OOM on failure. */
+kr_status kr_ctx_create(int32_t device, kr_ctx** out);
+/* Frees every resource of the context (synchronises its streams first). */
+void kr_ctx_destroy(kr_ctx* ctx);
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* kr_last_error(const kr_ctx* ctx);
+/* Fixed text for a status code. */
+const char* kron_strerror(kr_status s);
+/* Bytes of device scratch currently held by the context. */
+int64_t kr_ctx_scratch_bytes(const kr_ctx* ctx);
+/* Stage timing.  When enabled, every multiplication records a CUDA event on
+ * its stream after each pipeline stage (range_scan, zero_accumulators, encode,
+ * sort, gather, dense_plan, dense_accum, hash_insert, compact, output_sort,
+ * decode, copy_out); the durations of the last call are then readable.
+ * Stages that did not run are absent.  Times in milliseconds, each the
+ * interval between the previous event and the stage's own. */
+kr_status kr_ctx_set_profiling(kr_ctx* ctx, int32_t enable);
+int32_t kr_ctx_stage_count(const kr_ctx* ctx);
+/* name: static string owned by the library. */
+kr_status kr_ctx_stage(const kr_ctx* ctx, int32_t i, const char** name, double* ms);
+/* Kernels this context has launched since its creation (all calls). */
+int64_t kr_ctx_launch_count(const kr_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Kronecker coding (Sec. 2, Table 2 and the equations after it)            */
+/* ------------------------------------------------------------------------ */
+
+/* Host-only.  For the box [emin, emax] of nvars variables writes the coding
+ * vector c (cvec_out[k] = prod_{l<k} w_l) and the number of codes
+ * W = prod_k w_k (range_out).  KR_ERR_OVERFLOW when W > 2^63 - 1,
+ * KR_ERR_INVALID when emin > emax for some k.  Host arrays, caller-owned. */
+kr_status kron_plan(const int32_t* emin, const int32_t* emax, int32_t nvars,
+                    int64_t* cvec_out, int64_t* range_out);
+
+/* codes_out[i] = sum_k c_k (exps[k][i] - emin[k]) for the box [emin, emax]
+ * (host arrays).  exps: [nvars][n]; codes_out: [n].  KR_ERR_RANGE when a
+ * term lies outside the box.  Synchronises the stream. */
+kr_status kron_encode(kr_ctx* ctx, const int32_t* exps, int64_t n, int32_t nvars,
+                      const int32_t* emin, const int32_t* emax, int64_t* codes_out,
+                      kr_stream stream);
+
+/* Inverse of kron_encode: exps_out[k][i] = (codes[i] / c_k) mod w_k + emin[k].
+ * KR_ERR_RANGE when a code lies outside [0, W).  Synchronises the stream. */
+kr_status kron_decode(kr_ctx* ctx, const int64_t* codes, int64_t n, int32_t nvars,
+                      const int32_t* emin, const int32_t* emax, int32_t* exps_out,
+                      kr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Multiplication                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* h = f * g for sparse Laurent polynomials (Sec. 3).  Each operand is coded in
+ * the product's box (widths of the output, each operand offset by its own
+ * minimum), so a code sum is the product's code.  Dense path (Sec. 3.1): the
+ * output code range is split into blocks, each accumulated in on-chip shared
+ * memory; hash path (Sec. 3.2): an open-addressing table in device memory.
+ * Returns KR_ERR_CAPACITY with h->nterms = required when h->capacity is too
+ * small: the product is kept in the context and kron_fetch_poly copies it out
+ * without recomputing.  Synchronises the stream. */
+kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out* h,
+                   const kr_opts* opts, kr_stream stream);
+
+/* h = f * g for Poisson series (Eq. 1, Eq. 6 with the factor 1/2); hash path.
+ * Polynomial exponents are coded in the product's box; trig multipliers in the
+ * symmetric box |t_k| <= R_k = max|f_k| + max|g_k|, so that sums and
+ * differences of codes are the codes of the sums and differences (the
+ * extension of the coding vector to negated operands described in Sec. 2).
+ * Capacity contract as poly_mul. */
+kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g,
+                      kr_pseries_out* h, const kr_opts* opts, kr_stream stream);
+
+/* Copy the product kept by the last poly_mul / poisson_mul of this context
+ * (after KR_ERR_CAPACITY) into h.  KR_ERR_INVALID if there is none. */
+kr_status kron_fetch_poly(kr_ctx* ctx, kr_poly_out* h, kr_stream stream);
+kr_status kron_fetch_pseries(kr_ctx* ctx, kr_pseries_out* h, kr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Chip-wide rate of conflict-free shared-memory 64-bit atomic adds (int64
+ * when f64 = 0, float64 otherwise) on CUDA device `device`: best of `reps`
+ * launches timed with CUDA events, in adds per second; < 0 on failure.  Sec. 5
+ * measures a multiplication in clock cycles per monomial-by-monomial
+ * multiplication and calls it optimal when that approaches the cost of one
+ * coefficient multiply-add; on the dense path that step is one shared-memory
+ * atomic add, so this rate is the path's ceiling.  Allocates and frees a
+ * small device buffer; synchronises the device's default stream. */
+double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t reps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRON_H */

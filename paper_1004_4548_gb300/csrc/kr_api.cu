@@ -1,0 +1,955 @@
+// The C ABI of libkron (include/kron.h): context, scratch arenas, the
+// multiplication pipeline, and the entry points.
+//
+// Pipeline of one call (one or many products):
+//   range scan  -> [sync] host plan (coding box, path, sizes)
+//   encode -> sort -> gather   (Kronecker codes of both operands, ascending)
+//   dense:  block plan -> shared-memory accumulation -> flush
+//   hash:   table inserts
+//   compaction -> [sync] -> output sort (hash) -> decode into the caller's buffers
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kr_plan.h"
+
+using namespace kr;
+
+struct kr_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  void* in_arena = nullptr;
+  size_t in_cap = 0;
+  void* work = nullptr;
+  size_t work_cap = 0;
+  void* pinned = nullptr;
+  size_t pinned_cap = 0;
+  // product kept after the last multiplication (for kron_fetch_*)
+  bool has_result = false;
+  bool res_poisson = false;
+  Prod res_prod{};
+  Prod* res_dprod = nullptr;   // device copy of res_prod (in the work arena)
+  const uint64_t* res_key = nullptr;
+  const uint64_t* res_val = nullptr;
+  int64_t res_n = 0;
+  // stage timing (CUDA events on the call's stream) and launch counting
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<const char*> ev_name;
+  int nev = 0;
+  std::vector<double> stage_ms;
+  std::vector<const char*> stage_name;
+  int64_t launches = 0;
+};
+
+namespace {
+
+struct CudaFail {
+  cudaError_t e;
+};
+
+inline void ck(kr_ctx* ctx, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    throw CudaFail{e};
+  }
+}
+
+kr_status from_cuda(cudaError_t e) {
+  return e == cudaErrorMemoryAllocation ? KR_ERR_OOM : KR_ERR_CUDA;
+}
+
+// Bump allocation over a base pointer; base == nullptr measures only.
+struct Bump {
+  char* base;
+  size_t off = 0;
+  explicit Bump(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(int64_t count, size_t align = 256) {
+    off = (off + align - 1) / align * align;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += (size_t)std::max<int64_t>(count, 0) * sizeof(T);
+    return p;
+  }
+};
+
+void ensure(kr_ctx* ctx, void** buf, size_t* cap, size_t need, cudaStream_t s) {
+  if (need <= *cap) return;
+  ck(ctx, cudaStreamSynchronize(s), "sync before scratch growth");
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  size_t want = need + need / 4 + (1 << 20);
+  ck(ctx, cudaMalloc(buf, want), "cudaMalloc scratch");
+  *cap = want;
+}
+
+void ensure_pinned(kr_ctx* ctx, size_t need, cudaStream_t s) {
+  if (need <= ctx->pinned_cap) return;
+  ck(ctx, cudaStreamSynchronize(s), "sync before pinned growth");
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  ctx->pinned = nullptr;
+  ctx->pinned_cap = 0;
+  size_t want = need + need / 4 + (1 << 16);
+  ck(ctx, cudaMallocHost(&ctx->pinned, want), "cudaMallocHost");
+  ctx->pinned_cap = want;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Records a stage boundary when profiling is on.
+void mark(kr_ctx* ctx, cudaStream_t s, const char* name) {
+  if (!ctx->profile) return;
+  if (ctx->nev >= (int)ctx->ev.size()) {
+    cudaEvent_t e;
+    ck(ctx, cudaEventCreate(&e), "cudaEventCreate");
+    ctx->ev.push_back(e);
+    ctx->ev_name.push_back(nullptr);
+  }
+  ctx->ev_name[ctx->nev] = name;
+  ck(ctx, cudaEventRecord(ctx->ev[ctx->nev], s), "cudaEventRecord");
+  ctx->nev++;
+}
+
+// After a synchronisation: turn the recorded marks into per-stage times.
+void collect_stages(kr_ctx* ctx) {
+  if (!ctx->profile) return;
+  for (int i = 1; i < ctx->nev; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[i - 1], ctx->ev[i]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = -1.f;
+    }
+    ctx->stage_ms.push_back(ms);
+    ctx->stage_name.push_back(ctx->ev_name[i]);
+  }
+  ctx->nev = 0;
+}
+
+kr_status status_to_kr(uint32_t st) {
+  if (st & ST_INVALID) return KR_ERR_INVALID;
+  if (st & ST_RANGE) return KR_ERR_RANGE;
+  if (st & ST_DUP) return KR_ERR_DUP;
+  if (st & ST_TABLE_FULL) return KR_ERR_TABLE_FULL;
+  if (st & ST_OUTCAP) return KR_ERR_CUDA;
+  return KR_OK;
+}
+
+// Result of one product of a pipeline run.
+struct ProdResult {
+  kr_status st = KR_OK;
+  int64_t n = 0;
+  const uint64_t* key = nullptr;
+  const uint64_t* val = nullptr;
+  Prod prod{};
+  Prod* dprod = nullptr;
+};
+
+// Host input of one product before staging (pointers may be host or device).
+struct JobIn {
+  bool poisson = false;
+  bool f64 = false;
+  int np = 0, nt = 0;
+  const int32_t* fe = nullptr; const int32_t* ft = nullptr; const uint8_t* fk = nullptr;
+  const void* fc = nullptr; int64_t nf = 0;
+  const int32_t* ge = nullptr; const int32_t* gt = nullptr; const uint8_t* gk = nullptr;
+  const void* gc = nullptr; int64_t ng = 0;
+  kr_opts opts{};
+};
+
+// Stage host inputs into the input arena; returns device pointers.
+template <typename T>
+const T* stage(kr_ctx* ctx, Bump& b, const T* src, int64_t count, cudaStream_t s) {
+  if (!src || count <= 0) return src;
+  if (is_device_ptr(src)) return src;
+  T* dst = b.take<T>(count);
+  if (b.base) ck(ctx, cudaMemcpyAsync(dst, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice, s),
+                 "stage input");
+  return dst;
+}
+
+// The pipeline over a set of products.  All products must have nf, ng >= 1.
+void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
+                  std::vector<ProdResult>& res) {
+  const int nprod = (int)ins.size();
+  res.assign(nprod, ProdResult());
+  std::vector<Job> jobs(nprod);
+  std::vector<int> regrows(nprod, 0);
+  std::vector<int64_t> hints(nprod, 0);
+  for (int attempt = 0;; ++attempt) {
+    // ---------------- phase A: staged inputs and metadata
+    const int nops = 2 * nprod;
+    size_t in_need = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      Bump b(pass ? ctx->in_arena : nullptr);
+      for (int p = 0; p < nprod; ++p) {
+        const JobIn& in = ins[p];
+        Job& J = jobs[p];
+        J = Job();
+        J.poisson = in.poisson;
+        J.f64 = in.f64;
+        J.np = in.np;
+        J.nt = in.nt;
+        J.opts = in.opts;
+        J.slots_hint = hints[p];
+        const size_t csz = 8;
+        J.f.n = in.nf;
+        J.g.n = in.ng;
+        J.f.e = stage(ctx, b, in.fe, (int64_t)in.np * in.nf, s);
+        J.g.e = stage(ctx, b, in.ge, (int64_t)in.np * in.ng, s);
+        J.f.c = (const void*)stage(ctx, b, (const uint64_t*)in.fc, in.nf * (int64_t)(csz / 8), s);
+        J.g.c = (const void*)stage(ctx, b, (const uint64_t*)in.gc, in.ng * (int64_t)(csz / 8), s);
+        if (in.poisson) {
+          J.f.t = stage(ctx, b, in.ft, (int64_t)in.nt * in.nf, s);
+          J.g.t = stage(ctx, b, in.gt, (int64_t)in.nt * in.ng, s);
+          J.f.k = stage(ctx, b, in.fk, in.nf, s);
+          J.g.k = stage(ctx, b, in.gk, in.ng, s);
+        }
+      }
+      if (!pass) {
+        in_need = b.off;
+        ensure(ctx, &ctx->in_arena, &ctx->in_cap, in_need + 1, s);
+      }
+    }
+    size_t meta_need;
+    Prod* dprods;
+    OpRef* dops;
+    int32_t* dranges;
+    {
+      Bump m(nullptr);
+      m.take<Prod>(nprod);
+      m.take<OpRef>(nops);
+      m.take<int32_t>((int64_t)nops * 3 * MAXV);
+      meta_need = m.off;
+    }
+    ensure_pinned(ctx, meta_need + 4096, s);
+    // The metadata sits at the start of the work arena.  The work arena may be
+    // regrown after planning; the metadata is then re-uploaded.
+    ensure(ctx, &ctx->work, &ctx->work_cap, meta_need, s);
+    {
+      Bump m(ctx->work);
+      dprods = m.take<Prod>(nprod);
+      dops = m.take<OpRef>(nops);
+      dranges = m.take<int32_t>((int64_t)nops * 3 * MAXV);
+    }
+    Bump hp(ctx->pinned);
+    Prod* hprods = hp.take<Prod>(nprod);
+    OpRef* hops = hp.take<OpRef>(nops);
+    int32_t* hranges = hp.take<int32_t>((int64_t)nops * 3 * MAXV);
+    for (int p = 0; p < nprod; ++p) {
+      Prod P{};
+      P.f = jobs[p].f;
+      P.g = jobs[p].g;
+      P.np = jobs[p].np;
+      P.nt = jobs[p].nt;
+      P.f64 = jobs[p].f64;
+      hprods[p] = P;
+      hops[2 * p] = OpRef{p, 0};
+      hops[2 * p + 1] = OpRef{p, 1};
+    }
+    ck(ctx, cudaMemcpyAsync(dprods, hprods, sizeof(Prod) * nprod, cudaMemcpyHostToDevice, s), "upload");
+    ck(ctx, cudaMemcpyAsync(dops, hops, sizeof(OpRef) * nops, cudaMemcpyHostToDevice, s), "upload");
+    mark(ctx, s, "begin");
+    ck(ctx, launch_range_scan(dprods, dops, nops, dranges, s), "range scan");
+    ctx->launches += 1;
+    mark(ctx, s, "range_scan");
+    ck(ctx, cudaMemcpyAsync(hranges, dranges, sizeof(int32_t) * nops * 3 * MAXV, cudaMemcpyDeviceToHost, s),
+       "download ranges");
+    ck(ctx, cudaStreamSynchronize(s), "sync ranges");
+    collect_stages(ctx);
+    // ---------------- host planning
+    std::vector<Plan> plans(nprod);
+    for (int p = 0; p < nprod; ++p) {
+      plan_product(jobs[p], hranges + (2 * p) * 3 * MAXV, hranges + (2 * p + 1) * 3 * MAXV,
+                   ctx->num_sms, &plans[p]);
+      res[p].st = plans[p].st;
+    }
+    // ---------------- phase B: work arena layout (two passes: measure, assign)
+    int64_t dense_tasks_total = 0, nblocks_total = 0, hash_tasks_total = 0, nchunks_total = 0;
+    int64_t out_total = 0, scan_entries = 0;
+    int64_t max_S = 0;
+    std::vector<int> dense_ids, hash_ids, live_ids;
+    for (int p = 0; p < nprod; ++p) {
+      if (plans[p].st != KR_OK) continue;
+      const Prod& P = plans[p].p;
+      live_ids.push_back(p);
+      if (P.path == PATH_DENSE) {
+        dense_ids.push_back(p);
+        dense_tasks_total += plans[p].dense_task_cap;
+        nblocks_total += P.nblocks;
+        max_S = std::max(max_S, P.S);
+      } else {
+        hash_ids.push_back(p);
+        hash_tasks_total += P.ntasks;
+        scan_entries = std::max(scan_entries, radix_scan_entries(plans[p].out_cap));
+      }
+      nchunks_total += P.nchunks;
+      out_total += plans[p].out_cap;
+      scan_entries = std::max(scan_entries, radix_scan_entries(plans[p].radix_sort_n));
+    }
+    const int nlive = (int)live_ids.size();
+    size_t work_need = 0;
+    struct Arr {
+      DenseTask* tasks; int64_t* counters; int32_t* dense_ids; int64_t* block_begin;
+      int32_t* hash_ids; int64_t* task_begin; int64_t* chunk_begin; int64_t* counts;
+      int64_t* scan; uint64_t *okey, *oval, *okey2, *oval2; Prod* lprods; OpRef* oplists;
+      char* zero; size_t zero_bytes;
+    } A{};
+    for (int pass = 0; pass < 2; ++pass) {
+      Bump b(pass ? ctx->work : nullptr);
+      b.take<char>((int64_t)meta_need);
+      A.lprods = b.take<Prod>(nlive);
+      A.oplists = b.take<OpRef>(3 * (int64_t)nops);
+      A.dense_ids = b.take<int32_t>((int64_t)dense_ids.size() + 1);
+      A.block_begin = b.take<int64_t>((int64_t)dense_ids.size() + 1);
+      A.hash_ids = b.take<int32_t>((int64_t)hash_ids.size() + 1);
+      A.task_begin = b.take<int64_t>((int64_t)hash_ids.size() + 1);
+      A.chunk_begin = b.take<int64_t>(nlive + 1);
+      A.counts = b.take<int64_t>(nchunks_total + 1);
+      A.scan = b.take<int64_t>(scan_entries + 1);
+      A.tasks = b.take<DenseTask>(dense_tasks_total);
+      A.okey = b.take<uint64_t>(out_total);
+      A.oval = b.take<uint64_t>(out_total);
+      A.okey2 = b.take<uint64_t>(hash_ids.empty() ? 0 : out_total);
+      A.oval2 = b.take<uint64_t>(hash_ids.empty() ? 0 : out_total);
+      for (int p : live_ids) {
+        Plan& pl = plans[p];
+        for (int which = 0; which < 2; ++which) {
+          Operand& op = which ? pl.p.g : pl.p.f;
+          const int64_t n = op.n;
+          uint64_t* ka = b.take<uint64_t>(n);
+          uint64_t* kb = b.take<uint64_t>(n);
+          uint64_t* ia = b.take<uint64_t>(n);
+          uint64_t* ib = b.take<uint64_t>(n);
+          op.skey = ka;
+          op.sidx = ia;
+          op.skey2 = kb;
+          op.sidx2 = ib;
+          const int passes = which ? pl.passes_g : pl.passes_f;
+          if (op.sort_method == SORT_RADIX && passes % 2 == 0) { op.skey2 = ka; op.sidx2 = ia; }
+          op.code = b.take<int64_t>(n);
+          op.coef = (void*)b.take<uint64_t>(n);
+          if (pl.p.nt > 0) {
+            op.tcode = b.take<int64_t>(n);
+            op.kind = b.take<uint8_t>(n);
+          }
+        }
+      }
+      // zeroed region: task counters, dense arrays, tables (one memset)
+      b.off = (b.off + 255) / 256 * 256;
+      const size_t zero_start = b.off;
+      A.zero = b.base ? b.base + zero_start : nullptr;
+      A.counters = b.take<int64_t>(4);
+      for (int p : live_ids) {
+        Plan& pl = plans[p];
+        if (pl.p.path == PATH_DENSE) pl.p.dense = (void*)b.take<uint64_t>(pl.p.krange);
+        else pl.p.table = b.take<uint64_t>(2 * pl.p.slots);
+      }
+      A.zero_bytes = b.off - zero_start;
+      if (!pass) {
+        work_need = b.off;
+        ensure(ctx, &ctx->work, &ctx->work_cap, work_need + 1, s);
+        // the metadata lived in the old arena: re-upload after a regrowth
+        Bump m(ctx->work);
+        dprods = m.take<Prod>(nprod);
+        dops = m.take<OpRef>(nops);
+      }
+    }
+    // ---------------- finish the plans, upload
+    std::vector<int64_t> h_block_begin(dense_ids.size() + 1, 0), h_task_begin(hash_ids.size() + 1, 0);
+    std::vector<int64_t> h_chunk_begin(nlive + 1, 0);
+    std::vector<int32_t> h_dense_local, h_hash_local;
+    {
+      int64_t ob = 0, cb = 0;
+      for (int q = 0; q < nlive; ++q) {
+        Plan& pl = plans[live_ids[q]];
+        pl.p.out_cap = pl.out_cap;
+        pl.p.out_begin = ob;
+        pl.p.chunk_begin = cb;
+        h_chunk_begin[q] = cb;
+        ob += pl.out_cap;
+        cb += pl.p.nchunks;
+      }
+      h_chunk_begin[nlive] = cb;
+      int64_t bb = 0, tb = 0;
+      for (size_t q = 0; q < dense_ids.size(); ++q) {
+        h_block_begin[q] = bb;
+        bb += plans[dense_ids[q]].p.nblocks;
+      }
+      h_block_begin[dense_ids.size()] = bb;
+      for (size_t q = 0; q < hash_ids.size(); ++q) {
+        Plan& pl = plans[hash_ids[q]];
+        pl.p.task_begin = tb;
+        h_task_begin[q] = tb;
+        tb += pl.p.ntasks;
+      }
+      h_task_begin[hash_ids.size()] = tb;
+      // local (live) index of each product
+      std::vector<int> local(nprod, -1);
+      for (int q = 0; q < nlive; ++q) local[live_ids[q]] = q;
+      for (int p : dense_ids) h_dense_local.push_back(local[p]);
+      for (int p : hash_ids) h_hash_local.push_back(local[p]);
+    }
+    size_t pin_need = sizeof(Prod) * (nlive + 1) + 8 * (h_block_begin.size() + h_task_begin.size() +
+                                                      h_chunk_begin.size()) +
+                      4 * (h_dense_local.size() + h_hash_local.size()) +
+                      sizeof(OpRef) * 3 * (size_t)nops + 16 * 256;
+    ensure_pinned(ctx, pin_need, s);
+    Bump hb(ctx->pinned);
+    Prod* hl = hb.take<Prod>(nlive);
+    for (int q = 0; q < nlive; ++q) hl[q] = plans[live_ids[q]].p;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+      if (bytes == 0) return;
+      void* st = hb.take<char>((int64_t)bytes);
+      memcpy(st, src, bytes);
+      ck(ctx, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyHostToDevice, s), "upload plan");
+    };
+    if (nlive > 0) ck(ctx, cudaMemcpyAsync(A.lprods, hl, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s),
+                      "upload plan");
+    up(A.block_begin, h_block_begin.data(), 8 * h_block_begin.size());
+    up(A.task_begin, h_task_begin.data(), 8 * h_task_begin.size());
+    up(A.chunk_begin, h_chunk_begin.data(), 8 * h_chunk_begin.size());
+    up(A.dense_ids, h_dense_local.data(), 4 * h_dense_local.size());
+    up(A.hash_ids, h_hash_local.data(), 4 * h_hash_local.size());
+    // ---------------- device work
+    if (nlive > 0) {
+      std::vector<OpRef> bm, bt, all;
+      for (int q = 0; q < nlive; ++q) {
+        const Prod& P = plans[live_ids[q]].p;
+        for (int which = 0; which < 2; ++which) {
+          const Operand& op = which ? P.g : P.f;
+          all.push_back(OpRef{q, which});
+          if (op.sort_method == SORT_BITMAP) bm.push_back(OpRef{q, which});
+          if (op.sort_method == SORT_BITONIC) bt.push_back(OpRef{q, which});
+        }
+      }
+      std::vector<OpRef> packed = all;
+      packed.insert(packed.end(), bm.begin(), bm.end());
+      packed.insert(packed.end(), bt.begin(), bt.end());
+      OpRef* dlists = A.oplists;
+      up(dlists, packed.data(), sizeof(OpRef) * packed.size());
+      const OpRef* d_all = dlists;
+      const OpRef* d_bm = dlists + all.size();
+      const OpRef* d_bt = d_bm + bm.size();
+      mark(ctx, s, "plan_upload");
+      ck(ctx, cudaMemsetAsync(A.zero, 0, A.zero_bytes, s), "memset accumulators");
+      mark(ctx, s, "zero_accumulators");
+      ck(ctx, launch_encode(A.lprods, d_all, (int)all.size(), s), "encode");
+      ctx->launches += 1;
+      mark(ctx, s, "encode");
+      if (!bm.empty()) {
+        int64_t mx = 0;
+        for (auto& r : bm) {
+          const Prod& P = plans[live_ids[r.prod]].p;
+          const Operand& op = r.which ? P.g : P.f;
+          mx = std::max(mx, (op.key_range + 1023) / 1024);
+        }
+        const size_t smem = (size_t)mx * 33 * 4 + 64;
+        ck(ctx, launch_sort_small(A.lprods, d_bm, (int)bm.size(), SORT_BITMAP, smem, s), "bitmap sort");
+        ctx->launches += 1;
+      }
+      if (!bt.empty()) {
+        int64_t mx = 0;
+        for (auto& r : bt) {
+          const Prod& P = plans[live_ids[r.prod]].p;
+          mx = std::max(mx, (r.which ? P.g : P.f).n);
+        }
+        ck(ctx, launch_sort_small(A.lprods, d_bt, (int)bt.size(), SORT_BITONIC, (size_t)mx * 8, s),
+           "bitonic sort");
+        ctx->launches += 1;
+      }
+      for (int q = 0; q < nlive; ++q) {
+        const Plan& pl = plans[live_ids[q]];
+        for (int which = 0; which < 2; ++which) {
+          const Operand& op = which ? pl.p.g : pl.p.f;
+          if (op.sort_method != SORT_RADIX) continue;
+          const int bits = bits_for((uint64_t)op.key_range);
+          bool in_tmp = false;
+          // keys in skey/sidx; result must end in skey2/sidx2 (aliases skey when passes are even)
+          uint64_t* tk = op.skey2 == op.skey ? (uint64_t*)nullptr : op.skey2;
+          uint64_t* tv = op.sidx2 == op.sidx ? (uint64_t*)nullptr : op.sidx2;
+          if (!tk) {
+            // even number of passes: ping-pong through the spare buffers after skey/sidx
+            tk = (uint64_t*)op.code;            // n int64, free until the gather
+            tv = (uint64_t*)op.coef;            // n 8-byte values, free until the gather
+          }
+          ck(ctx, radix_sort_pairs(op.skey, op.sidx, tk, tv, op.n, bits, A.scan, s, &in_tmp),
+             "radix sort operand");
+          ctx->launches += 3 * ((bits + 7) / 8);
+        }
+      }
+      mark(ctx, s, "sort");
+      ck(ctx, launch_gather(A.lprods, d_all, (int)all.size(), s), "gather");
+      ctx->launches += 1;
+      mark(ctx, s, "gather");
+      if (!dense_ids.empty()) {
+        ck(ctx, launch_dense_plan(A.lprods, A.dense_ids, A.block_begin, (int)dense_ids.size(),
+                                  nblocks_total, A.tasks, dense_tasks_total, A.counters, s),
+           "dense plan");
+        ctx->launches += 1;
+        mark(ctx, s, "dense_plan");
+        const int64_t smem = max_S * 8;
+        const int per_sm = (int)std::max<int64_t>(1, std::min<int64_t>(4, (220 * 1024) / (smem + 2048)));
+        ck(ctx, launch_dense_accum(A.lprods, A.tasks, A.counters, dense_tasks_total, A.counters + 1,
+                                   ctx->num_sms * per_sm, max_S, s),
+           "dense accumulate");
+        ctx->launches += 1;
+        mark(ctx, s, "dense_accum");
+      }
+      if (!hash_ids.empty()) {
+        ck(ctx, launch_hash_insert(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(),
+                                   ctx->num_sms * 8, s),
+           "hash insert");
+        ctx->launches += 1;
+        mark(ctx, s, "hash_insert");
+      }
+      ck(ctx, launch_compact(A.lprods, nlive, A.chunk_begin, h_chunk_begin[nlive], A.counts, A.okey,
+                             A.oval, s),
+         "compaction");
+      ctx->launches += h_chunk_begin[nlive] > 0 ? 4 : 1;
+      mark(ctx, s, "compact");
+      ck(ctx, cudaMemcpyAsync(hl, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
+    }
+    ck(ctx, cudaStreamSynchronize(s), "sync results");
+    collect_stages(ctx);
+    // ---------------- statuses; regrow full tables
+    bool retry = false;
+    for (int q = 0; q < nlive; ++q) {
+      const int p = live_ids[q];
+      const Prod& P = hl[q];
+      if (P.status & ST_TABLE_FULL) {
+        const int mr = ins[p].opts.max_regrow;
+        const int allowed = mr > 0 ? mr : (mr < 0 ? 0 : 4);
+        // grow x4; the last allowed regrowth goes straight to the table the
+        // term-product bound asks for (a full table of that size means the
+        // probe limit, not the size, failed)
+        const int64_t bound = plans[p].bound_slots;
+        if (regrows[p] < allowed && P.slots < bound) {
+          regrows[p]++;
+          hints[p] = regrows[p] == allowed ? bound : std::min(P.slots * 4, bound);
+          retry = true;
+          continue;
+        }
+      }
+      res[p].st = status_to_kr(P.status);
+      res[p].n = P.nout;
+      res[p].prod = P;
+      res[p].dprod = A.lprods + q;
+      res[p].key = A.okey + P.out_start;
+      res[p].val = A.oval + P.out_start;
+      if (P.nout > P.out_cap) res[p].st = KR_ERR_CUDA;
+    }
+    if (retry) continue;
+    // ---------------- hash outputs: sort by key
+    mark(ctx, s, "begin");
+    for (int q = 0; q < nlive; ++q) {
+      const int p = live_ids[q];
+      ProdResult& r = res[p];
+      if (r.st != KR_OK || r.prod.path != PATH_HASH || r.n < 2 || ins[p].opts.unsorted) continue;
+      const int bits = bits_for((uint64_t)r.prod.krange);
+      bool in_tmp = false;
+      uint64_t* k = A.okey + r.prod.out_start;
+      uint64_t* v = A.oval + r.prod.out_start;
+      uint64_t* k2 = A.okey2 + r.prod.out_start;
+      uint64_t* v2 = A.oval2 + r.prod.out_start;
+      ck(ctx, radix_sort_pairs(k, v, k2, v2, r.n, bits, A.scan, s, &in_tmp), "output sort");
+      ctx->launches += 3 * ((bits + 7) / 8);
+      if (in_tmp) { r.key = k2; r.val = v2; }
+    }
+    mark(ctx, s, "output_sort");
+    return;
+  }
+}
+
+struct CtxGuard {
+  kr_ctx* c;
+  int prev = -1;
+  explicit CtxGuard(kr_ctx* ctx) : c(ctx) {
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+  }
+  ~CtxGuard() {
+    if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+  }
+};
+
+template <typename F>
+kr_status guarded(kr_ctx* ctx, F body) {
+  if (!ctx) return KR_ERR_INVALID;
+  try {
+    CtxGuard g(ctx);
+    return body();
+  } catch (const CudaFail& f) {
+    return from_cuda(f.e);
+  } catch (const std::bad_alloc&) {
+    ctx->err = "host allocation failed";
+    return KR_ERR_OOM;
+  } catch (...) {
+    ctx->err = "unexpected exception";
+    return KR_ERR_CUDA;
+  }
+}
+
+// copy n values from device src to dst (device or host)
+void copy_out(kr_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (!dst || bytes == 0) return;
+  ck(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s), "copy output");
+}
+
+kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
+  const Prod& P = ctx->res_prod;
+  const int64_t n = ctx->res_n;
+  h->nterms = n;
+  for (int k = 0; k < KR_MAXV; ++k) { h->omin[k] = 0; h->omax[k] = 0; }
+  for (int k = 0; k < P.np; ++k) {
+    h->omin[k] = P.omin[k];
+    h->omax[k] = P.omin[k] + P.w[k] - 1;
+  }
+  if (n > h->capacity) return KR_ERR_CAPACITY;
+  if (n == 0) return KR_OK;
+  const bool exps_dev = is_device_ptr(h->exps);
+  const bool codes_dev = is_device_ptr(h->codes);
+  int32_t* exps_tmp = nullptr;
+  int64_t ld = h->capacity;
+  if (h->exps && !exps_dev) {
+    // decode into the input arena, then one copy per variable row
+    ensure(ctx, &ctx->in_arena, &ctx->in_cap, (size_t)n * P.np * 4 + 256, s);
+    exps_tmp = (int32_t*)ctx->in_arena;
+    ld = n;
+  }
+  int32_t* ex = h->exps ? (exps_dev ? h->exps : exps_tmp) : nullptr;
+  ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, n, ex, ld, codes_dev ? h->codes : nullptr, s),
+     "decode");
+  ctx->launches += 1;
+  mark(ctx, s, "decode");
+  if (exps_tmp) {
+    for (int k = 0; k < P.np; ++k)
+      copy_out(ctx, h->exps + (int64_t)k * h->capacity, exps_tmp + (int64_t)k * n, (size_t)n * 4, s);
+  }
+  if (h->codes && !codes_dev) copy_out(ctx, h->codes, ctx->res_key, (size_t)n * 8, s);
+  copy_out(ctx, h->coef, ctx->res_val, (size_t)n * 8, s);
+  mark(ctx, s, "copy_out");
+  ck(ctx, cudaStreamSynchronize(s), "sync output");
+  collect_stages(ctx);
+  return KR_OK;
+}
+
+kr_status emit_pseries(kr_ctx* ctx, kr_pseries_out* h, cudaStream_t s) {
+  const Prod& P = ctx->res_prod;
+  const int64_t n = ctx->res_n;
+  h->nterms = n;
+  if (n > h->capacity) return KR_ERR_CAPACITY;
+  if (n == 0) return KR_OK;
+  const bool any_host = (h->exps && !is_device_ptr(h->exps)) || (h->trig && !is_device_ptr(h->trig)) ||
+                        (h->kind && !is_device_ptr(h->kind)) || (h->codes && !is_device_ptr(h->codes));
+  if (!any_host) {
+    ck(ctx, launch_decode_pseries(ctx->res_dprod, 0, ctx->res_key, n, h->exps, h->trig, h->kind,
+                                  h->capacity, h->codes, s),
+       "decode");
+    ctx->launches += 1;
+  } else {
+    ensure(ctx, &ctx->in_arena, &ctx->in_cap, (size_t)n * (4 * (P.np + P.nt) + 1 + 8) + 1024, s);
+    Bump b(ctx->in_arena);
+    int32_t* ex = b.take<int32_t>((int64_t)n * P.np);
+    int32_t* tr = b.take<int32_t>((int64_t)n * P.nt);
+    uint8_t* kd = b.take<uint8_t>(n);
+    ck(ctx, launch_decode_pseries(ctx->res_dprod, 0, ctx->res_key, n, ex, tr, kd, n, nullptr, s), "decode");
+    ctx->launches += 1;
+    if (h->exps)
+      for (int k = 0; k < P.np; ++k)
+        copy_out(ctx, h->exps + (int64_t)k * h->capacity, ex + (int64_t)k * n, (size_t)n * 4, s);
+    if (h->trig)
+      for (int k = 0; k < P.nt; ++k)
+        copy_out(ctx, h->trig + (int64_t)k * h->capacity, tr + (int64_t)k * n, (size_t)n * 4, s);
+    copy_out(ctx, h->kind, kd, (size_t)n, s);
+    copy_out(ctx, h->codes, ctx->res_key, (size_t)n * 8, s);
+  }
+  mark(ctx, s, "decode");
+  copy_out(ctx, h->coef, ctx->res_val, (size_t)n * 8, s);
+  mark(ctx, s, "copy_out");
+  ck(ctx, cudaStreamSynchronize(s), "sync output");
+  collect_stages(ctx);
+  return KR_OK;
+}
+
+void keep_result(kr_ctx* ctx, const ProdResult& r, bool poisson) {
+  ctx->has_result = true;
+  ctx->res_poisson = poisson;
+  ctx->res_prod = r.prod;
+  ctx->res_dprod = r.dprod;
+  ctx->res_key = r.key;
+  ctx->res_val = r.val;
+  ctx->res_n = r.n;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+kr_status kr_ctx_create(int32_t device, kr_ctx** out) {
+  if (!out) return KR_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return KR_ERR_CUDA;
+  }
+  kr_ctx* c = new (std::nothrow) kr_ctx;
+  if (!c) return KR_ERR_OOM;
+  c->device = device;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaSetDevice(prev);
+  if (c->num_sms <= 0) c->num_sms = 1;
+  *out = c;
+  return KR_OK;
+}
+
+void kr_ctx_destroy(kr_ctx* ctx) {
+  if (!ctx) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->in_arena) cudaFree(ctx->in_arena);
+  if (ctx->work) cudaFree(ctx->work);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  cudaSetDevice(prev);
+  delete ctx;
+}
+
+const char* kr_last_error(const kr_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+int64_t kr_ctx_scratch_bytes(const kr_ctx* ctx) {
+  return ctx ? (int64_t)(ctx->in_cap + ctx->work_cap) : 0;
+}
+
+kr_status kr_ctx_set_profiling(kr_ctx* ctx, int32_t enable) {
+  if (!ctx) return KR_ERR_INVALID;
+  ctx->profile = enable != 0;
+  ctx->nev = 0;
+  return KR_OK;
+}
+
+int32_t kr_ctx_stage_count(const kr_ctx* ctx) { return ctx ? (int32_t)ctx->stage_ms.size() : 0; }
+
+kr_status kr_ctx_stage(const kr_ctx* ctx, int32_t i, const char** name, double* ms) {
+  if (!ctx || i < 0 || i >= (int32_t)ctx->stage_ms.size()) return KR_ERR_INVALID;
+  if (name) *name = ctx->stage_name[i];
+  if (ms) *ms = ctx->stage_ms[i];
+  return KR_OK;
+}
+
+int64_t kr_ctx_launch_count(const kr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* kron_strerror(kr_status s) {
+  switch (s) {
+    case KR_OK: return "ok";
+    case KR_ERR_INVALID: return "invalid argument";
+    case KR_ERR_RANGE: return "exponent outside the coding box";
+    case KR_ERR_OVERFLOW: return "code range exceeds 2^63-1";
+    case KR_ERR_DUP: return "duplicate term in an input series";
+    case KR_ERR_OOM: return "out of memory";
+    case KR_ERR_CAPACITY: return "output capacity too small";
+    case KR_ERR_TIMEOUT: return "bounded device wait timed out";
+    case KR_ERR_CUDA: return "CUDA error";
+    case KR_ERR_TABLE_FULL: return "hash table full after the allowed regrowths";
+  }
+  return "unknown status";
+}
+
+kr_status kron_plan(const int32_t* emin, const int32_t* emax, int32_t nvars, int64_t* cvec_out,
+                    int64_t* range_out) {
+  if (!emin || !emax || nvars < 1 || nvars > KR_MAXV) return KR_ERR_INVALID;
+  int64_t w[KR_MAXV], c[KR_MAXV], W = 0;
+  for (int k = 0; k < nvars; ++k) {
+    if (emin[k] > emax[k]) return KR_ERR_INVALID;
+    w[k] = (int64_t)emax[k] - (int64_t)emin[k] + 1;
+  }
+  kr_status st = coding_vector(w, nvars, c, &W);
+  if (st != KR_OK) return st;
+  if (cvec_out)
+    for (int k = 0; k < nvars; ++k) cvec_out[k] = c[k];
+  if (range_out) *range_out = W;
+  return KR_OK;
+}
+
+kr_status kron_encode(kr_ctx* ctx, const int32_t* exps, int64_t n, int32_t nvars, const int32_t* emin,
+                      const int32_t* emax, int64_t* codes_out, kr_stream stream) {
+  if (n < 0 || (n > 0 && (!exps || !codes_out))) return KR_ERR_INVALID;
+  int64_t c[KR_MAXV], W;
+  kr_status st = kron_plan(emin, emax, nvars, c, &W);
+  if (st != KR_OK) return st;
+  if (n == 0) return KR_OK;
+  return guarded(ctx, [&]() -> kr_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    Bump b(nullptr);
+    b.take<uint32_t>(1);
+    const bool in_dev = is_device_ptr(exps), out_dev = is_device_ptr(codes_out);
+    if (!in_dev) b.take<int32_t>(n * nvars);
+    if (!out_dev) b.take<int64_t>(n);
+    ensure(ctx, &ctx->in_arena, &ctx->in_cap, b.off, s);
+    Bump a(ctx->in_arena);
+    uint32_t* dst = a.take<uint32_t>(1);
+    const int32_t* e = exps;
+    if (!in_dev) {
+      int32_t* t = a.take<int32_t>(n * nvars);
+      ck(ctx, cudaMemcpyAsync(t, exps, (size_t)n * nvars * 4, cudaMemcpyHostToDevice, s), "copy");
+      e = t;
+    }
+    int64_t* out = out_dev ? codes_out : a.take<int64_t>(n);
+    ck(ctx, cudaMemsetAsync(dst, 0, 4, s), "memset");
+    ck(ctx, launch_encode_box(e, n, nvars, emin, emax, c, out, dst, s), "encode");
+    if (!out_dev) ck(ctx, cudaMemcpyAsync(codes_out, out, (size_t)n * 8, cudaMemcpyDeviceToHost, s), "copy");
+    uint32_t hst = 0;
+    ck(ctx, cudaMemcpyAsync(&hst, dst, 4, cudaMemcpyDeviceToHost, s), "status");
+    ck(ctx, cudaStreamSynchronize(s), "sync");
+    return hst ? KR_ERR_RANGE : KR_OK;
+  });
+}
+
+kr_status kron_decode(kr_ctx* ctx, const int64_t* codes, int64_t n, int32_t nvars, const int32_t* emin,
+                      const int32_t* emax, int32_t* exps_out, kr_stream stream) {
+  if (n < 0 || (n > 0 && (!codes || !exps_out))) return KR_ERR_INVALID;
+  int64_t c[KR_MAXV], W;
+  kr_status st = kron_plan(emin, emax, nvars, c, &W);
+  if (st != KR_OK) return st;
+  if (n == 0) return KR_OK;
+  int32_t w[KR_MAXV];
+  for (int k = 0; k < nvars; ++k) w[k] = emax[k] - emin[k] + 1;
+  return guarded(ctx, [&]() -> kr_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool in_dev = is_device_ptr(codes), out_dev = is_device_ptr(exps_out);
+    Bump b(nullptr);
+    b.take<uint32_t>(1);
+    if (!in_dev) b.take<int64_t>(n);
+    if (!out_dev) b.take<int32_t>(n * nvars);
+    ensure(ctx, &ctx->in_arena, &ctx->in_cap, b.off, s);
+    Bump a(ctx->in_arena);
+    uint32_t* dst = a.take<uint32_t>(1);
+    const int64_t* cd = codes;
+    if (!in_dev) {
+      int64_t* t = a.take<int64_t>(n);
+      ck(ctx, cudaMemcpyAsync(t, codes, (size_t)n * 8, cudaMemcpyHostToDevice, s), "copy");
+      cd = t;
+    }
+    int32_t* out = out_dev ? exps_out : a.take<int32_t>(n * nvars);
+    ck(ctx, cudaMemsetAsync(dst, 0, 4, s), "memset");
+    ck(ctx, launch_decode_box(cd, n, nvars, emin, w, c, W, out, dst, s), "decode");
+    if (!out_dev)
+      ck(ctx, cudaMemcpyAsync(exps_out, out, (size_t)n * nvars * 4, cudaMemcpyDeviceToHost, s), "copy");
+    uint32_t hst = 0;
+    ck(ctx, cudaMemcpyAsync(&hst, dst, 4, cudaMemcpyDeviceToHost, s), "status");
+    ck(ctx, cudaStreamSynchronize(s), "sync");
+    return hst ? KR_ERR_RANGE : KR_OK;
+  });
+}
+
+kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out* h, const kr_opts* opts,
+                   kr_stream stream) {
+  if (!ctx || !f || !g || !h) return KR_ERR_INVALID;
+  if (f->nvars < 1 || f->nvars > KR_MAXV || g->nvars != f->nvars || h->nvars != f->nvars) return KR_ERR_INVALID;
+  if (f->type != g->type || (f->type != KR_I64 && f->type != KR_F64)) return KR_ERR_INVALID;
+  if (f->nterms < 0 || g->nterms < 0 || h->capacity < 0) return KR_ERR_INVALID;
+  if ((f->nterms > 0 && (!f->exps || !f->coef)) || (g->nterms > 0 && (!g->exps || !g->coef)))
+    return KR_ERR_INVALID;
+  if (h->capacity > 0 && !h->coef) return KR_ERR_INVALID;
+  return guarded(ctx, [&]() -> kr_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->has_result = false;
+    ctx->stage_ms.clear();
+    ctx->stage_name.clear();
+    ctx->nev = 0;
+    if (f->nterms == 0 || g->nterms == 0) {
+      h->nterms = 0;
+      for (int k = 0; k < KR_MAXV; ++k) { h->omin[k] = 0; h->omax[k] = 0; }
+      return KR_OK;
+    }
+    JobIn in;
+    in.poisson = false;
+    in.f64 = f->type == KR_F64;
+    in.np = f->nvars;
+    in.nt = 0;
+    in.fe = f->exps; in.fc = f->coef; in.nf = f->nterms;
+    in.ge = g->exps; in.gc = g->coef; in.ng = g->nterms;
+    if (opts) in.opts = *opts;
+    std::vector<ProdResult> res;
+    run_pipeline(ctx, {in}, s, res);
+    if (res[0].st != KR_OK) return res[0].st;
+    keep_result(ctx, res[0], false);
+    return emit_poly(ctx, h, s);
+  });
+}
+
+kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g, kr_pseries_out* h,
+                      const kr_opts* opts, kr_stream stream) {
+  if (!ctx || !f || !g || !h) return KR_ERR_INVALID;
+  if (f->ntrig < 1 || f->npoly < 0 || f->npoly + f->ntrig > KR_MAXV) return KR_ERR_INVALID;
+  if (g->npoly != f->npoly || g->ntrig != f->ntrig || h->npoly != f->npoly || h->ntrig != f->ntrig)
+    return KR_ERR_INVALID;
+  if (f->nterms < 0 || g->nterms < 0 || h->capacity < 0) return KR_ERR_INVALID;
+  auto bad = [](const kr_pseries* p) {
+    return p->nterms > 0 && ((p->npoly > 0 && !p->exps) || !p->trig || !p->kind || !p->coef);
+  };
+  if (bad(f) || bad(g)) return KR_ERR_INVALID;
+  if (h->capacity > 0 && !h->coef) return KR_ERR_INVALID;
+  if (opts && opts->path == KR_PATH_DENSE) return KR_ERR_INVALID;
+  return guarded(ctx, [&]() -> kr_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->has_result = false;
+    ctx->stage_ms.clear();
+    ctx->stage_name.clear();
+    ctx->nev = 0;
+    if (f->nterms == 0 || g->nterms == 0) {
+      h->nterms = 0;
+      return KR_OK;
+    }
+    JobIn in;
+    in.poisson = true;
+    in.f64 = true;
+    in.np = f->npoly;
+    in.nt = f->ntrig;
+    in.fe = f->exps; in.ft = f->trig; in.fk = f->kind; in.fc = f->coef; in.nf = f->nterms;
+    in.ge = g->exps; in.gt = g->trig; in.gk = g->kind; in.gc = g->coef; in.ng = g->nterms;
+    if (opts) in.opts = *opts;
+    std::vector<ProdResult> res;
+    run_pipeline(ctx, {in}, s, res);
+    if (res[0].st != KR_OK) return res[0].st;
+    keep_result(ctx, res[0], true);
+    return emit_pseries(ctx, h, s);
+  });
+}
+
+kr_status kron_fetch_poly(kr_ctx* ctx, kr_poly_out* h, kr_stream stream) {
+  if (!ctx || !h) return KR_ERR_INVALID;
+  if (!ctx->has_result || ctx->res_poisson || h->nvars != ctx->res_prod.np) return KR_ERR_INVALID;
+  return guarded(ctx, [&]() -> kr_status { return emit_poly(ctx, h, (cudaStream_t)stream); });
+}
+
+kr_status kron_fetch_pseries(kr_ctx* ctx, kr_pseries_out* h, kr_stream stream) {
+  if (!ctx || !h) return KR_ERR_INVALID;
+  if (!ctx->has_result || !ctx->res_poisson || h->npoly != ctx->res_prod.np ||
+      h->ntrig != ctx->res_prod.nt)
+    return KR_ERR_INVALID;
+  return guarded(ctx, [&]() -> kr_status { return emit_pseries(ctx, h, (cudaStream_t)stream); });
+}
+
+}  // extern "C"

@@ -1,0 +1,344 @@
+// Kronecker coding kernels: exponent range scan, encoding of the operands into
+// sort keys, gathering of the sorted operands, and decoding of output codes.
+//
+// Coding (Sec. 2, Table 2 and the equations after it): for a box
+// [e_min, e_max] with widths w_k = 1 + e_k,max - e_k,min the code of e is
+// sum_k c_k (e_k - e_k,min), c_0 = 1, c_k = prod_{l<k} w_l.  Each operand of a
+// product is coded with the product's widths and offset by its own minimum,
+// so that code_f(a) + code_g(b) = code_h(a + b) (the additivity of Eq. 5).
+// Trig multipliers use the balanced form sum_k c_k t_k over the symmetric box
+// |t_k| <= R_k; sums and differences of such codes are the codes of the sums
+// and differences of the vectors, and the sign of a code is the sign of the
+// highest-index nonzero entry, which is what the canonical form looks at.
+#include "kr_internal.cuh"
+
+namespace kr {
+
+// ---------------------------------------------------------------------------
+// per-operand minima / maxima of the exponents, max |t| of the multipliers
+// ranges layout per operand: [0, MAXV) min, [MAXV, 2 MAXV) max, [2 MAXV, 3 MAXV) max|t|
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_range_scan(const Prod* __restrict__ prods,
+                                                    const OpRef* __restrict__ ops,
+                                                    int32_t* __restrict__ ranges) {
+  const OpRef r = ops[blockIdx.x];
+  const Prod& P = prods[r.prod];
+  const Operand& O = r.which ? P.g : P.f;
+  __shared__ int32_t smin[MAXV][16], smax[MAXV][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nvar = P.np + P.nt;
+  for (int k = 0; k < nvar; ++k) {
+    const bool is_trig = k >= P.np;
+    const int32_t* row = is_trig ? O.t + (int64_t)(k - P.np) * O.n : O.e + (int64_t)k * O.n;
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x) {
+      int32_t x = row[i];
+      if (is_trig) x = x < 0 ? -x : x;
+      lo = min(lo, x);
+      hi = max(hi, x);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) { smin[k][warp] = lo; smax[k][warp] = hi; }
+  }
+  __syncthreads();
+  if (threadIdx.x < nvar) {
+    const int k = threadIdx.x;
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { lo = min(lo, smin[k][w]); hi = max(hi, smax[k][w]); }
+    int32_t* out = ranges + (int64_t)blockIdx.x * 3 * MAXV;
+    if (k < P.np) { out[k] = lo; out[MAXV + k] = hi; }
+    else { out[2 * MAXV + (k - P.np)] = hi; }
+  }
+}
+
+cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int32_t* dranges,
+                              cudaStream_t s) {
+  if (nops > 0) k_range_scan<<<nops, 512, 0, s>>>(dprods, dops, dranges);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// encoding of one term of an operand into its input key
+// poly:    key = code = sum_k c_k (e_k - emin_k)
+// Poisson: key = ((kind * T2) + tcode) * Wp + pcode, tcode >= 0 for canonical input
+// ---------------------------------------------------------------------------
+struct TermCode {
+  int64_t pcode;
+  int64_t tcode;
+  int kind;
+  uint32_t bad;   // status bits
+};
+
+__device__ __forceinline__ TermCode encode_term(const Prod& P, const Operand& O, int64_t i) {
+  TermCode tc;
+  tc.pcode = 0; tc.tcode = 0; tc.kind = 0; tc.bad = 0;
+  for (int k = 0; k < P.np; ++k) {
+    int32_t e = O.e[(int64_t)k * O.n + i];
+    if (e < O.emin[k] || e > O.emax[k]) tc.bad |= ST_RANGE;
+    tc.pcode += P.c[k] * (int64_t)(e - O.emin[k]);
+  }
+  if (P.nt > 0) {
+    for (int k = 0; k < P.nt; ++k) {
+      int32_t t = O.t[(int64_t)k * O.n + i];
+      int32_t a = t < 0 ? -t : t;
+      if (a > O.tmax[k]) tc.bad |= ST_RANGE;
+      tc.tcode += P.c[P.np + k] * (int64_t)t;
+    }
+    tc.kind = O.k[i];
+    if (tc.kind > 1) tc.bad |= ST_INVALID;
+    // canonical input: highest-index nonzero multiplier positive (code > 0),
+    // or the zero vector under a cosine
+    if (tc.tcode < 0 || (tc.tcode == 0 && tc.kind != 0)) tc.bad |= ST_INVALID;
+  }
+  return tc;
+}
+
+__device__ __forceinline__ uint64_t term_key(const Prod& P, const TermCode& tc) {
+  if (P.nt == 0) return (uint64_t)tc.pcode;
+  return (uint64_t)(((int64_t)tc.kind * P.T2 + tc.tcode) * P.Wp + tc.pcode);
+}
+
+__global__ void __launch_bounds__(256) k_encode(Prod* __restrict__ prods, const OpRef* __restrict__ ops) {
+  const OpRef r = ops[blockIdx.y];
+  Prod& P = prods[r.prod];
+  Operand& O = r.which ? P.g : P.f;
+  uint32_t bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < O.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TermCode tc = encode_term(P, O, i);
+    bad |= tc.bad;
+    uint64_t key = term_key(P, tc);
+    if (tc.bad) key = 0;   // keeps later kernels in bounds; the status fails the product
+    if (O.sort_method == SORT_BITONIC) {
+      O.skey[i] = (key << O.idx_bits) | (uint64_t)i;
+    } else {
+      O.skey[i] = key;
+      if (O.sort_method == SORT_RADIX) ((uint64_t*)O.sidx)[i] = (uint64_t)i;
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(&P.status, bad);
+}
+
+cudaError_t launch_encode(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s) {
+  if (nops > 0) k_encode<<<dim3(8, nops), 256, 0, s>>>(dprods, dops);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// gather: sorted keys (+ source index) -> sorted encoded operand arrays.
+// Duplicate keys are adjacent after the sort.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gather(Prod* __restrict__ prods, const OpRef* __restrict__ ops) {
+  const OpRef r = ops[blockIdx.y];
+  Prod& P = prods[r.prod];
+  Operand& O = r.which ? P.g : P.f;
+  const uint64_t mask = (O.idx_bits > 0) ? ((1ull << O.idx_bits) - 1) : 0;
+  uint32_t bad = 0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < O.n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t key, prev = ~0ull;
+    int64_t src;
+    if (O.sort_method == SORT_BITONIC) {
+      uint64_t v = O.skey[q];
+      key = v >> O.idx_bits;
+      src = (int64_t)(v & mask);
+      if (q > 0) prev = O.skey[q - 1] >> O.idx_bits;
+    } else {
+      // bitmap and radix sorts leave sorted keys in skey2 and indices in sidx2
+      key = O.skey2[q];
+      src = (int64_t)((const uint64_t*)O.sidx2)[q];
+      if (q > 0) prev = O.skey2[q - 1];
+    }
+    if (q > 0 && prev == key) bad |= ST_DUP;
+    if (src < 0 || src >= O.n) { bad |= ST_DUP; src = 0; }
+    if (P.nt == 0) {
+      O.code[q] = (int64_t)key;
+      if (P.f64) ((double*)O.coef)[q] = ((const double*)O.c)[src];
+      else ((int64_t*)O.coef)[q] = ((const int64_t*)O.c)[src];
+    } else {
+      TermCode tc = encode_term(P, O, src);
+      O.code[q] = tc.pcode;
+      O.tcode[q] = tc.tcode;
+      O.kind[q] = (uint8_t)tc.kind;
+      double c = ((const double*)O.c)[src];
+      // the 1/2 of the product-to-sum identities is applied to f once here;
+      // scaling by 1/2 is exact, so (c_f / 2) * c_g == (c_f * c_g) / 2
+      ((double*)O.coef)[q] = r.which == 0 ? 0.5 * c : c;
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (bad && (threadIdx.x & 31) == 0) atomicOr(&P.status, bad);
+}
+
+cudaError_t launch_gather(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s) {
+  if (nops > 0) k_gather<<<dim3(8, nops), 256, 0, s>>>(dprods, dops);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// decoding of output keys (inverse of the coding: mixed-radix digits)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_decode_poly(const Prod* __restrict__ prods, int prod,
+                                                     const uint64_t* __restrict__ okey, int64_t n,
+                                                     int32_t* __restrict__ exps, int64_t ld,
+                                                     int64_t* __restrict__ codes) {
+  const Prod& P = prods[prod];
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t code = (int64_t)okey[q];
+    if (codes) codes[q] = code;
+    if (exps) {
+      int64_t rem = code;
+      for (int k = 0; k < P.np; ++k) {
+        const int64_t d = (k + 1 < P.np) ? rem % P.w[k] : rem;
+        rem = (k + 1 < P.np) ? rem / P.w[k] : 0;
+        exps[(int64_t)k * ld + q] = (int32_t)(d + P.omin[k]);
+      }
+    }
+  }
+}
+
+cudaError_t launch_decode_poly(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
+                               int32_t* exps, int64_t ld, int64_t* codes, cudaStream_t s) {
+  if (n > 0) {
+    int64_t grid = (n + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_decode_poly<<<(unsigned)grid, 256, 0, s>>>(dprods, prod, okey, n, exps, ld, codes);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_decode_pseries(const Prod* __restrict__ prods, int prod,
+                                                        const uint64_t* __restrict__ okey, int64_t n,
+                                                        int32_t* __restrict__ exps,
+                                                        int32_t* __restrict__ trig,
+                                                        uint8_t* __restrict__ kind, int64_t ld,
+                                                        int64_t* __restrict__ codes) {
+  const Prod& P = prods[prod];
+  const int64_t per_kind = P.T2 * P.Wp;
+  const int64_t half = P.T2 - 1;   // sum_k c_k R_k
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t key = (int64_t)okey[q];
+    if (codes) codes[q] = key;
+    const int64_t kd = key / per_kind;
+    const int64_t rem = key - kd * per_kind;
+    const int64_t T = rem / P.Wp;
+    int64_t pc = rem - T * P.Wp;
+    if (kind) kind[q] = (uint8_t)kd;
+    if (exps) {
+      for (int k = 0; k < P.np; ++k) {
+        const int64_t d = (k + 1 < P.np) ? pc % P.w[k] : pc;
+        pc = (k + 1 < P.np) ? pc / P.w[k] : 0;
+        exps[(int64_t)k * ld + q] = (int32_t)(d + P.omin[k]);
+      }
+    }
+    if (trig) {
+      int64_t u = T + half;
+      for (int k = 0; k < P.nt; ++k) {
+        const int32_t wk = P.w[P.np + k];
+        const int64_t d = (k + 1 < P.nt) ? u % wk : u;
+        u = (k + 1 < P.nt) ? u / wk : 0;
+        trig[(int64_t)k * ld + q] = (int32_t)(d + P.omin[P.np + k]);
+      }
+    }
+  }
+}
+
+cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
+                                  int32_t* exps, int32_t* trig, uint8_t* kind, int64_t ld,
+                                  int64_t* codes, cudaStream_t s) {
+  if (n > 0) {
+    int64_t grid = (n + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_decode_pseries<<<(unsigned)grid, 256, 0, s>>>(dprods, prod, okey, n, exps, trig, kind, ld,
+                                                    codes);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// standalone coding of a box (kron_encode / kron_decode entry points)
+// ---------------------------------------------------------------------------
+struct Box {
+  int32_t emin[MAXV];
+  int32_t emax[MAXV];
+  int32_t w[MAXV];
+  int64_t c[MAXV];
+};
+
+__global__ void k_encode_box(const int32_t* __restrict__ exps, int64_t n, int nvars, Box b,
+                             int64_t* __restrict__ codes, uint32_t* status) {
+  uint32_t bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t code = 0;
+    for (int k = 0; k < nvars; ++k) {
+      int32_t e = exps[(int64_t)k * n + i];
+      if (e < b.emin[k] || e > b.emax[k]) bad = 1;
+      code += b.c[k] * (int64_t)(e - b.emin[k]);
+    }
+    codes[i] = code;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_RANGE);
+}
+
+__global__ void k_decode_box(const int64_t* __restrict__ codes, int64_t n, int nvars, Box b,
+                             int64_t W, int32_t* __restrict__ exps, uint32_t* status) {
+  uint32_t bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = codes[i];
+    if (rem < 0 || rem >= W) { bad = 1; rem = 0; }
+    for (int k = 0; k < nvars; ++k) {
+      const int64_t d = (k + 1 < nvars) ? rem % b.w[k] : rem;
+      rem = (k + 1 < nvars) ? rem / b.w[k] : 0;
+      exps[(int64_t)k * n + i] = (int32_t)(d + b.emin[k]);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_RANGE);
+}
+
+static Box make_box(int nvars, const int32_t* emin, const int32_t* emax, const int64_t* cvec) {
+  Box b;
+  for (int k = 0; k < MAXV; ++k) { b.emin[k] = 0; b.emax[k] = 0; b.w[k] = 1; b.c[k] = 0; }
+  for (int k = 0; k < nvars; ++k) {
+    b.emin[k] = emin[k];
+    b.emax[k] = emax[k];
+    b.w[k] = emax[k] - emin[k] + 1;
+    b.c[k] = cvec[k];
+  }
+  return b;
+}
+
+cudaError_t launch_encode_box(const int32_t* exps, int64_t n, int nvars, const int32_t* emin,
+                              const int32_t* emax, const int64_t* cvec, int64_t* codes,
+                              uint32_t* dstatus, cudaStream_t s) {
+  if (n > 0) {
+    int64_t grid = (n + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_encode_box<<<(unsigned)grid, 256, 0, s>>>(exps, n, nvars, make_box(nvars, emin, emax, cvec),
+                                                codes, dstatus);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode_box(const int64_t* codes, int64_t n, int nvars, const int32_t* emin,
+                              const int32_t* w, const int64_t* cvec, int64_t W, int32_t* exps,
+                              uint32_t* dstatus, cudaStream_t s) {
+  if (n > 0) {
+    int32_t emax[MAXV];
+    for (int k = 0; k < nvars; ++k) emax[k] = emin[k] + w[k] - 1;
+    int64_t grid = (n + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_decode_box<<<(unsigned)grid, 256, 0, s>>>(codes, n, nvars, make_box(nvars, emin, emax, cvec), W,
+                                                exps, dstatus);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kr

@@ -1,0 +1,212 @@
+// Hash (highly sparse) path, Sec. 3.2: the schoolbook loop accumulates
+// coefficient-code pairs into a hash table keyed by the code.
+//
+// GB300 design.  The paper's bucketed, cache-line table with an overflow
+// bucket and mod-N term ordering is prior art for a cache hierarchy; here the
+// table is one open-addressing array in device memory shared by the whole
+// grid.  A slot is 16 bytes: (key + 1, value), key 0 meaning empty.  A thread
+// claims an empty slot with a 64-bit atomicCAS on the key word and then adds
+// its coefficient with an atomic add on the value word (int64 wraps, so the
+// integer result does not depend on the order of the adds).  Collisions are
+// resolved by linear probing (the alternative the paper names in Sec. 3.2)
+// with a bounded probe count; a product that reaches the bound raises
+// TABLE_FULL and the host grows the table and multiplies again (the paper's
+// resize-and-rehash on a failed insert).  The home slot comes from a 64-bit
+// mixing function of the key, not from key mod N, because warps insert many
+// keys at once and structured codes would otherwise pile onto neighbouring
+// slots.
+//
+// Poisson series (Sec. 2, Eq. 6 with the factor 1/2): each pair of terms
+// gives one insert at the sum and one at the difference of the trig codes;
+// the result kind is cos when the factors have the same kind and sin
+// otherwise; the sign is - for the sum of sin*sin and for the difference of
+// cos*sin.  A negative trig code is folded to its absolute value (cos is even,
+// sin is odd) and a sine at code 0 is dropped.
+#include "kr_internal.cuh"
+
+namespace kr {
+
+constexpr int HASH_THREADS = 256;
+constexpr int HGROUP_R = 4;
+
+template <typename T>
+__device__ __forceinline__ void gatomic_add(T* p, T v);
+template <>
+__device__ __forceinline__ void gatomic_add<int64_t>(int64_t* p, int64_t v) {
+  atomicAdd((unsigned long long*)p, (unsigned long long)v);
+}
+template <>
+__device__ __forceinline__ void gatomic_add<double>(double* p, double v) {
+  atomicAdd(p, v);
+}
+
+// Insert-or-add; false when probe_limit slots were all taken by other keys.
+template <typename T>
+__device__ __forceinline__ bool hash_add(uint64_t* __restrict__ table, uint64_t mask, int limit,
+                                         uint64_t key, T val) {
+  const unsigned long long stored = key + 1ull;
+  uint64_t slot = mix64(key) & mask;
+  for (int p = 0; p < limit; ++p) {
+    unsigned long long* e = (unsigned long long*)(table + 2 * slot);
+    unsigned long long k = __ldcg(e);
+    if (k == 0ull) {
+      k = atomicCAS(e, 0ull, stored);
+      if (k == 0ull) k = stored;
+    }
+    if (k == stored) {
+      gatomic_add<T>((T*)(e + 1), val);
+      return true;
+    }
+    slot = (slot + 1) & mask;
+  }
+  return false;
+}
+
+struct HashTile {
+  int pid;
+  int64_t i0, i1, j0, j1;
+};
+
+__device__ __forceinline__ HashTile find_tile(const Prod* prods, const int32_t* hash_prods,
+                                              const int64_t* task_begin, int nhash, int64_t t) {
+  int lo = 0, hi = nhash - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (task_begin[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  HashTile h;
+  h.pid = hash_prods[lo];
+  const Prod& P = prods[h.pid];
+  const int64_t local = t - task_begin[lo];
+  const int64_t ti = local / P.tiles_j, tj = local - ti * P.tiles_j;
+  h.i0 = ti * P.tile_i;
+  h.i1 = min(P.f.n, h.i0 + P.tile_i);
+  h.j0 = tj * P.tile_j;
+  h.j1 = min(P.g.n, h.j0 + P.tile_j);
+  return h;
+}
+
+template <typename T>
+__device__ __forceinline__ bool poly_tile(const Prod& P, const HashTile& h) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = HASH_THREADS / 32;
+  const int64_t* __restrict__ F = P.f.code;
+  const int64_t* __restrict__ G = P.g.code;
+  const T* __restrict__ CF = (const T*)P.f.coef;
+  const T* __restrict__ CG = (const T*)P.g.coef;
+  const uint64_t mask = (uint64_t)P.slots - 1;
+  bool ok = true;
+  const int64_t ngroups = (h.i1 - h.i0 + HGROUP_R - 1) / HGROUP_R;
+  for (int64_t grp = warp; grp < ngroups; grp += NW) {
+    const int64_t ia = h.i0 + grp * HGROUP_R;
+    const int m = (int)min((int64_t)HGROUP_R, h.i1 - ia);
+    int64_t fr[HGROUP_R];
+    T cr[HGROUP_R];
+#pragma unroll
+    for (int r = 0; r < HGROUP_R; ++r) {
+      const int64_t i = ia + (r < m ? r : 0);
+      fr[r] = F[i];
+      cr[r] = CF[i];
+    }
+    for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
+      const int64_t gj = G[j];
+      const T cg = CG[j];
+#pragma unroll
+      for (int r = 0; r < HGROUP_R; ++r) {
+        if (r < m && ok) ok = hash_add<T>(P.table, mask, P.probe_limit, (uint64_t)(fr[r] + gj), cr[r] * cg);
+      }
+    }
+  }
+  return ok;
+}
+
+__device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = HASH_THREADS / 32;
+  const int64_t* __restrict__ PF = P.f.code;
+  const int64_t* __restrict__ PG = P.g.code;
+  const int64_t* __restrict__ TF = P.f.tcode;
+  const int64_t* __restrict__ TG = P.g.tcode;
+  const uint8_t* __restrict__ KF = P.f.kind;
+  const uint8_t* __restrict__ KG = P.g.kind;
+  const double* __restrict__ CF = (const double*)P.f.coef;   // already halved
+  const double* __restrict__ CG = (const double*)P.g.coef;
+  const uint64_t mask = (uint64_t)P.slots - 1;
+  const int64_t T2Wp = P.T2 * P.Wp;
+  bool ok = true;
+  const int64_t ngroups = (h.i1 - h.i0 + HGROUP_R - 1) / HGROUP_R;
+  for (int64_t grp = warp; grp < ngroups; grp += NW) {
+    const int64_t ia = h.i0 + grp * HGROUP_R;
+    const int m = (int)min((int64_t)HGROUP_R, h.i1 - ia);
+    int64_t pr[HGROUP_R], tr[HGROUP_R];
+    double cr[HGROUP_R];
+    int kr_[HGROUP_R];
+#pragma unroll
+    for (int r = 0; r < HGROUP_R; ++r) {
+      const int64_t i = ia + (r < m ? r : 0);
+      pr[r] = PF[i];
+      tr[r] = TF[i];
+      cr[r] = CF[i];
+      kr_[r] = KF[i];
+    }
+    for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
+      const int64_t pg = PG[j], tg = TG[j];
+      const int kg = KG[j];
+      const double cg = CG[j];
+#pragma unroll
+      for (int r = 0; r < HGROUP_R; ++r) {
+        if (r >= m || !ok) continue;
+        const int64_t pc = pr[r] + pg;
+        const double hcoef = cr[r] * cg;         // (C_f / 2) * C_g
+        const int kd = kr_[r] ^ kg;              // cos if same kinds, sin otherwise
+        // sum term
+        {
+          int64_t T = tr[r] + tg;
+          double v = (kr_[r] & kg) ? -hcoef : hcoef;   // sin*sin: -cos(a+b)
+          if (T < 0) { T = -T; if (kd) v = -v; }
+          if (!(T == 0 && kd)) {
+            const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+            ok = hash_add<double>(P.table, mask, P.probe_limit, key, v);
+          }
+        }
+        // difference term
+        if (ok) {
+          int64_t T = tr[r] - tg;
+          double v = (!kr_[r] && kg) ? -hcoef : hcoef;  // cos*sin: -sin(a-b)
+          if (T < 0) { T = -T; if (kd) v = -v; }
+          if (!(T == 0 && kd)) {
+            const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+            ok = hash_add<double>(P.table, mask, P.probe_limit, key, v);
+          }
+        }
+      }
+    }
+  }
+  return ok;
+}
+
+__global__ void __launch_bounds__(HASH_THREADS) k_hash_insert(Prod* __restrict__ prods,
+                                                              const int32_t* __restrict__ hash_prods,
+                                                              const int64_t* __restrict__ task_begin,
+                                                              int nhash) {
+  const int64_t ntasks = task_begin[nhash];
+  for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const HashTile h = find_tile(prods, hash_prods, task_begin, nhash, t);
+    Prod& P = prods[h.pid];
+    if (*(volatile uint32_t*)&P.status) continue;   // failed product: skip its remaining tiles
+    bool ok;
+    if (P.nt > 0) ok = pseries_tile(P, h);
+    else if (P.f64) ok = poly_tile<double>(P, h);
+    else ok = poly_tile<int64_t>(P, h);
+    if (!ok) atomicOr(&P.status, ST_TABLE_FULL);
+  }
+}
+
+cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
+                               int nhash, int grid, cudaStream_t s) {
+  if (nhash <= 0) return cudaSuccess;
+  k_hash_insert<<<grid, HASH_THREADS, 0, s>>>(dprods, dhash_prods, dtask_begin, nhash);
+  return cudaGetLastError();
+}
+
+}  // namespace kr

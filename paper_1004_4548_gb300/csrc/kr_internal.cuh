@@ -1,0 +1,170 @@
+// Internal declarations of libkron: the per-product plan that the host writes
+// and every kernel reads, device helpers, and the kernel launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kron.h"
+
+namespace kr {
+
+constexpr int MAXV = KR_MAXV;
+constexpr int PATH_DENSE = 1;
+constexpr int PATH_HASH = 2;
+
+// status bits a kernel may raise for one product (OR-ed into Prod::status)
+constexpr uint32_t ST_RANGE = 1u;       // exponent outside the coding box
+constexpr uint32_t ST_DUP = 2u;         // repeated input key
+constexpr uint32_t ST_INVALID = 4u;     // non-canonical trig input, sine of zero vector
+constexpr uint32_t ST_TABLE_FULL = 8u;  // hash probe limit reached
+constexpr uint32_t ST_OUTCAP = 16u;     // compaction found more terms than reserved
+
+// sort method chosen per operand by the host
+constexpr int SORT_BITMAP = 1;   // key range fits an on-chip bitmap
+constexpr int SORT_BITONIC = 2;  // n fits a shared-memory bitonic network
+constexpr int SORT_RADIX = 3;    // device-wide LSD radix sort
+
+// One input series on the device.
+struct Operand {
+  const int32_t* e;     // [np][n] exponents
+  const int32_t* t;     // [nt][n] trig multipliers (Poisson)
+  const uint8_t* k;     // [n] kinds (Poisson)
+  const void* c;        // [n] coefficients (int64 or double)
+  int64_t n;
+  int32_t emin[MAXV];   // this operand's exponent minima (its coding offset)
+  int32_t emax[MAXV];   // declared maxima (range check)
+  int32_t tmax[MAXV];   // max |t_k| of this operand (range check)
+  // encoded, sorted copies in scratch
+  uint64_t* skey;       // sort keys (bitonic: key << idx_bits | index, sorted in place)
+  uint64_t* sidx;       // radix path: source indices
+  uint64_t* skey2;      // bitmap / radix paths: sorted keys
+  uint64_t* sidx2;      // bitmap / radix paths: source index of each sorted key
+  int64_t* code;        // sorted: polynomial code (poly) or poly part (Poisson)
+  int64_t* tcode;       // sorted: signed trig code (Poisson)
+  uint8_t* kind;        // sorted kinds (Poisson)
+  void* coef;           // sorted coefficients (Poisson f: pre-multiplied by 1/2)
+  int32_t sort_method;
+  int32_t idx_bits;     // bits of the index packed under the key (bitmap/bitonic)
+  int64_t key_range;    // input keys lie in [0, key_range)
+};
+
+// One product, planned on the host, read by every kernel.
+struct Prod {
+  Operand f, g;
+  int32_t np, nt;       // polynomial variables, trig variables (0: polynomial product)
+  int32_t f64;          // coefficients are double
+  int32_t path;         // PATH_DENSE or PATH_HASH
+  int64_t c[MAXV];      // coding vector; poly part [0, np), trig part [np, np + nt)
+  int32_t w[MAXV];      // output widths
+  int32_t omin[MAXV];   // output box minimum (poly), -R_k (trig)
+  int64_t Wp;           // polynomial code range (product of poly widths)
+  int64_t T2;           // canonical |trig code| values: (Wt - 1) / 2 + 1
+  int64_t krange;       // output key range: Wp, or 2 * T2 * Wp for Poisson
+  // dense path
+  int64_t S;            // output codes per block
+  int64_t nblocks;
+  int64_t work_target;  // pairs per task
+  void* dense;          // [krange] accumulators
+  // hash path
+  uint64_t* table;      // [slots][2] = (key + 1, value); key 0 = empty
+  int64_t slots;        // power of two
+  int32_t probe_limit;
+  int32_t tile_i, tile_j;
+  int64_t tiles_j;      // tiles along g
+  int64_t task_begin;   // first task index of this product (hash tiles)
+  int64_t ntasks;
+  // compaction
+  int64_t chunk;        // accumulator slots per compaction chunk
+  int64_t nchunks;
+  int64_t chunk_begin;  // first chunk index of this product
+  int64_t out_cap;      // output terms reserved
+  int64_t out_begin;    // first output slot in the batch output arrays (reserved)
+  // results
+  uint32_t status;
+  int64_t nout;
+  int64_t out_start;    // start of this product's terms in the output arrays
+};
+
+// A dense-path task: one output block, a slice of f.
+struct DenseTask {
+  int32_t prod;
+  int32_t pad;
+  int64_t block;
+  int64_t i0, i1;
+  int64_t single;       // 1 when the block has one task (no other writer)
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t lower_bound_i64(const int64_t* a, int64_t n, int64_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// 64-bit mixing function (the finaliser of MurmurHash3, Appleby) for table slots
+__device__ __forceinline__ uint64_t mix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (host side); each returns cudaGetLastError()
+// ---------------------------------------------------------------------------
+struct OpRef {      // (product, operand) pair addressed by a per-operand kernel
+  int32_t prod;
+  int32_t which;    // 0 = f, 1 = g
+};
+
+cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int32_t* dranges,
+                              cudaStream_t s);
+cudaError_t launch_encode(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s);
+cudaError_t launch_sort_small(Prod* dprods, const OpRef* dops, int nops, int method,
+                              size_t smem, cudaStream_t s);
+cudaError_t launch_gather(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s);
+
+cudaError_t launch_dense_plan(const Prod* dprods, const int32_t* ddense_prods,
+                              const int64_t* dblock_begin, int ndense, int64_t nblocks_total,
+                              DenseTask* dtasks, int64_t task_cap, int64_t* dtask_count,
+                              cudaStream_t s);
+cudaError_t launch_dense_accum(const Prod* dprods, const DenseTask* dtasks,
+                               const int64_t* dtask_count, int64_t task_cap, int64_t* dtask_next,
+                               int grid, int64_t max_S, cudaStream_t s);
+int dense_accum_threads();
+cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
+                               int nhash, int grid, cudaStream_t s);
+cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
+                           int64_t* dcounts, uint64_t* okey, uint64_t* oval, cudaStream_t s);
+cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, cudaStream_t s);
+
+// Device-wide LSD radix sort of (key, 8-byte payload) pairs over the low
+// `bits` bits of the key.  key/val and key_tmp/val_tmp ping-pong; after the
+// call the sorted data is in the tmp arrays when *result_in_tmp is true.
+// dscan holds radix_scan_entries(n) int64.
+constexpr int RADIX_TILE = 4096;
+int64_t radix_scan_entries(int64_t n);
+cudaError_t radix_sort_pairs(uint64_t* key, uint64_t* val, uint64_t* key_tmp, uint64_t* val_tmp,
+                             int64_t n, int bits, int64_t* dscan, cudaStream_t s,
+                             bool* result_in_tmp);
+
+cudaError_t launch_decode_poly(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
+                               int32_t* exps, int64_t ld, int64_t* codes, cudaStream_t s);
+cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
+                                  int32_t* exps, int32_t* trig, uint8_t* kind, int64_t ld,
+                                  int64_t* codes, cudaStream_t s);
+cudaError_t launch_encode_box(const int32_t* exps, int64_t n, int nvars, const int32_t* emin,
+                              const int32_t* emax, const int64_t* cvec, int64_t* codes,
+                              uint32_t* dstatus, cudaStream_t s);
+cudaError_t launch_decode_box(const int64_t* codes, int64_t n, int nvars, const int32_t* emin,
+                              const int32_t* w, const int64_t* cvec, int64_t W, int32_t* exps,
+                              uint32_t* dstatus, cudaStream_t s);
+
+}  // namespace kr

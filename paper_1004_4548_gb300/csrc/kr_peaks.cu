@@ -1,0 +1,92 @@
+// Peak-rate probes for the roofline of the dense path.  The paper measures a
+// multiplication by its clock cycles per monomial-by-monomial multiplication
+// (Sec. 5) and calls a kernel optimal when that count approaches the cost of
+// one coefficient multiply-add.  On the GPU the dense path's multiply-add is a
+// shared-memory atomic add of a product, so its ceiling is the chip-wide rate
+// of conflict-free shared-memory atomic adds, measured here.
+#include <algorithm>
+
+#include "kr_internal.cuh"
+
+namespace kr {
+
+constexpr int PK_THREADS = 512;
+constexpr int PK_SLOTS = 8192;   // 64 KB of 8-byte counters
+constexpr int PK_ITERS = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(PK_THREADS) k_probe_smem_atomic(T* __restrict__ sink, T inc) {
+  __shared__ T s[PK_SLOTS];
+  for (int i = threadIdx.x; i < PK_SLOTS; i += blockDim.x) s[i] = (T)0;
+  __syncthreads();
+  // consecutive lanes hit consecutive 8-byte words: no bank conflicts, no
+  // two lanes of a warp on one address
+  int a = threadIdx.x;
+#pragma unroll 16
+  for (int it = 0; it < PK_ITERS; ++it) {
+    atomicAdd(&s[a], inc);
+    a = (a + PK_THREADS) & (PK_SLOTS - 1);
+  }
+  __syncthreads();
+  T acc = (T)0;
+  for (int i = threadIdx.x; i < PK_SLOTS; i += blockDim.x) acc += s[i];
+  if (acc == (T)-1) sink[blockIdx.x] = acc;   // keeps the work observable
+}
+
+template <>
+__global__ void __launch_bounds__(PK_THREADS) k_probe_smem_atomic<int64_t>(int64_t* __restrict__ sink,
+                                                                           int64_t inc) {
+  __shared__ unsigned long long s[PK_SLOTS];
+  for (int i = threadIdx.x; i < PK_SLOTS; i += blockDim.x) s[i] = 0;
+  __syncthreads();
+  int a = threadIdx.x;
+#pragma unroll 16
+  for (int it = 0; it < PK_ITERS; ++it) {
+    atomicAdd(&s[a], (unsigned long long)inc);
+    a = (a + PK_THREADS) & (PK_SLOTS - 1);
+  }
+  __syncthreads();
+  unsigned long long acc = 0;
+  for (int i = threadIdx.x; i < PK_SLOTS; i += blockDim.x) acc += s[i];
+  if (acc == ~0ull) sink[blockIdx.x] = (int64_t)acc;
+}
+
+}  // namespace kr
+
+using namespace kr;
+
+extern "C" double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t reps) {
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return -1.0; }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  int per_sm = 0;
+  if (f64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_smem_atomic<double>, PK_THREADS, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_smem_atomic<int64_t>, PK_THREADS, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int grid = sms * per_sm;
+  void* sink = nullptr;
+  double best = -1.0;
+  cudaEvent_t a, b;
+  if (cudaMalloc(&sink, (size_t)grid * 8) != cudaSuccess) { cudaGetLastError(); cudaSetDevice(prev); return -1.0; }
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int r = 0; r < (reps > 0 ? reps : 5) + 1; ++r) {
+    cudaEventRecord(a, 0);
+    if (f64) k_probe_smem_atomic<double><<<grid, PK_THREADS>>>((double*)sink, 1.0);
+    else k_probe_smem_atomic<int64_t><<<grid, PK_THREADS>>>((int64_t*)sink, 1);
+    cudaEventRecord(b, 0);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double ops = (double)grid * PK_THREADS * PK_ITERS;
+    if (r > 0 && ms > 0.f) best = std::max(best, ops / (ms * 1e-3));
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (cudaGetLastError() != cudaSuccess) best = -1.0;
+  cudaSetDevice(prev);
+  return best;
+}

@@ -1,0 +1,172 @@
+// Host-side planning of one product: coding box, path, scratch sizes.
+#include <cmath>
+
+#include "kr_plan.h"
+
+namespace kr {
+
+int bits_for(uint64_t range) {
+  int b = 0;
+  if (range <= 1) return 0;
+  const uint64_t top = range - 1;
+  while (b < 64 && (top >> b) != 0) ++b;
+  return b;
+}
+
+// Coding vector of Sec. 2: c_0 = 1, c_k = prod_{l<k} w_l; W = prod_k w_k.
+kr_status coding_vector(const int64_t* w, int n, int64_t* c, int64_t* W) {
+  unsigned __int128 acc = 1;
+  for (int k = 0; k < n; ++k) {
+    if (w[k] < 1) return KR_ERR_INVALID;
+    c[k] = (int64_t)acc;
+    acc *= (unsigned __int128)w[k];
+    if (acc > (unsigned __int128)INT64_MAX) return KR_ERR_OVERFLOW;
+  }
+  *W = (int64_t)acc;
+  return KR_OK;
+}
+
+static int64_t next_pow2(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static void plan_sort(Operand& op, int64_t key_range, int* passes, int64_t* radix_n) {
+  op.key_range = key_range;
+  op.idx_bits = 0;
+  *passes = 0;
+  if (key_range <= BITMAP_MAX_BITS) {
+    op.sort_method = SORT_BITMAP;
+  } else if (op.n <= BITONIC_MAX_N && bits_for((uint64_t)key_range) + bits_for((uint64_t)op.n) <= 63) {
+    op.sort_method = SORT_BITONIC;
+    op.idx_bits = bits_for((uint64_t)op.n);
+  } else {
+    op.sort_method = SORT_RADIX;
+    *passes = (bits_for((uint64_t)key_range) + 7) / 8;
+    if (op.n > *radix_n) *radix_n = op.n;
+  }
+}
+
+void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_sms, Plan* out) {
+  Plan& pl = *out;
+  pl = Plan();
+  Prod& P = pl.p;
+  P.f = job.f;
+  P.g = job.g;
+  P.np = job.np;
+  P.nt = job.nt;
+  P.f64 = job.f64 ? 1 : 0;
+  const kr_opts& o = job.opts;
+  // ---- coding box of the product (output widths; each operand offset by its own minimum)
+  int64_t w[MAXV], c[MAXV];
+  for (int k = 0; k < P.np; ++k) {
+    P.f.emin[k] = rf[k];
+    P.f.emax[k] = rf[MAXV + k];
+    P.g.emin[k] = rg[k];
+    P.g.emax[k] = rg[MAXV + k];
+    const int64_t lo = (int64_t)rf[k] + rg[k], hi = (int64_t)rf[MAXV + k] + rg[MAXV + k];
+    if (lo < INT32_MIN || hi > INT32_MAX) { pl.st = KR_ERR_OVERFLOW; return; }
+    P.omin[k] = (int32_t)lo;
+    w[k] = hi - lo + 1;
+    if (w[k] > INT32_MAX) { pl.st = KR_ERR_OVERFLOW; return; }
+    P.w[k] = (int32_t)w[k];
+  }
+  int64_t Wp = 1;
+  if (P.np > 0) {
+    pl.st = coding_vector(w, P.np, c, &Wp);
+    if (pl.st != KR_OK) return;
+  }
+  for (int k = 0; k < P.np; ++k) P.c[k] = c[k];
+  P.Wp = Wp;
+  P.T2 = 1;
+  P.krange = Wp;
+  if (P.nt > 0) {
+    int64_t wt[MAXV], ct[MAXV], Wt = 1;
+    for (int k = 0; k < P.nt; ++k) {
+      P.f.tmax[k] = rf[2 * MAXV + k];
+      P.g.tmax[k] = rg[2 * MAXV + k];
+      const int64_t R = (int64_t)rf[2 * MAXV + k] + rg[2 * MAXV + k];
+      wt[k] = 2 * R + 1;
+      if (wt[k] > INT32_MAX) { pl.st = KR_ERR_OVERFLOW; return; }
+      P.w[P.np + k] = (int32_t)wt[k];
+      P.omin[P.np + k] = (int32_t)(-R);
+    }
+    pl.st = coding_vector(wt, P.nt, ct, &Wt);
+    if (pl.st != KR_OK) return;
+    for (int k = 0; k < P.nt; ++k) P.c[P.np + k] = ct[k];
+    P.T2 = (Wt - 1) / 2 + 1;
+    const unsigned __int128 kr = (unsigned __int128)2 * (unsigned __int128)P.T2 * (unsigned __int128)Wp;
+    if (kr > (unsigned __int128)INT64_MAX) { pl.st = KR_ERR_OVERFLOW; return; }
+    P.krange = (int64_t)kr;
+  }
+  const int64_t nf = P.f.n, ng = P.g.n;
+  const double pairs = (double)nf * (double)ng;
+  // ---- path (Sec. 3.2: the density of the product decides)
+  if (job.poisson) {
+    P.path = PATH_HASH;
+  } else if (o.path == KR_PATH_DENSE) {
+    if ((double)P.krange * 8.0 > (double)DENSE_MAX_BYTES) { pl.st = KR_ERR_INVALID; return; }
+    P.path = PATH_DENSE;
+  } else if (o.path == KR_PATH_HASH) {
+    P.path = PATH_HASH;
+  } else {
+    const bool fits = (double)P.krange * 8.0 <= (double)DENSE_MAX_BYTES;
+    const bool dense_enough = (double)P.krange <= DENSE_KAPPA * pairs + 65536.0;
+    P.path = (fits && dense_enough) ? PATH_DENSE : PATH_HASH;
+  }
+  // ---- operand sorts
+  for (int which = 0; which < 2; ++which) {
+    Operand& op = which ? P.g : P.f;
+    int64_t kr;
+    if (P.nt == 0) {
+      int64_t span = 0;
+      for (int k = 0; k < P.np; ++k) span += P.c[k] * (int64_t)(op.emax[k] - op.emin[k]);
+      kr = span + 1;
+    } else {
+      kr = P.krange;
+    }
+    plan_sort(op, kr, which ? &pl.passes_g : &pl.passes_f, &pl.radix_sort_n);
+    pl.op_bytes[which] = op.n * (8 * 7 + 1) + 8 * 256;
+  }
+  // ---- accumulators
+  if (P.path == PATH_DENSE) {
+    int64_t S = o.block_slots > 0 ? o.block_slots : DEFAULT_S;
+    if (S < 256) S = 256;
+    if (S > MAX_S) S = MAX_S;
+    S = ceil_div(S, 32) * 32;
+    const int64_t kr32 = ceil_div(P.krange, 32) * 32;
+    if (S > kr32) S = kr32;
+    P.S = S;
+    P.nblocks = ceil_div(P.krange, S);
+    const double tgt = pairs / (double)(num_sms * 4);
+    P.work_target = (int64_t)std::max(tgt, (double)(2 * S));
+    pl.dense_task_cap = P.nblocks * 64;
+    pl.accum_bytes = P.krange * 8;
+    P.chunk = COMPACT_CHUNK;
+    P.nchunks = ceil_div(P.krange, P.chunk);
+    pl.out_cap = std::min((double)P.krange, pairs) > 0 ? (int64_t)std::min((double)P.krange, pairs) : 0;
+  } else {
+    const double m = job.poisson ? 2.0 : 1.0;
+    const double est = std::min(m * pairs, (double)P.krange);
+    double alpha = o.load_factor > 0.0 && o.load_factor <= 0.9 ? o.load_factor : DEFAULT_LOAD;
+    int64_t slots = next_pow2(std::max<int64_t>(1024, (int64_t)std::ceil(est / alpha)));
+    pl.bound_slots = slots;
+    if (o.table_slots > 0) slots = next_pow2(o.table_slots);
+    if (job.slots_hint > 0) slots = job.slots_hint;
+    P.slots = slots;
+    P.probe_limit = o.probe_limit > 0 ? o.probe_limit : DEFAULT_PROBES;
+    P.tile_i = HASH_TILE_I;
+    P.tile_j = HASH_TILE_J;
+    P.tiles_j = ceil_div(ng, HASH_TILE_J);
+    P.ntasks = ceil_div(nf, HASH_TILE_I) * P.tiles_j;
+    pl.accum_bytes = slots * 16;
+    P.chunk = COMPACT_CHUNK;
+    P.nchunks = ceil_div(slots, P.chunk);
+    pl.out_cap = (int64_t)std::min((double)slots, est);
+  }
+}
+
+}  // namespace kr

@@ -1,0 +1,94 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports every
+symbol include/kron.h declares, and its host-side coding plan reproduces the
+paper's worked examples.  No device compute is called here."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1004_4548_gb300 as kron
+from paper_1004_4548_gb300 import binding
+from workloads import total_degree_tuples
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "kron.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w]+\s*\**\s+\**(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "return")))
+
+
+def test_library_builds_and_loads():
+    L = kron.load()
+    assert os.path.exists(kron.lib_path())
+    assert L is not None
+
+
+def test_every_declared_symbol_is_exported():
+    L = kron.load()
+    names = declared_functions()
+    assert len(names) >= 12, names
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in kron.h but not exported"
+    assert set(binding.SIGNATURES) <= set(names)
+
+
+def test_table1_codes():
+    """Table 1: three variables in [0, 3]; c = (1, 4, 16), Eq. 2: 3 + 4 = 7."""
+    c, W = kron.kron_plan([0, 0, 0], [3, 3, 3])
+    assert list(c) == [1, 4, 16] and W == 64
+    rows = [list(map(int, l.split())) for l in open(os.path.join(GOLDEN, "table1_codes.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 10
+    for z, y, x, code in rows:
+        assert c[0] * x + c[1] * y + c[2] * z == code
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_table2_rows(seed):
+    """Table 2: codes of the generalised substitution in terms of w0."""
+    rng = np.random.default_rng(seed)
+    lo = rng.integers(-20, 5, size=3).astype(np.int32)
+    hi = lo + rng.integers(2, 9, size=3).astype(np.int32)
+    c, W = kron.kron_plan(lo, hi)
+    w0 = int(hi[0] - lo[0] + 1)
+    assert W == int(np.prod((hi - lo + 1).astype(np.int64)))
+    for l in open(os.path.join(GOLDEN, "table2_rows.txt")):
+        if not l.strip() or l.startswith("#"):
+            continue
+        d1, d0, a, b = l.split()
+        e = lo.astype(np.int64).copy()
+        e[1] = lo[1] + int(d1)
+        e[0] = hi[0] if d0 == "max" else lo[0] + int(d0)
+        code = int(np.dot(c, e - lo))
+        assert code == int(a) + int(b) * w0
+
+
+def test_overflow_boundary():
+    # 2^63 - 1 = 7^2 * 73 * 127 * 337 * 92737 * 649657: accepted
+    w = [7, 7, 73, 127, 337, 92737, 649657]
+    assert math.prod(w) == (1 << 63) - 1
+    c, W = kron.kron_plan([0] * 7, [x - 1 for x in w])
+    assert W == (1 << 63) - 1
+    # 2^63: rejected
+    with pytest.raises(kron.KronError) as e:
+        kron.kron_plan([0, 0, 0], [(1 << 21) - 1] * 3)
+    assert e.value.status == kron.KR_ERR_OVERFLOW
+    with pytest.raises(kron.KronError) as e:
+        kron.kron_plan([3], [2])
+    assert e.value.status == kron.KR_ERR_INVALID
+
+
+def test_fateman_density_matches_paper():
+    """Sec. 3: the Fateman factors have about one nonzero monomial every 300 codes
+    when coded with the widths of the product (the reading used throughout)."""
+    rows = total_degree_tuples(4, 30)
+    assert rows.shape[0] == 46376
+    c, W = kron.kron_plan([0] * 4, [60] * 4)
+    assert W == 61 ** 4
+    assert 290 < W / rows.shape[0] < 310

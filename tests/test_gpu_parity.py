@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+int64 products: bit-exact.  float64 products: per output term
+|gpu - oracle| <= 1e-12 * (sum of |contributions| to that term).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_compare import (assert_poly_close, assert_poly_equal, assert_pseries_close, to_np)
+from workloads import (PSeries, Poly, Rng, poisson_random, random_poly, random_pseries,
+                       workload_cfg1, workload_cfg2, workload_cfg3, workload_cfg4)
+
+pytestmark = pytest.mark.gpu
+NT = max(1, min(16, os.cpu_count() or 1))
+REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def kron():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1004_4548_gb300 as k
+    k.load()
+    return k
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_poly(k, f, g, device_inputs=True, **opts):
+    if device_inputs:
+        ex, cf, _, _ = k.poly_mul(dev(f.exps), dev(f.coef), dev(g.exps), dev(g.coef), **opts)
+    else:
+        ex, cf, _, _ = k.poly_mul(f.exps, f.coef, g.exps, g.coef, host_out=True, **opts)
+    return to_np(ex), to_np(cf)
+
+
+def run_pseries(k, f, g, device_inputs=True, **opts):
+    if device_inputs:
+        F = PSeries(dev(f.exps), dev(f.trig), dev(f.kind), dev(f.coef))
+        G = PSeries(dev(g.exps), dev(g.trig), dev(g.kind), dev(g.coef))
+        out = k.poisson_mul(F, G, **opts)
+    else:
+        out = k.poisson_mul(f, g, host_out=True, **opts)
+    return tuple(to_np(x) for x in out[:4])
+
+
+# ---------------------------------------------------------------------------
+# the benchmark workloads
+# ---------------------------------------------------------------------------
+
+def test_cfg1_dense_and_hash_bit_exact(kron):
+    f, g = workload_cfg1()
+    r = oracle.poly_mul(f, g)
+    for path in (kron.KR_PATH_AUTO, kron.KR_PATH_DENSE, kron.KR_PATH_HASH):
+        ex, cf = run_poly(kron, f, g, path=path)
+        assert_poly_equal(ex, cf, r, f"cfg1 path={path}")
+
+
+def test_cfg2_dense_bit_exact(kron):
+    f, g = workload_cfg2()
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    assert r.coef.shape[0] == 135751 and not r.overflow
+    ex, cf = run_poly(kron, f, g)
+    assert_poly_equal(ex, cf, r, "cfg2 dense")
+    for S in (2048, 28672):
+        ex, cf = run_poly(kron, f, g, path=kron.KR_PATH_DENSE, block_slots=S)
+        assert_poly_equal(ex, cf, r, f"cfg2 dense S={S}")
+
+
+def test_cfg3_hash_bit_exact(kron):
+    f, g = workload_cfg3()
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    ex, cf = run_poly(kron, f, g)
+    assert_poly_equal(ex, cf, r, "cfg3 hash")
+
+
+def test_cfg4_reduced_full_compare(kron):
+    f, g = workload_cfg4(2500)
+    r = oracle.poisson_mul(f, g, nthreads=NT, keep_zero=True)
+    out = run_pseries(kron, f, g)
+    assert_pseries_close(out, r, REL, "cfg4 n=2500")
+
+
+def test_cfg4_full_size_sampled_shard(kron):
+    """Full cfg4 (20000 x 20000 terms) on the GPU; one 1/4096 slice of the output
+    keys (FNV-1a shard) recomputed exactly by the oracle."""
+    f, g = workload_cfg4()
+    out = run_pseries(kron, f, g)
+    ge, gt, gk, gc = out
+    keys = np.concatenate([gk.astype(np.int32)[None, :], gt, ge], axis=0).T
+    mod, sid = 4096, 17
+    sh = oracle.shard_of_keys(keys, mod)
+    sel = sh == sid
+    r = oracle.poisson_mul(f, g, nthreads=NT, shard=(mod, sid), keep_zero=True)
+    assert r.coef.shape[0] > 1000
+    assert_pseries_close((ge[:, sel], gt[:, sel], gk[sel], gc[sel]), r, REL, "cfg4 shard")
+
+
+# ---------------------------------------------------------------------------
+# random cases: sizes spanning several tiles plus ragged tails
+# ---------------------------------------------------------------------------
+
+POLY_CASES = [
+    # v, nf, ng, lo, hi
+    (1, 1, 1, -3, 3),
+    (1, 37, 1000, -500, 700),
+    (2, 1, 777, -40, 40),
+    (3, 513, 257, [-5, 0, -9], [6, 30, 2]),
+    (4, 2000, 1500, -6, 6),
+    (5, 3000, 4100, [0, -2, -3, 0, -1], [9, 7, 5, 11, 3]),
+    (7, 1200, 900, -2, 3),
+    (2, 20000, 300, [-5000, -3], [5000, 4]),      # radix-sorted operand
+]
+
+
+@pytest.mark.parametrize("case", range(len(POLY_CASES)))
+@pytest.mark.parametrize("dtype", ["i64", "f64"])
+def test_random_poly(kron, case, dtype):
+    v, nf, ng, lo, hi = POLY_CASES[case]
+    f = random_poly(v, nf, lo, hi, 1000 + case, dtype)
+    g = random_poly(v, ng, lo, hi, 2000 + case, dtype)
+    r = oracle.poly_mul(f, g, nthreads=NT, keep_zero=(dtype == "f64"))
+    for path in (kron.KR_PATH_AUTO, kron.KR_PATH_DENSE, kron.KR_PATH_HASH):
+        for device_inputs in (True, False):
+            try:
+                ex, cf = run_poly(kron, f, g, device_inputs, path=path)
+            except kron.KronError as e:
+                if e.status == kron.KR_ERR_INVALID and path == kron.KR_PATH_DENSE:
+                    continue   # code range too large for a dense array
+                raise
+            what = f"case {case} {dtype} path={path} dev={device_inputs}"
+            if dtype == "i64":
+                assert_poly_equal(ex, cf, r, what)
+            else:
+                assert_poly_close(ex, cf, r, REL, what)
+
+
+PS_CASES = [
+    # npoly, ntrig, nf, ng, prange, trange
+    (0, 1, 1, 1, 0, 3),
+    (1, 1, 40, 33, 3, 5),
+    (2, 3, 700, 1100, 3, 4),
+    (3, 4, 3000, 2500, 4, 8),
+    (1, 6, 1500, 1700, 2, 2),
+]
+
+
+@pytest.mark.parametrize("case", range(len(PS_CASES)))
+def test_random_pseries(kron, case):
+    np_, nt, nf, ng, pr, tr = PS_CASES[case]
+    f = random_pseries(np_, nt, nf, pr, tr, 3000 + case)
+    g = random_pseries(np_, nt, ng, pr, tr, 4000 + case)
+    r = oracle.poisson_mul(f, g, nthreads=NT, keep_zero=True)
+    for device_inputs in (True, False):
+        out = run_pseries(kron, f, g, device_inputs)
+        assert_pseries_close(out, r, REL, f"pseries case {case} dev={device_inputs}")
+
+
+def test_werner_special_cases_on_gpu(kron):
+    """t_g = 0, t_f = t_g, and non-canonical sums/differences through the hash path."""
+    f = PSeries(np.array([[0, 1, -1, 2]], np.int32), np.array([[1, 1, 2, 0], [1, 0, 1, 1]], np.int32),
+                np.array([0, 1, 0, 1], np.uint8), np.array([2.0, -3.0, 0.5, 7.0]))
+    g = PSeries(np.array([[3, -1, 0]], np.int32), np.array([[0, 1, 1], [0, 0, 1]], np.int32),
+                np.array([0, 1, 1], np.uint8), np.array([5.0, 11.0, -13.0]))
+    r = oracle.poisson_mul(f, g, keep_zero=True)
+    out = run_pseries(kron, f, g)
+    assert_pseries_close(out, r, REL, "werner special")
+
+
+# ---------------------------------------------------------------------------
+# path independence, capacity contract, regrowth, errors, coding entry points
+# ---------------------------------------------------------------------------
+
+def test_dense_equals_hash_bit_exact(kron):
+    for s in range(3):
+        f = random_poly(4, 1500 + 97 * s, -7, 7, 50 + s)
+        g = random_poly(4, 1300 + 31 * s, -7, 7, 60 + s)
+        a = run_poly(kron, f, g, path=kron.KR_PATH_DENSE)
+        b = run_poly(kron, f, g, path=kron.KR_PATH_HASH)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_capacity_two_phase(kron):
+    import ctypes
+    from paper_1004_4548_gb300 import binding as B
+    f = random_poly(3, 300, -4, 4, 71)
+    g = random_poly(3, 200, -4, 4, 72)
+    r = oracle.poly_mul(f, g)
+    ctx = kron.context()
+    cap = 5
+    F = B.kr_poly(3, f.n, f.exps.ctypes.data, f.coef.ctypes.data, 0)
+    G = B.kr_poly(3, g.n, g.exps.ctypes.data, g.coef.ctypes.data, 0)
+    ex = np.zeros((3, cap), np.int32); cf = np.zeros(cap, np.int64)
+    H = B.kr_poly_out(3, cap, 0, ex.ctypes.data, cf.ctypes.data, None)
+    st = ctx.L.poly_mul(ctx.h, ctypes.byref(F), ctypes.byref(G), ctypes.byref(H), None, None)
+    assert st == kron.KR_ERR_CAPACITY and H.nterms == r.coef.shape[0]
+    n = int(H.nterms)
+    ex = np.zeros((3, n), np.int32); cf = np.zeros(n, np.int64)
+    H = B.kr_poly_out(3, n, 0, ex.ctypes.data, cf.ctypes.data, None)
+    assert ctx.L.kron_fetch_poly(ctx.h, ctypes.byref(H), None) == kron.KR_OK
+    assert_poly_equal(ex, cf, r, "two-phase fetch")
+
+
+def test_table_full_regrows(kron):
+    f, g = workload_cfg3()
+    f = Poly(f.exps[:, :1500].copy(), f.coef[:1500].copy())
+    g = Poly(g.exps[:, :1500].copy(), g.coef[:1500].copy())
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    assert r.coef.shape[0] > 4096
+    ex, cf = run_poly(kron, f, g, path=kron.KR_PATH_HASH, table_slots=4096, probe_limit=64)
+    assert_poly_equal(ex, cf, r, "after regrowth")
+    ex, cf = run_poly(kron, f, g, path=kron.KR_PATH_HASH, table_slots=1024, probe_limit=64, max_regrow=2)
+    assert_poly_equal(ex, cf, r, "after two regrowths")
+    with pytest.raises(kron.KronError) as e:
+        run_poly(kron, f, g, path=kron.KR_PATH_HASH, table_slots=4096, probe_limit=64, max_regrow=-1)
+    assert e.value.status == kron.KR_ERR_TABLE_FULL
+
+
+def test_error_statuses(kron):
+    f = random_poly(2, 50, -3, 3, 81)
+    dup = Poly(np.concatenate([f.exps, f.exps[:, :1]], axis=1), np.concatenate([f.coef, f.coef[:1]]))
+    with pytest.raises(kron.KronError) as e:
+        run_poly(kron, dup, f)
+    assert e.value.status == kron.KR_ERR_DUP
+    big = Poly(np.array([[0, 1 << 22], [0, 1 << 22], [0, 1 << 22]], np.int32), np.array([1, 2], np.int64))
+    with pytest.raises(kron.KronError) as e:
+        run_poly(kron, big, big)
+    assert e.value.status == kron.KR_ERR_OVERFLOW
+    p = random_pseries(1, 2, 20, 2, 3, 82)
+    bad = PSeries(p.exps.copy(), p.trig.copy(), p.kind.copy(), p.coef.copy())
+    bad.trig[:, 0] = [0, -1]   # highest-index multiplier negative: not canonical
+    with pytest.raises(kron.KronError) as e:
+        run_pseries(kron, bad, p)
+    assert e.value.status == kron.KR_ERR_INVALID
+
+
+def test_empty_and_single_terms(kron):
+    f = random_poly(3, 10, -2, 2, 91)
+    e = Poly(np.zeros((3, 0), np.int32), np.zeros(0, np.int64))
+    ex, cf, _, _ = kron.poly_mul(e.exps, e.coef, f.exps, f.coef, host_out=True)
+    assert to_np(cf).shape[0] == 0
+    one = Poly(np.array([[1], [-2], [0]], np.int32), np.array([3], np.int64))
+    r = oracle.poly_mul(one, f)
+    assert_poly_equal(*run_poly(kron, one, f), r, "single term")
+
+
+def test_encode_decode_roundtrip(kron):
+    rows = [list(map(int, l.split())) for l in open(os.path.join(os.path.dirname(__file__),
+            "golden", "table1_codes.txt")) if l.strip() and not l.startswith("#")]
+    exps = np.array([[x for z, y, x, c in rows], [y for z, y, x, c in rows], [z for z, y, x, c in rows]],
+                    np.int32)
+    codes = to_np(kron.kron_encode(dev(exps), [0, 0, 0], [3, 3, 3]))
+    assert list(codes) == [c for *_, c in rows]
+    back = to_np(kron.kron_decode(dev(codes), [0, 0, 0], [3, 3, 3]))
+    assert np.array_equal(back, exps)
+    # exhaustive round trip on a Laurent box, host buffers
+    lo, hi = np.array([-3, 2, -1, 0], np.int32), np.array([1, 5, 4, 2], np.int32)
+    grid = np.stack(np.meshgrid(*[np.arange(a, b + 1) for a, b in zip(lo, hi)], indexing="ij"), 0)
+    allp = grid.reshape(4, -1).astype(np.int32)
+    c = to_np(kron.kron_encode(allp, lo, hi))
+    assert np.array_equal(np.sort(c), np.arange(allp.shape[1]))
+    assert np.array_equal(to_np(kron.kron_decode(c, lo, hi)), allp)
+    with pytest.raises(kron.KronError) as e:
+        kron.kron_encode(allp, lo, hi - 1)
+    assert e.value.status == kron.KR_ERR_RANGE
