@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary hash/Poisson lines")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiler runs)")
     return ap.parse_args()
 
 
@@ -317,7 +318,7 @@ def main():
                 "sm_cycles_per_term_product": (clk["sm_mhz"] * 1e6 * ms * 1e-3 / tp * 152)
                 if clk.get("sm_mhz") else None,
                 "paths": paths}
-        line["cpu_baseline"] = cpu_baseline(f, g)
+        line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(f, g)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
