@@ -63,7 +63,8 @@ typedef enum {
   KR_ERR_CAPACITY = 6,   /* output buffers too small; required count returned */
   KR_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
   KR_ERR_CUDA = 8,       /* a CUDA runtime call failed; see kr_last_error */
-  KR_ERR_TABLE_FULL = 9  /* hash table full after every allowed regrowth */
+  KR_ERR_TABLE_FULL = 9, /* hash table full after every allowed regrowth */
+  KR_ERR_TOO_LARGE = 10  /* the problem exceeds a fixed limit of the entry point */
 } kr_status;
 
 typedef enum { KR_I64 = 0, KR_F64 = 1 } kr_coef_t;
@@ -212,6 +213,34 @@ kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g,
  * (after KR_ERR_CAPACITY) into h.  KR_ERR_INVALID if there is none. */
 kr_status kron_fetch_poly(kr_ctx* ctx, kr_poly_out* h, kr_stream stream);
 kr_status kron_fetch_pseries(kr_ctx* ctx, kr_pseries_out* h, kr_stream stream);
+
+/* Dense-path accumulation that allocates nothing.  The paper has no
+ * counterpart: this entry point serves callers that cannot let a library call
+ * cudaMalloc or cudaFree, because their device memory is owned by their own
+ * allocator or a fixed budget, or because they cannot accept the device
+ * synchronisation that an allocation or a free brings.
+ *
+ * Computes out[c] = sum over pairs with fcode[i] + gcode[j] = c of
+ * fcoef[i] * gcoef[j] for c in [0, W): the dense distributed product of
+ * Sec. 3.1, with the same kernels as poly_mul's dense path.
+ *   fcode, gcode: device int64 [nf], [ng]: Kronecker codes of both operands in
+ *     the product's box (each operand offset by its own minimum, as poly_mul
+ *     codes them), ascending, without repeats, with fcode[i] + gcode[j] < W.
+ *   fcoef, gcoef: device int64 or double (type) [nf], [ng].
+ *   out: device int64 or double [W], written in full (zero where no term).
+ * Scratch: a file-scope device array of 8 MiB (every GPU that loads the
+ * library holds it until the process exits).  W > 2^24 returns
+ * KR_ERR_TOO_LARGE.  No device or host memory is allocated.  The first call
+ * on each device looks up the array's device address with that device
+ * current (cudaGetSymbolAddress) and caches it; that first call should come
+ * before any stream capture.  Every call uses the same array and leaves its
+ * contents behind; the call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the array:
+ * order them.  Asynchronous on `stream`; inputs with violated preconditions
+ * give a wrong product but no access outside the caller's buffers. */
+kr_status kron_dense_product_static(const int64_t* fcode, const void* fcoef, int64_t nf,
+                                    const int64_t* gcode, const void* gcoef, int64_t ng,
+                                    kr_coef_t type, int64_t W, void* out, kr_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Measurement                                                               */

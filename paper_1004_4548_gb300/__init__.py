@@ -7,8 +7,9 @@ include/kron.h.  This package is the thin Python binding of that library.
 """
 from .binding import (  # noqa: F401
     KR_OK, KR_ERR_INVALID, KR_ERR_RANGE, KR_ERR_OVERFLOW, KR_ERR_DUP, KR_ERR_OOM,
-    KR_ERR_CAPACITY, KR_ERR_TIMEOUT, KR_ERR_CUDA, KR_ERR_TABLE_FULL,
+    KR_ERR_CAPACITY, KR_ERR_TIMEOUT, KR_ERR_CUDA, KR_ERR_TABLE_FULL, KR_ERR_TOO_LARGE,
     KR_PATH_AUTO, KR_PATH_DENSE, KR_PATH_HASH, KR_MAXV,
     Context, KronError, context, load, lib_path,
     kron_plan, kron_encode, kron_decode, poly_mul, poisson_mul, kr_probe_smem_atomic_rate,
+    kron_dense_product_static,
 )

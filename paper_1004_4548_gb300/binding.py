@@ -17,7 +17,7 @@ from . import _build
 
 KR_MAXV = 16
 KR_OK, KR_ERR_INVALID, KR_ERR_RANGE, KR_ERR_OVERFLOW, KR_ERR_DUP, KR_ERR_OOM, \
-    KR_ERR_CAPACITY, KR_ERR_TIMEOUT, KR_ERR_CUDA, KR_ERR_TABLE_FULL = range(10)
+    KR_ERR_CAPACITY, KR_ERR_TIMEOUT, KR_ERR_CUDA, KR_ERR_TABLE_FULL, KR_ERR_TOO_LARGE = range(11)
 KR_I64, KR_F64 = 0, 1
 KR_PATH_AUTO, KR_PATH_DENSE, KR_PATH_HASH = 0, 1, 2
 
@@ -63,6 +63,8 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_double)]),
     "kr_ctx_launch_count": (_i64, [_vp]),
     "kr_probe_smem_atomic_rate": (ctypes.c_double, [_i32, _i32, _i32]),
+    "kron_dense_product_static": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_int, _i64,
+                                                 _vp, _vp]),
     "kron_plan": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
     "kron_encode": (ctypes.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
     "kron_decode": (ctypes.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp]),
@@ -352,3 +354,23 @@ def poisson_mul(f, g, ctx: Context | None = None, stream=None, capacity: int | N
     _check(ctx.L, ctx.h, st, "poisson_mul")
     n = int(h.nterms)
     return ex[:, :n], tr[:, :n], kd[:n], cf[:n], (cd[:n] if cd is not None else None)
+
+
+def kron_dense_product_static(fcode, fcoef, gcode, gcoef, W: int, out=None, stream=None):
+    """Dense product array out[W] of two sorted, coded operands, using only the
+    library's static scratch array (no allocation inside the library).
+
+    All arrays are CUDA torch tensors; out (int64 or float64 [W]) is allocated
+    here by torch when not given.
+    """
+    L = load()
+    torch = _torch()
+    is_f64 = fcoef.dtype == torch.float64
+    if out is None:
+        out = torch.empty((W,), dtype=fcoef.dtype, device=fcoef.device)
+    st = L.kron_dense_product_static(fcode.data_ptr(), fcoef.data_ptr(), int(fcode.shape[0]),
+                                     gcode.data_ptr(), gcoef.data_ptr(), int(gcode.shape[0]),
+                                     KR_F64 if is_f64 else KR_I64, int(W), out.data_ptr(),
+                                     _stream_ptr(stream))
+    _check(L, None, st, "kron_dense_product_static")
+    return out

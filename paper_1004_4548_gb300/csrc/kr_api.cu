@@ -772,6 +772,7 @@ const char* kron_strerror(kr_status s) {
     case KR_ERR_TIMEOUT: return "bounded device wait timed out";
     case KR_ERR_CUDA: return "CUDA error";
     case KR_ERR_TABLE_FULL: return "hash table full after the allowed regrowths";
+    case KR_ERR_TOO_LARGE: return "problem exceeds the fixed limit of this entry point";
   }
   return "unknown status";
 }
