@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary hash/Poisson lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiler runs)")
+    ap.add_argument("--block-slots", type=int, default=0, help="dense output block size (0 = library default)")
     return ap.parse_args()
 
 
@@ -205,6 +206,7 @@ def main():
     oc = torch.empty((nout,), dtype=torch.int64, device=dev)
     H = B.kr_poly_out(4, nout, 0, oe.data_ptr(), oc.data_ptr(), None)
     O = B.kr_opts()
+    O.block_slots = args.block_slots
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():

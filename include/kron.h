@@ -77,7 +77,7 @@ typedef struct kr_ctx kr_ctx;
 /* A sparse polynomial (Sec. 3.1, "sparse distributed" representation). */
 typedef struct {
   int32_t nvars;         /* 1 .. KR_MAXV */
-  int64_t nterms;        /* >= 0 */
+  int64_t nterms;        /* 0 .. 2^31 - 2 */
   const int32_t* exps;   /* [nvars][nterms] */
   const void* coef;      /* int64_t or double [nterms] */
   kr_coef_t type;

@@ -231,7 +231,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Bump m(nullptr);
       m.take<Prod>(nprod);
       m.take<OpRef>(nops);
-      m.take<int32_t>((int64_t)nops * 3 * MAXV);
+      m.take<int32_t>((int64_t)nops * RANGE_STRIDE);
       meta_need = m.off;
     }
     ensure_pinned(ctx, meta_need + 4096, s);
@@ -242,12 +242,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Bump m(ctx->work);
       dprods = m.take<Prod>(nprod);
       dops = m.take<OpRef>(nops);
-      dranges = m.take<int32_t>((int64_t)nops * 3 * MAXV);
+      dranges = m.take<int32_t>((int64_t)nops * RANGE_STRIDE);
     }
     Bump hp(ctx->pinned);
     Prod* hprods = hp.take<Prod>(nprod);
     OpRef* hops = hp.take<OpRef>(nops);
-    int32_t* hranges = hp.take<int32_t>((int64_t)nops * 3 * MAXV);
+    int32_t* hranges = hp.take<int32_t>((int64_t)nops * RANGE_STRIDE);
     for (int p = 0; p < nprod; ++p) {
       Prod P{};
       P.f = jobs[p].f;
@@ -265,20 +265,20 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     ck(ctx, launch_range_scan(dprods, dops, nops, dranges, s), "range scan");
     ctx->launches += 1;
     mark(ctx, s, "range_scan");
-    ck(ctx, cudaMemcpyAsync(hranges, dranges, sizeof(int32_t) * nops * 3 * MAXV, cudaMemcpyDeviceToHost, s),
+    ck(ctx, cudaMemcpyAsync(hranges, dranges, sizeof(int32_t) * nops * RANGE_STRIDE, cudaMemcpyDeviceToHost, s),
        "download ranges");
     ck(ctx, cudaStreamSynchronize(s), "sync ranges");
     collect_stages(ctx);
     // ---------------- host planning
     std::vector<Plan> plans(nprod);
     for (int p = 0; p < nprod; ++p) {
-      plan_product(jobs[p], hranges + (2 * p) * 3 * MAXV, hranges + (2 * p + 1) * 3 * MAXV,
+      plan_product(jobs[p], hranges + (2 * p) * RANGE_STRIDE, hranges + (2 * p + 1) * RANGE_STRIDE,
                    ctx->num_sms, &plans[p]);
       res[p].st = plans[p].st;
     }
     // ---------------- phase B: work arena layout (two passes: measure, assign)
     int64_t dense_tasks_total = 0, nblocks_total = 0, hash_tasks_total = 0, nchunks_total = 0;
-    int64_t out_total = 0, scan_entries = 0;
+    int64_t out_total = 0, scan_entries = 0, bins_total = 0;
     int64_t max_S = 0;
     std::vector<int> dense_ids, hash_ids, live_ids;
     for (int p = 0; p < nprod; ++p) {
@@ -293,7 +293,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       } else {
         hash_ids.push_back(p);
         hash_tasks_total += P.ntasks;
-        scan_entries = std::max(scan_entries, radix_scan_entries(plans[p].out_cap));
+        const int64_t nb = order_bins(P.krange);
+        if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, 2 * (nb + 1));
+        else scan_entries = std::max(scan_entries, radix_scan_entries(plans[p].out_cap));
       }
       nchunks_total += P.nchunks;
       out_total += plans[p].out_cap;
@@ -305,6 +307,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       DenseTask* tasks; int64_t* counters; int32_t* dense_ids; int64_t* block_begin;
       int32_t* hash_ids; int64_t* task_begin; int64_t* chunk_begin; int64_t* counts;
       int64_t* scan; uint64_t *okey, *oval, *okey2, *oval2; Prod* lprods; OpRef* oplists;
+      int64_t* bins;
       char* zero; size_t zero_bytes;
     } A{};
     for (int pass = 0; pass < 2; ++pass) {
@@ -319,6 +322,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       A.chunk_begin = b.take<int64_t>(nlive + 1);
       A.counts = b.take<int64_t>(nchunks_total + 1);
       A.scan = b.take<int64_t>(scan_entries + 1);
+      A.bins = b.take<int64_t>(bins_total);
       A.tasks = b.take<DenseTask>(dense_tasks_total);
       A.okey = b.take<uint64_t>(out_total);
       A.oval = b.take<uint64_t>(out_total);
@@ -345,6 +349,10 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
             op.tcode = b.take<int64_t>(n);
             op.kind = b.take<uint8_t>(n);
           }
+        }
+        if (pl.p.path == PATH_DENSE) {
+          pl.p.gidx = b.take<int32_t>(pl.p.gidx_n + 1);
+          pl.p.g.code32 = b.take<int32_t>(pl.p.g.n);
         }
       }
       // zeroed region: task counters, dense arrays, tables (one memset)
@@ -495,15 +503,18 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       ctx->launches += 1;
       mark(ctx, s, "gather");
       if (!dense_ids.empty()) {
+        int64_t max_ng = 0;
+        for (int p : dense_ids) max_ng = std::max(max_ng, plans[p].p.g.n);
+        ck(ctx, launch_build_gindex(A.lprods, A.dense_ids, (int)dense_ids.size(), max_ng, s),
+           "g index");
+        ctx->launches += 1;
         ck(ctx, launch_dense_plan(A.lprods, A.dense_ids, A.block_begin, (int)dense_ids.size(),
                                   nblocks_total, A.tasks, dense_tasks_total, A.counters, s),
            "dense plan");
         ctx->launches += 1;
         mark(ctx, s, "dense_plan");
-        const int64_t smem = max_S * 8;
-        const int per_sm = (int)std::max<int64_t>(1, std::min<int64_t>(4, (220 * 1024) / (smem + 2048)));
         ck(ctx, launch_dense_accum(A.lprods, A.tasks, A.counters, dense_tasks_total, A.counters + 1,
-                                   ctx->num_sms * per_sm, max_S, s),
+                                   ctx->num_sms, max_S, s),
            "dense accumulate");
         ctx->launches += 1;
         mark(ctx, s, "dense_accum");
@@ -564,9 +575,14 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       uint64_t* v = A.oval + r.prod.out_start;
       uint64_t* k2 = A.okey2 + r.prod.out_start;
       uint64_t* v2 = A.oval2 + r.prod.out_start;
-      ck(ctx, radix_sort_pairs(k, v, k2, v2, r.n, bits, A.scan, s, &in_tmp), "output sort");
-      ctx->launches += 3 * ((bits + 7) / 8);
-      if (in_tmp) { r.key = k2; r.val = v2; }
+      if (order_bins(r.prod.krange) <= ORDER_MAX_BINS) {
+        ck(ctx, order_by_bins(k, v, k2, v2, r.n, r.prod.krange, A.bins, s), "output order");
+        ctx->launches += 4;
+      } else {
+        ck(ctx, radix_sort_pairs(k, v, k2, v2, r.n, bits, A.scan, s, &in_tmp), "output sort");
+        ctx->launches += 3 * ((bits + 7) / 8);
+        if (in_tmp) { r.key = k2; r.val = v2; }
+      }
     }
     mark(ctx, s, "output_sort");
     return;
@@ -870,6 +886,7 @@ kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out*
   if (f->nvars < 1 || f->nvars > KR_MAXV || g->nvars != f->nvars || h->nvars != f->nvars) return KR_ERR_INVALID;
   if (f->type != g->type || (f->type != KR_I64 && f->type != KR_F64)) return KR_ERR_INVALID;
   if (f->nterms < 0 || g->nterms < 0 || h->capacity < 0) return KR_ERR_INVALID;
+  if (f->nterms >= INT32_MAX || g->nterms >= INT32_MAX) return KR_ERR_INVALID;
   if ((f->nterms > 0 && (!f->exps || !f->coef)) || (g->nterms > 0 && (!g->exps || !g->coef)))
     return KR_ERR_INVALID;
   if (h->capacity > 0 && !h->coef) return KR_ERR_INVALID;
@@ -907,6 +924,7 @@ kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g, kr_
   if (g->npoly != f->npoly || g->ntrig != f->ntrig || h->npoly != f->npoly || h->ntrig != f->ntrig)
     return KR_ERR_INVALID;
   if (f->nterms < 0 || g->nterms < 0 || h->capacity < 0) return KR_ERR_INVALID;
+  if (f->nterms >= INT32_MAX || g->nterms >= INT32_MAX) return KR_ERR_INVALID;
   auto bad = [](const kr_pseries* p) {
     return p->nterms > 0 && ((p->npoly > 0 && !p->exps) || !p->trig || !p->kind || !p->coef);
   };

@@ -19,7 +19,6 @@ namespace kr {
 constexpr int PLAN_SAMPLES = 32;   // sampled i per block for the work estimate
 constexpr int MAX_SPLIT = 64;      // tasks per block at most
 constexpr int ACC_THREADS = 512;
-constexpr int GROUP_R = 4;         // f terms per warp step (register reuse of g loads)
 
 // One warp per (dense product, block): i-range by binary search, sampled work
 // estimate, then 1..MAX_SPLIT tasks over equal i-slices.
@@ -48,13 +47,16 @@ __global__ void __launch_bounds__(256) k_dense_plan(const Prod* __restrict__ pro
   const int64_t nf = P.f.n, ng = P.g.n;
   const int64_t i_lo = lower_bound_i64(F, nf, B - G[ng - 1]);
   const int64_t i_hi = lower_bound_i64(F, nf, E - G[0]);
+  const int32_t* gx = P.gidx;
+  const int64_t gn = P.gidx_n;
+  const int gsh = P.gshift;
   if (i_lo >= i_hi) return;
   const int64_t span = i_hi - i_lo;
   int64_t cnt = 0;
   const int ns = span < PLAN_SAMPLES ? (int)span : PLAN_SAMPLES;
   if (lane < ns) {
     const int64_t i = i_lo + (span * lane) / ns;
-    cnt = lower_bound_i64(G, ng, E - F[i]) - lower_bound_i64(G, ng, B - F[i]);
+    cnt = g_lower_bound(G, ng, gx, gn, gsh, E - F[i]) - g_lower_bound(G, ng, gx, gn, gsh, B - F[i]);
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if (lane != 0) return;
@@ -90,6 +92,50 @@ cudaError_t launch_dense_plan(const Prod* dprods, const int32_t* ddense_prods,
   return cudaGetLastError();
 }
 
+// Bucket index over the sorted g codes of every dense product: bucket b
+// covers codes [b << gshift, (b + 1) << gshift); gidx[b] = lower_bound(b << gshift).
+// Each j writes the buckets whose lower bound it is; the buckets after the
+// last code get ng.
+__global__ void __launch_bounds__(256) k_build_gindex(const Prod* __restrict__ prods,
+                                                     const int32_t* __restrict__ dense_prods) {
+  const Prod& P = prods[dense_prods[blockIdx.y]];
+  const int64_t* G = P.g.code;
+  const int64_t ng = P.g.n;
+  const int sh = P.gshift;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= ng;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blo = j == 0 ? 0 : (G[j - 1] >> sh) + 1;
+    const int64_t bhi = j == ng ? P.gidx_n : min(G[j] >> sh, P.gidx_n);
+    for (int64_t b = blo; b <= bhi; ++b) P.gidx[b] = (int32_t)j;
+  }
+}
+
+cudaError_t launch_build_gindex(const Prod* dprods, const int32_t* ddense_prods, int ndense,
+                                int64_t max_ng, cudaStream_t s) {
+  if (ndense <= 0) return cudaSuccess;
+  int64_t gx = (max_ng + 1 + 255) / 256;
+  if (gx > 64) gx = 64;
+  k_build_gindex<<<dim3((unsigned)gx, ndense), 256, 0, s>>>(dprods, ddense_prods);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned long long to_bits(T v);
+template <>
+__device__ __forceinline__ unsigned long long to_bits<int64_t>(int64_t v) { return (unsigned long long)v; }
+template <>
+__device__ __forceinline__ unsigned long long to_bits<double>(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+template <typename T>
+__device__ __forceinline__ T from_bits(unsigned long long b);
+template <>
+__device__ __forceinline__ int64_t from_bits<int64_t>(unsigned long long b) { return (int64_t)b; }
+template <>
+__device__ __forceinline__ double from_bits<double>(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
 template <typename T>
 __device__ __forceinline__ void smem_add(T* p, T v);
 template <>
@@ -101,47 +147,123 @@ __device__ __forceinline__ void smem_add<double>(double* p, double v) {
   atomicAdd(p, v);
 }
 
+// Per-chunk window table of a task, in shared memory: for the chunk's f terms,
+// the slice offset of F_i (32-bit), the first j of its window, the exclusive
+// prefix of the window lengths (excl[ACC_THREADS] = total) and the coefficient.
+struct ChunkTable {
+  int32_t f32[ACC_THREADS];
+  int32_t lo[ACC_THREADS];
+  int32_t excl[ACC_THREADS + 1];
+  int32_t warp_sum[ACC_THREADS / 32];
+  unsigned long long coef[ACC_THREADS];
+};
+
 // Accumulate the pairs of one task into the shared slice acc[0, S).
-// Warps take groups of GROUP_R consecutive f terms; the lanes walk the union
-// of their j-ranges, loading each g term once and testing each of the R
-// output codes against the block.
-template <typename T>
-__device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& tk, T* acc) {
+// The task's f terms are taken ACC_THREADS at a time.  Each thread finds the
+// exact j-window of one f term in the sorted g codes; a block-wide prefix sum
+// flattens the windows into one range of pair indices, which is cut into
+// equal contiguous shares, one per warp, so that every warp reaches the
+// task's barrier with the same amount of work done.  A warp walks its share
+// 32 pairs at a time: consecutive lanes take consecutive g terms, and the
+// slice offset a = (F_i - B) + G_j lies in [0, S) by construction (32-bit
+// arithmetic is exact there; a guard keeps it in bounds regardless).
+template <typename T, bool C32>
+__device__ __forceinline__ T mul(T a, T b) {
+  if constexpr (C32) return (T)((int64_t)(int32_t)a * (int64_t)(int32_t)b);
+  else return a * b;
+}
+
+template <typename T, bool C32>
+__device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& tk, T* acc,
+                                                ChunkTable& ct) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = ACC_THREADS / 32;
+  constexpr unsigned FULL = 0xffffffffu;
   const int64_t S = P.S;
   const int64_t B = tk.block * S;
   const int64_t* __restrict__ F = P.f.code;
   const int64_t* __restrict__ G = P.g.code;
+  const int32_t* __restrict__ G32 = P.g.code32;
   const T* __restrict__ CF = (const T*)P.f.coef;
   const T* __restrict__ CG = (const T*)P.g.coef;
   const int64_t ng = P.g.n;
-  const int64_t ngroups = (tk.i1 - tk.i0 + GROUP_R - 1) / GROUP_R;
-  for (int64_t grp = warp; grp < ngroups; grp += NW) {
-    const int64_t ia = tk.i0 + grp * GROUP_R;
-    const int m = (int)min((int64_t)GROUP_R, tk.i1 - ia);
-    int64_t fr[GROUP_R];
-    T cr[GROUP_R];
-#pragma unroll
-    for (int r = 0; r < GROUP_R; ++r) {
-      const int64_t i = ia + (r < m ? r : 0);
-      fr[r] = F[i] - B;
-      cr[r] = CF[i];
-      if (r >= m) fr[r] = INT64_MIN / 4;   // never inside the block
+  for (int64_t ib = tk.i0; ib < tk.i1; ib += ACC_THREADS) {
+    const int64_t i = ib + threadIdx.x;
+    int32_t cnt = 0;
+    if (i < tk.i1) {
+      const int64_t fi = F[i] - B;
+      const int64_t l = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, -fi);
+      const int64_t h = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, S - fi);
+      ct.f32[threadIdx.x] = (int32_t)fi;
+      ct.lo[threadIdx.x] = (int32_t)l;
+      cnt = (int32_t)(h - l);
+      ct.coef[threadIdx.x] = to_bits<T>(CF[i]);
+    } else {
+      ct.f32[threadIdx.x] = 0;
+      ct.lo[threadIdx.x] = 0;
+      ct.coef[threadIdx.x] = 0ull;
     }
-    const int64_t flast = F[ia + m - 1] - B;
-    // union of the j-ranges: codes in [B, B + S) for the largest and smallest F
-    const int64_t jlo = lower_bound_i64(G, ng, -flast);
-    const int64_t jhi = lower_bound_i64(G, ng, S - fr[0]);
-    for (int64_t j = jlo + lane; j < jhi; j += 32) {
-      const int64_t gj = G[j];
-      const T cg = CG[j];
+    // block-wide exclusive scan of the window lengths
+    int32_t x = cnt;
 #pragma unroll
-      for (int r = 0; r < GROUP_R; ++r) {
-        const int64_t a = fr[r] + gj;
-        if ((uint64_t)a < (uint64_t)S) smem_add<T>(&acc[a], cr[r] * cg);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ct.warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t w = lane < NW ? ct.warp_sum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < NW) ct.warp_sum[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    const int32_t wbase = warp > 0 ? ct.warp_sum[warp - 1] : 0;
+    ct.excl[threadIdx.x] = wbase + x - cnt;
+    if (threadIdx.x == ACC_THREADS - 1) ct.excl[ACC_THREADS] = wbase + x;
+    __syncthreads();
+    const int32_t total = ct.excl[ACC_THREADS];
+    // this warp's share [pb, pe) of the flattened pairs
+    const int32_t pb = (int32_t)(((int64_t)total * warp) / NW);
+    const int32_t pe = (int32_t)(((int64_t)total * (warp + 1)) / NW);
+    if (pb < pe) {
+      // k = last f term whose window starts at or before pb
+      int lo_k = 0, hi_k = ACC_THREADS;
+      while (hi_k - lo_k > 1) {
+        const int mid = (lo_k + hi_k) >> 1;
+        if (ct.excl[mid] <= pb) lo_k = mid; else hi_k = mid;
+      }
+      // walk this warp's windows one by one; the lanes stride the j-range
+      for (int k = lo_k; k < ACC_THREADS; ++k) {
+        const int32_t e0 = ct.excl[k];
+        if (e0 >= pe) break;
+        const int32_t e1 = ct.excl[k + 1];
+        const int32_t s0 = max(pb, e0), s1 = min(pe, e1);
+        if (s0 >= s1) continue;
+        const int64_t jb = (int64_t)ct.lo[k] + (s0 - e0);
+        const int64_t je = (int64_t)ct.lo[k] + (s1 - e0);
+        const int32_t fk = ct.f32[k];
+        const T ck = from_bits<T>(ct.coef[k]);
+        int64_t j = jb + lane;
+        for (; j + 32 < je; j += 64) {
+          const int32_t a0 = fk + (G32 ? G32[j] : (int32_t)G[j]);
+          const int32_t a1 = fk + (G32 ? G32[j + 32] : (int32_t)G[j + 32]);
+          const T v0 = mul<T, C32>(ck, CG[j]);
+          const T v1 = mul<T, C32>(ck, CG[j + 32]);
+          if ((uint32_t)a0 < (uint32_t)S) smem_add<T>(&acc[a0], v0);
+          if ((uint32_t)a1 < (uint32_t)S) smem_add<T>(&acc[a1], v1);
+        }
+        if (j < je) {
+          const int32_t a0 = fk + (G32 ? G32[j] : (int32_t)G[j]);
+          if ((uint32_t)a0 < (uint32_t)S) smem_add<T>(&acc[a0], mul<T, C32>(ck, CG[j]));
+        }
       }
     }
+    __syncthreads();   // the table is rewritten by the next chunk
   }
 }
 
@@ -160,13 +282,14 @@ __device__ __forceinline__ void dense_flush(const Prod& P, const DenseTask& tk, 
   }
 }
 
-__global__ void __launch_bounds__(ACC_THREADS) k_dense_accum(const Prod* __restrict__ prods,
+__global__ void __launch_bounds__(ACC_THREADS, 3) k_dense_accum(const Prod* __restrict__ prods,
                                                              const DenseTask* __restrict__ tasks,
                                                              const int64_t* __restrict__ task_count,
                                                              int64_t task_cap,
                                                              unsigned long long* __restrict__ task_next) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int64_t s_task;
+  __shared__ ChunkTable ct;
   const int64_t ntasks = min(*task_count, task_cap);
   for (;;) {
     if (threadIdx.x == 0) s_task = (int64_t)atomicAdd(task_next, 1ull);
@@ -182,8 +305,9 @@ __global__ void __launch_bounds__(ACC_THREADS) k_dense_accum(const Prod* __restr
     int64_t* z = (int64_t*)smem_raw;
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x) z[s] = 0;
     __syncthreads();
-    if (P.f64) dense_task_body<double>(P, tk, (double*)smem_raw);
-    else dense_task_body<int64_t>(P, tk, (int64_t*)smem_raw);
+    if (P.f64) dense_task_body<double, false>(P, tk, (double*)smem_raw, ct);
+    else if (P.coef32) dense_task_body<int64_t, true>(P, tk, (int64_t*)smem_raw, ct);
+    else dense_task_body<int64_t, false>(P, tk, (int64_t*)smem_raw, ct);
     __syncthreads();
     if (P.f64) dense_flush<double>(P, tk, (double*)smem_raw);
     else dense_flush<int64_t>(P, tk, (int64_t*)smem_raw);
@@ -198,6 +322,13 @@ cudaError_t launch_dense_accum(const Prod* dprods, const DenseTask* dtasks,
   cudaError_t e = cudaFuncSetAttribute(k_dense_accum, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  // persistent grid: every CTA that fits on the GPU at once (grid = SMs on entry)
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense_accum, ACC_THREADS, smem) ==
+          cudaSuccess && per_sm > 0)
+    grid *= per_sm;
+  else
+    cudaGetLastError();
   k_dense_accum<<<grid, ACC_THREADS, smem, s>>>(dprods, dtasks, dtask_count, task_cap,
                                                (unsigned long long*)dtask_next);
   return cudaGetLastError();

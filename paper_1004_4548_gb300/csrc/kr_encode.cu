@@ -43,15 +43,29 @@ __global__ void __launch_bounds__(512) k_range_scan(const Prod* __restrict__ pro
     }
     if (lane == 0) { smin[k][warp] = lo; smax[k][warp] = hi; }
   }
+  // do all coefficients (int64) fit in int32?
+  __shared__ int fits_all;
+  if (threadIdx.x == 0) fits_all = 1;
   __syncthreads();
+  if (!P.f64) {
+    int fits = 1;
+    const int64_t* c = (const int64_t*)O.c;
+    for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x)
+      if (c[i] < INT32_MIN || c[i] > INT32_MAX) fits = 0;
+    if (!__all_sync(0xffffffffu, fits) && lane == 0) fits_all = 0;
+  } else if (threadIdx.x == 0) {
+    fits_all = 0;
+  }
+  __syncthreads();
+  int32_t* out = ranges + (int64_t)blockIdx.x * RANGE_STRIDE;
   if (threadIdx.x < nvar) {
     const int k = threadIdx.x;
     int32_t lo = INT32_MAX, hi = INT32_MIN;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { lo = min(lo, smin[k][w]); hi = max(hi, smax[k][w]); }
-    int32_t* out = ranges + (int64_t)blockIdx.x * 3 * MAXV;
     if (k < P.np) { out[k] = lo; out[MAXV + k] = hi; }
     else { out[2 * MAXV + (k - P.np)] = hi; }
   }
+  if (threadIdx.x == 0) out[3 * MAXV] = fits_all;
 }
 
 cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int32_t* dranges,
@@ -157,6 +171,7 @@ __global__ void __launch_bounds__(256) k_gather(Prod* __restrict__ prods, const 
     if (src < 0 || src >= O.n) { bad |= ST_DUP; src = 0; }
     if (P.nt == 0) {
       O.code[q] = (int64_t)key;
+      if (O.code32) O.code32[q] = (int32_t)key;
       if (P.f64) ((double*)O.coef)[q] = ((const double*)O.c)[src];
       else ((int64_t*)O.coef)[q] = ((const int64_t*)O.c)[src];
     } else {

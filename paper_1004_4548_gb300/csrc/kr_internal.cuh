@@ -9,6 +9,10 @@
 namespace kr {
 
 constexpr int MAXV = KR_MAXV;
+// per-operand range record written by k_range_scan: [0, MAXV) exponent minima,
+// [MAXV, 2 MAXV) maxima, [2 MAXV, 3 MAXV) max |t|, [3 MAXV] 1 when every
+// coefficient is an int64 within the int32 range
+constexpr int RANGE_STRIDE = 3 * MAXV + 4;
 constexpr int PATH_DENSE = 1;
 constexpr int PATH_HASH = 2;
 
@@ -40,6 +44,7 @@ struct Operand {
   uint64_t* skey2;      // bitmap / radix paths: sorted keys
   uint64_t* sidx2;      // bitmap / radix paths: source index of each sorted key
   int64_t* code;        // sorted: polynomial code (poly) or poly part (Poisson)
+  int32_t* code32;      // dense path, g only: the sorted codes as int32 (W <= 2^31)
   int64_t* tcode;       // sorted: signed trig code (Poisson)
   uint8_t* kind;        // sorted kinds (Poisson)
   void* coef;           // sorted coefficients (Poisson f: pre-multiplied by 1/2)
@@ -54,6 +59,7 @@ struct Prod {
   int32_t np, nt;       // polynomial variables, trig variables (0: polynomial product)
   int32_t f64;          // coefficients are double
   int32_t path;         // PATH_DENSE or PATH_HASH
+  int32_t coef32;       // int64 coefficients that all fit in int32 (32x32->64 multiply)
   int64_t c[MAXV];      // coding vector; poly part [0, np), trig part [np, np + nt)
   int32_t w[MAXV];      // output widths
   int32_t omin[MAXV];   // output box minimum (poly), -R_k (trig)
@@ -65,6 +71,9 @@ struct Prod {
   int64_t nblocks;
   int64_t work_target;  // pairs per task
   void* dense;          // [krange] accumulators
+  int32_t* gidx;        // gidx[b] = first j with g.code[j] >= b << gshift, b in [0, gidx_n]
+  int64_t gidx_n;       // buckets (the last entry gidx[gidx_n] = g.n)
+  int32_t gshift;
   // hash path
   uint64_t* table;      // [slots][2] = (key + 1, value); key 0 = empty
   int64_t slots;        // power of two
@@ -106,6 +115,21 @@ __device__ __forceinline__ int64_t lower_bound_i64(const int64_t* a, int64_t n, 
   return lo;
 }
 
+// lower_bound over the sorted g codes through the coarse bucket index: the
+// answer for x lies in [gidx[x >> gshift], gidx[(x >> gshift) + 1]].
+__device__ __forceinline__ int64_t g_lower_bound(const int64_t* G, int64_t ng, const int32_t* gidx,
+                                                 int64_t gidx_n, int gshift, int64_t x) {
+  if (x <= 0) return 0;
+  const int64_t b = x >> gshift;
+  if (b >= gidx_n) return ng;
+  int64_t lo = gidx[b], hi = gidx[b + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (G[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 // 64-bit mixing function (the finaliser of MurmurHash3, Appleby) for table slots
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   k ^= k >> 33;
@@ -135,6 +159,8 @@ cudaError_t launch_dense_plan(const Prod* dprods, const int32_t* ddense_prods,
                               const int64_t* dblock_begin, int ndense, int64_t nblocks_total,
                               DenseTask* dtasks, int64_t task_cap, int64_t* dtask_count,
                               cudaStream_t s);
+cudaError_t launch_build_gindex(const Prod* dprods, const int32_t* ddense_prods, int ndense,
+                                int64_t max_ng, cudaStream_t s);
 cudaError_t launch_dense_accum(const Prod* dprods, const DenseTask* dtasks,
                                const int64_t* dtask_count, int64_t task_cap, int64_t* dtask_next,
                                int grid, int64_t max_S, cudaStream_t s);
@@ -154,6 +180,14 @@ int64_t radix_scan_entries(int64_t n);
 cudaError_t radix_sort_pairs(uint64_t* key, uint64_t* val, uint64_t* key_tmp, uint64_t* val_tmp,
                              int64_t n, int bits, int64_t* dscan, cudaStream_t s,
                              bool* result_in_tmp);
+
+// Orders (key, val)[0, n) by key (keys distinct, < krange) through bins of
+// codes and shared-memory segment sorts; key2/val2 hold n terms of scratch,
+// bins 2 * (order_bins(krange) + 1) int64.  Result in key/val.
+constexpr int64_t ORDER_MAX_BINS = int64_t(1) << 24;
+int64_t order_bins(int64_t krange);
+cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
+                          int64_t krange, int64_t* bins, cudaStream_t s);
 
 cudaError_t launch_decode_poly(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
                                int32_t* exps, int64_t ld, int64_t* codes, cudaStream_t s);

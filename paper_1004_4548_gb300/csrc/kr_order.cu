@@ -1,0 +1,137 @@
+// Ordering of the hash path's output by code.  The paper's output of the
+// highly sparse algorithm is the hash table itself (Sec. 3.2); this library
+// returns terms sorted by code like the dense path does, so the table's terms
+// are ordered after compaction:
+//   1. count the terms in bins of C consecutive codes (keys are distinct, so no
+//      bin holds more than C terms),
+//   2. exclusive scan of the bin counts,
+//   3. scatter every term to its bin's range,
+//   4. sort segments of whole bins, at most 2C terms each, in shared memory.
+// Steps 1-3 are one counting-sort pass on the high part of the code; step 4
+// orders within bins.  Two reads and two writes of the terms in total.
+#include "kr_internal.cuh"
+
+namespace kr {
+
+constexpr int ORD_C = 4096;              // codes per bin
+constexpr int ORD_SEG = 2 * ORD_C;       // max terms per sorted segment
+constexpr int ORD_THREADS = 1024;
+
+__global__ void __launch_bounds__(256) k_bin_count(const uint64_t* __restrict__ key, int64_t n,
+                                                   int64_t nb, unsigned long long* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t b = key[i] / ORD_C;
+    if (b < (uint64_t)nb) atomicAdd(&cnt[b], 1ull);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bin_scatter(const uint64_t* __restrict__ key,
+                                                     const uint64_t* __restrict__ val, int64_t n,
+                                                     int64_t nb, const int64_t* __restrict__ off,
+                                                     unsigned long long* __restrict__ cur,
+                                                     uint64_t* __restrict__ okey,
+                                                     uint64_t* __restrict__ oval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    const int64_t b = (int64_t)(k / ORD_C);
+    if (b >= nb) continue;
+    const int64_t pos = off[b] + (int64_t)atomicAdd(&cur[b], 1ull);
+    if (pos < n) {
+      okey[pos] = k;
+      oval[pos] = val[i];
+    }
+  }
+}
+
+// One CTA per segment k: the bins whose exclusive offset lies in
+// [k ORD_C, (k + 1) ORD_C); their terms form the output range
+// [off[b_lo], off[b_hi]) of at most ORD_SEG terms.
+__global__ void __launch_bounds__(ORD_THREADS) k_seg_sort(const uint64_t* __restrict__ key,
+                                                          const uint64_t* __restrict__ val,
+                                                          const int64_t* __restrict__ off, int64_t nbins,
+                                                          uint64_t* __restrict__ okey,
+                                                          uint64_t* __restrict__ oval) {
+  extern __shared__ __align__(16) unsigned char ord_smem[];
+  uint64_t* sk = (uint64_t*)ord_smem;
+  uint16_t* si = (uint16_t*)(ord_smem + sizeof(uint64_t) * ORD_SEG);
+  const int64_t seg = blockIdx.x;
+  // lower bounds over off[0, nbins] (off[nbins] = total)
+  auto lb = [&](int64_t x) {
+    int64_t lo = 0, hi = nbins + 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (off[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo > nbins ? nbins : lo;
+  };
+  const int64_t b_lo = lb(seg * ORD_C), b_hi = lb((seg + 1) * ORD_C);
+  const int64_t start = off[b_lo];
+  int n = (int)(off[b_hi] - start);
+  if (n > ORD_SEG) n = ORD_SEG;   // cannot happen for distinct keys; keeps smem in bounds
+  if (n <= 0) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sk[i] = key[start + i];
+    si[i] = (uint16_t)i;
+  }
+  __syncthreads();
+  int N = 1;
+  while (N < n) N <<= 1;
+  const int pairs = N >> 1;
+  for (int size = 2; size <= N; size <<= 1) {
+    const int half = size >> 1;
+    for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
+      const int blk = p / half, o = p - blk * half;
+      const int i = blk * size + o, j = blk * size + size - 1 - o;
+      if (j < n && sk[i] > sk[j]) {
+        const uint64_t tk = sk[i]; sk[i] = sk[j]; sk[j] = tk;
+        const uint16_t ti = si[i]; si[i] = si[j]; si[j] = ti;
+      }
+    }
+    __syncthreads();
+    for (int stride = half >> 1; stride > 0; stride >>= 1) {
+      for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
+        const int i = (p / stride) * 2 * stride + (p % stride), j = i + stride;
+        if (j < n && sk[i] > sk[j]) {
+          const uint64_t tk = sk[i]; sk[i] = sk[j]; sk[j] = tk;
+          const uint16_t ti = si[i]; si[i] = si[j]; si[j] = ti;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    okey[start + i] = sk[i];
+    oval[start + i] = val[start + si[i]];
+  }
+}
+
+int64_t order_bins(int64_t krange) { return (krange + ORD_C - 1) / ORD_C; }
+
+// Sorts (key, val)[0, n) by key, keys distinct and < krange.  Uses key2/val2
+// as the binned copy and writes the sorted terms back to key/val.  bins:
+// 2 * (order_bins(krange) + 1) int64 of scratch.
+cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
+                          int64_t krange, int64_t* bins, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  const int64_t nb = order_bins(krange);
+  int64_t* off = bins;
+  unsigned long long* cur = (unsigned long long*)(bins + nb + 1);
+  cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int64_t) * 2 * (nb + 1), s);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (n + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_bin_count<<<(unsigned)grid, 256, 0, s>>>(key, n, nb, (unsigned long long*)off);
+  e = launch_scan_exclusive(off, nb, off + nb, s);
+  if (e != cudaSuccess) return e;
+  k_bin_scatter<<<(unsigned)grid, 256, 0, s>>>(key, val, n, nb, off, cur, key2, val2);
+  const int64_t nseg = (n + ORD_C - 1) / ORD_C;
+  const int smem = (int)((sizeof(uint64_t) + sizeof(uint16_t)) * ORD_SEG);
+  e = cudaFuncSetAttribute(k_seg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_seg_sort<<<(unsigned)nseg, ORD_THREADS, smem, s>>>(key2, val2, off, nb, key, val);
+  return cudaGetLastError();
+}
+
+}  // namespace kr

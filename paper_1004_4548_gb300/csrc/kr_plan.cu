@@ -104,6 +104,7 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
   }
   const int64_t nf = P.f.n, ng = P.g.n;
   const double pairs = (double)nf * (double)ng;
+  P.coef32 = (!job.f64 && P.nt == 0 && rf[3 * MAXV] == 1 && rg[3 * MAXV] == 1) ? 1 : 0;
   // ---- path (Sec. 3.2: the density of the product decides)
   if (job.poisson) {
     P.path = PATH_HASH;
@@ -141,9 +142,17 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     if (S > kr32) S = kr32;
     P.S = S;
     P.nblocks = ceil_div(P.krange, S);
-    const double tgt = pairs / (double)(num_sms * 4);
+    // ~6 tasks per resident CTA so the dynamic task queue evens out the
+    // uneven (diamond-shaped) work per output block
+    const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, (227 * 1024) / (S * 8 + 11264)));
+    const double tgt = pairs / (double)(num_sms * per_sm * 6);
     P.work_target = (int64_t)std::max(tgt, (double)(2 * S));
     pl.dense_task_cap = P.nblocks * 64;
+    // bucket index over g's codes: at most 65536 buckets
+    int sh = 0;
+    while (((P.g.key_range >> sh) + 1) > 65535) ++sh;
+    P.gshift = sh;
+    P.gidx_n = (P.g.key_range >> sh) + 1;
     pl.accum_bytes = P.krange * 8;
     P.chunk = COMPACT_CHUNK;
     P.nchunks = ceil_div(P.krange, P.chunk);

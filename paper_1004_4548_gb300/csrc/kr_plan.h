@@ -20,7 +20,7 @@ constexpr double DENSE_KAPPA = 4.0;
 constexpr int64_t BITMAP_MAX_BITS = 1600000;   // on-chip bitmap sort (<= 200 KB)
 constexpr int64_t BITONIC_MAX_N = 16384;       // shared-memory bitonic sort (128 KB)
 constexpr int64_t DEFAULT_S = 8192;            // dense block: 64 KB of shared memory
-constexpr int64_t MAX_S = 28672;               // 224 KB
+constexpr int64_t MAX_S = 27648;               // 216 KB slice + the 10 KB window table
 constexpr int64_t COMPACT_CHUNK = 8192;
 constexpr double DEFAULT_LOAD = 0.5;
 constexpr int DEFAULT_PROBES = 512;

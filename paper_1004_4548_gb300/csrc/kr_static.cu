@@ -69,10 +69,15 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
   const int64_t S = std::min<int64_t>(STATIC_BLOCK, (W + 31) / 32 * 32);
   const int64_t nblocks = (W + S - 1) / S;
   const int64_t task_cap = nblocks * dense_max_split();
-  // layout: [Prod][ids, block_begin][counters][tasks]
+  // bucket index over g's codes (codes < W): at most 65536 buckets
+  int gsh = 0;
+  while (((W >> gsh) + 1) > 65535) ++gsh;
+  const int64_t gidx_n = (W >> gsh) + 1;
+  // layout: [Prod][ids, block_begin][counters][g index][tasks]
   const size_t off_ids = align256(sizeof(Prod));
   const size_t off_cnt = off_ids + 256;
-  const size_t off_tasks = off_cnt + 256;
+  const size_t off_gidx = off_cnt + 256;
+  const size_t off_tasks = off_gidx + align256((size_t)(gidx_n + 1) * sizeof(int32_t));
   const size_t need = off_tasks + (size_t)task_cap * sizeof(DenseTask);
   if (need > STATIC_SCRATCH_BYTES) return KR_ERR_TOO_LARGE;
 
@@ -96,6 +101,9 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
   const double pairs = (double)nf * (double)ng;
   P.work_target = (int64_t)std::max(pairs / (double)(sms * 4), (double)(2 * S));
   P.dense = out;
+  P.gidx = (int32_t*)(base + off_gidx);
+  P.gidx_n = gidx_n;
+  P.gshift = gsh;
   struct Small {
     int32_t ids[2];
     int64_t block_begin[2];
@@ -117,12 +125,12 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
     cudaGetLastError();
     return KR_ERR_CUDA;
   }
-  if (launch_dense_plan(dprod, dids, dbb, 1, nblocks, dtasks, task_cap, dcnt, s) != cudaSuccess) {
+  if (launch_build_gindex(dprod, dids, 1, ng, s) != cudaSuccess ||
+      launch_dense_plan(dprod, dids, dbb, 1, nblocks, dtasks, task_cap, dcnt, s) != cudaSuccess) {
     cudaGetLastError();
     return KR_ERR_CUDA;
   }
-  const int per_sm = (int)std::max<int64_t>(1, std::min<int64_t>(4, (220 * 1024) / (S * 8 + 2048)));
-  if (launch_dense_accum(dprod, dtasks, dcnt, task_cap, dcnt + 1, sms * per_sm, S, s) != cudaSuccess) {
+  if (launch_dense_accum(dprod, dtasks, dcnt, task_cap, dcnt + 1, sms, S, s) != cudaSuccess) {
     cudaGetLastError();
     return KR_ERR_CUDA;
   }

@@ -44,14 +44,36 @@ def pseries_keys(exps, trig, kind):
 
 
 def assert_pseries_close(g, r, rel=1e-12, what=""):
-    """Poisson product: per key |gpu - oracle| <= rel * sum|contributions| (oracle kept zeros)."""
+    """Poisson product: per key |gpu - oracle| <= rel * sum|contributions| (oracle kept zeros).
+
+    Also checks the GPU output is in canonical order (kind, then trig multipliers
+    from the highest index, then exponents from the highest index) without repeats.
+    """
     ge, gt, gk, gc = (to_np(x) for x in g[:4])
-    gkeys = pseries_keys(ge, gt, gk)
-    okeys = pseries_keys(r.exps, r.trig, r.kind)
-    # canonical order check on the GPU side: sorted by (kind, trig desc-index, poly desc-index)
-    order = np.lexsort(tuple(gkeys[:, c] for c in _pseries_sort_cols(ge.shape[0], gt.shape[0])))
-    assert np.array_equal(order, np.arange(order.shape[0])), f"{what}: GPU output not in canonical order"
-    _assert_keyed_close(gkeys, gc, okeys, r.coef, r.mass, rel, what)
+    np_, nt = ge.shape[0], gt.shape[0]
+    cols = lambda e, t, k: np.concatenate([e, t, k.astype(np.int32)[None, :]], axis=0).T
+    gk_rows = cols(ge, gt, gk)   # least significant column first
+    ok_rows = cols(r.exps, r.trig, r.kind)
+    packed = _pack_rows(np.concatenate([ok_rows, gk_rows]))
+    if packed is None:
+        gkeys = pseries_keys(ge, gt, gk)
+        okeys = pseries_keys(r.exps, r.trig, r.kind)
+        _assert_keyed_close(gkeys, gc, okeys, r.coef, r.mass, rel, what)
+        return
+    po, pg = packed[: ok_rows.shape[0]], packed[ok_rows.shape[0]:]
+    assert (np.diff(pg) > 0).all(), f"{what}: GPU output not strictly in canonical order"
+    assert (np.diff(po) > 0).all(), f"{what}: oracle output not in canonical order"
+    pos = np.searchsorted(po, pg)
+    ok = (pos < po.shape[0])
+    ok[ok] = po[pos[ok]] == pg[ok]
+    assert ok.all(), f"{what}: {int((~ok).sum())} GPU keys the oracle never produced"
+    ov = r.coef.copy()
+    gv = np.zeros_like(ov)
+    gv[pos] = gc
+    err = np.abs(gv - ov)
+    bad = err > rel * r.mass
+    assert not bad.any(), (f"{what}: {int(bad.sum())} keys beyond {rel} x mass; worst ratio "
+                           f"{(err / np.maximum(r.mass, 1e-300)).max():.3e}")
 
 
 def _pseries_sort_cols(np_, nt):
@@ -60,10 +82,28 @@ def _pseries_sort_cols(np_, nt):
     return cols
 
 
+def _pack_rows(rows: np.ndarray):
+    """One int64 per row (mixed radix over the columns' ranges), or None if it overflows."""
+    if rows.shape[0] == 0:
+        return np.zeros(0, np.int64)
+    lo = rows.min(axis=0).astype(np.int64)
+    span = rows.max(axis=0).astype(np.int64) - lo + 1
+    if float(np.prod(span.astype(np.float64))) >= 2.0 ** 62:
+        return None
+    out = np.zeros(rows.shape[0], np.int64)
+    for c in range(rows.shape[1] - 1, -1, -1):
+        out = out * span[c] + (rows[:, c].astype(np.int64) - lo[c])
+    return out
+
+
 def _assert_keyed_close(gkeys, gcoef, okeys, ocoef, omass, rel, what):
     # join on the key rows
     allk = np.concatenate([okeys, gkeys])
-    _, inv = np.unique(allk, axis=0, return_inverse=True)
+    packed = _pack_rows(allk)
+    if packed is not None:
+        _, inv = np.unique(packed, return_inverse=True)
+    else:
+        _, inv = np.unique(allk, axis=0, return_inverse=True)
     inv = inv.ravel()
     oid, gid = inv[: okeys.shape[0]], inv[okeys.shape[0]:]
     m = inv.max() + 1 if inv.size else 0
