@@ -209,6 +209,39 @@ kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out*
 kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g,
                       kr_pseries_out* h, const kr_opts* opts, kr_stream stream);
 
+/* One product of a batch: kind 0 multiplies the polynomials f and g, kind 1
+ * the Poisson series pf and pg.  opts as for poly_mul (zero = defaults). */
+typedef struct {
+  int32_t kind;
+  kr_poly f, g;
+  kr_pseries pf, pg;
+  kr_opts opts;
+} kr_job;
+
+/* Result of one product of a batch.  The arrays are device memory owned by
+ * the context, valid until the next kron_mul_batch on it or its destruction;
+ * each is laid out [variables][nterms] (row stride nterms), sorted by code. */
+typedef struct {
+  kr_status status;
+  int32_t path;          /* KR_PATH_DENSE or KR_PATH_HASH as run */
+  int64_t nterms;
+  const int32_t* exps;   /* [nvars or npoly][nterms] */
+  const int32_t* trig;   /* [ntrig][nterms] (Poisson) */
+  const uint8_t* kind;   /* [nterms] (Poisson) */
+  const void* coef;      /* [nterms] */
+} kr_result;
+
+/* Many products of uneven sizes in one pipeline: one launch of each stage
+ * (range scan, encode, sorts, gather, accumulation of every dense and hash
+ * product by one persistent grid each, compaction, decode) for all products
+ * of a wave.  Products are grouped into waves of at most wave_pairs
+ * term-products (0 = 2^33) so that scratch stays bounded; a wave that runs
+ * out of device memory is split in two.  Every product gets its own status
+ * in res[i]; the call returns KR_OK unless the whole call failed (CUDA error,
+ * out of memory for a single product).  Synchronises the stream. */
+kr_status kron_mul_batch(kr_ctx* ctx, const kr_job* jobs, int32_t njobs, kr_result* res,
+                         int64_t wave_pairs, kr_stream stream);
+
 /* Copy the product kept by the last poly_mul / poisson_mul of this context
  * (after KR_ERR_CAPACITY) into h.  KR_ERR_INVALID if there is none. */
 kr_status kron_fetch_poly(kr_ctx* ctx, kr_poly_out* h, kr_stream stream);

@@ -50,6 +50,16 @@ class kr_opts(ctypes.Structure):
                 ("table_slots", _i64)]
 
 
+class kr_job(ctypes.Structure):
+    _fields_ = [("kind", _i32), ("f", kr_poly), ("g", kr_poly), ("pf", kr_pseries), ("pg", kr_pseries),
+                ("opts", kr_opts)]
+
+
+class kr_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("path", _i32), ("nterms", _i64), ("exps", _vp), ("trig", _vp),
+                ("kind", _vp), ("coef", _vp)]
+
+
 # name -> (restype, argtypes); every symbol include/kron.h declares
 SIGNATURES = {
     "kr_ctx_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp)]),
@@ -73,6 +83,7 @@ SIGNATURES = {
     "poisson_mul": (ctypes.c_int, [_vp, ctypes.POINTER(kr_pseries), ctypes.POINTER(kr_pseries),
                                    ctypes.POINTER(kr_pseries_out), ctypes.POINTER(kr_opts), _vp]),
     "kron_fetch_poly": (ctypes.c_int, [_vp, ctypes.POINTER(kr_poly_out), _vp]),
+    "kron_mul_batch": (ctypes.c_int, [_vp, ctypes.POINTER(kr_job), _i32, ctypes.POINTER(kr_result), _i64, _vp]),
     "kron_fetch_pseries": (ctypes.c_int, [_vp, ctypes.POINTER(kr_pseries_out), _vp]),
 }
 
@@ -373,4 +384,81 @@ def kron_dense_product_static(fcode, fcoef, gcode, gcoef, W: int, out=None, stre
                                      KR_F64 if is_f64 else KR_I64, int(W), out.data_ptr(),
                                      _stream_ptr(stream))
     _check(L, None, st, "kron_dense_product_static")
+    return out
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+def _view(ptr, shape, typestr, device):
+    torch = _torch()
+    if not ptr or any(d == 0 for d in shape):
+        dt = {"<i4": torch.int32, "<i8": torch.int64, "<f8": torch.float64, "|u1": torch.uint8}[typestr]
+        return torch.empty(shape, dtype=dt, device=f"cuda:{device}")
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device=f"cuda:{device}")
+
+
+def kron_mul_batch(pairs, ctx: Context | None = None, stream=None, wave_pairs: int = 0, opts=None):
+    """Multiply many (f, g) pairs in one batched pipeline.
+
+    pairs: list of (f, g), each a Poly-like (.exps, .coef) or PSeries-like
+    (.exps, .trig, .kind, .coef) object with numpy or torch arrays.
+    opts: None, one dict of kr_opts fields for all, or a list of dicts.
+    Returns a list of dicts {status, path, exps, trig, kind, coef}: torch views
+    of library-owned device memory, valid until the next batch on the context.
+    """
+    ctx = ctx or context()
+    n = len(pairs)
+    jobs = (kr_job * max(1, n))()
+    res = (kr_result * max(1, n))()
+    keep = []
+    for i, (f, g) in enumerate(pairs):
+        o = opts[i] if isinstance(opts, (list, tuple)) else (opts or {})
+        jobs[i].opts = _opts(**o)
+        if hasattr(f, "trig"):
+            def desc(p):
+                pe, a = _ptr_len(p.exps, np.int32)
+                pt, b = _ptr_len(p.trig, np.int32)
+                pk, c = _ptr_len(p.kind, np.uint8)
+                pc, d = _ptr_len(p.coef, np.float64)
+                keep.extend([a, b, c, d])
+                return kr_pseries(int(p.exps.shape[0]), int(p.trig.shape[0]), int(p.coef.shape[0]),
+                                  pe, pt, pk, pc)
+            jobs[i].kind = 1
+            jobs[i].pf = desc(f)
+            jobs[i].pg = desc(g)
+        else:
+            is_f64 = str(getattr(f.coef, "dtype", "")).endswith("float64")
+            cdt = np.float64 if is_f64 else np.int64
+            def desc(p):
+                pe, a = _ptr_len(p.exps, np.int32)
+                pc, b = _ptr_len(p.coef, cdt)
+                keep.extend([a, b])
+                return kr_poly(int(p.exps.shape[0]), int(p.coef.shape[0]), pe, pc, KR_F64 if is_f64 else KR_I64)
+            jobs[i].kind = 0
+            jobs[i].f = desc(f)
+            jobs[i].g = desc(g)
+    st = ctx.L.kron_mul_batch(ctx.h, jobs, n, res, int(wave_pairs), _stream_ptr(stream))
+    _check(ctx.L, ctx.h, st, "kron_mul_batch")
+    out = []
+    for i, (f, g) in enumerate(pairs):
+        r = res[i]
+        m = int(r.nterms)
+        d = {"status": int(r.status), "path": int(r.path), "nterms": m}
+        if jobs[i].kind == 1:
+            npl, nt = jobs[i].pf.npoly, jobs[i].pf.ntrig
+            d["exps"] = _view(r.exps, (npl, m), "<i4", ctx.device)
+            d["trig"] = _view(r.trig, (nt, m), "<i4", ctx.device)
+            d["kind"] = _view(r.kind, (m,), "|u1", ctx.device)
+            d["coef"] = _view(r.coef, (m,), "<f8", ctx.device)
+        else:
+            nv = jobs[i].f.nvars
+            d["exps"] = _view(r.exps, (nv, m), "<i4", ctx.device)
+            d["coef"] = _view(r.coef, (m,), "<f8" if jobs[i].f.type == KR_F64 else "<i8", ctx.device)
+        out.append(d)
     return out

@@ -26,6 +26,10 @@ struct kr_ctx {
   size_t in_cap = 0;
   void* work = nullptr;
   size_t work_cap = 0;
+  void* acc = nullptr;       // accumulators and outputs (phase B2)
+  size_t acc_cap = 0;
+  std::vector<Plan> plans;   // plans of the last pipeline run
+  std::vector<void*> batch_blocks;   // result memory of the last kron_mul_batch
   void* pinned = nullptr;
   size_t pinned_cap = 0;
   // product kept after the last multiplication (for kron_fetch_*)
@@ -181,69 +185,52 @@ const T* stage(kr_ctx* ctx, Bump& b, const T* src, int64_t count, cudaStream_t s
 }
 
 // The pipeline over a set of products.  All products must have nf, ng >= 1.
+//   A   staged inputs, range scan                       -> sync, host plan
+//   B1  (work arena) encode, sort, gather, g index, HLL -> sync, table sizes
+//   B2  (accumulator arena) zero, dense plan + accumulate, hash inserts,
+//       compaction                                      -> sync
+// A product whose table fills up is retried from B2 with a larger table.
 void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
                   std::vector<ProdResult>& res) {
   const int nprod = (int)ins.size();
   res.assign(nprod, ProdResult());
+  const int nops = 2 * nprod;
   std::vector<Job> jobs(nprod);
-  std::vector<int> regrows(nprod, 0);
-  std::vector<int64_t> hints(nprod, 0);
-  for (int attempt = 0;; ++attempt) {
-    // ---------------- phase A: staged inputs and metadata
-    const int nops = 2 * nprod;
-    size_t in_need = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-      Bump b(pass ? ctx->in_arena : nullptr);
-      for (int p = 0; p < nprod; ++p) {
-        const JobIn& in = ins[p];
-        Job& J = jobs[p];
-        J = Job();
-        J.poisson = in.poisson;
-        J.f64 = in.f64;
-        J.np = in.np;
-        J.nt = in.nt;
-        J.opts = in.opts;
-        J.slots_hint = hints[p];
-        const size_t csz = 8;
-        J.f.n = in.nf;
-        J.g.n = in.ng;
-        J.f.e = stage(ctx, b, in.fe, (int64_t)in.np * in.nf, s);
-        J.g.e = stage(ctx, b, in.ge, (int64_t)in.np * in.ng, s);
-        J.f.c = (const void*)stage(ctx, b, (const uint64_t*)in.fc, in.nf * (int64_t)(csz / 8), s);
-        J.g.c = (const void*)stage(ctx, b, (const uint64_t*)in.gc, in.ng * (int64_t)(csz / 8), s);
-        if (in.poisson) {
-          J.f.t = stage(ctx, b, in.ft, (int64_t)in.nt * in.nf, s);
-          J.g.t = stage(ctx, b, in.gt, (int64_t)in.nt * in.ng, s);
-          J.f.k = stage(ctx, b, in.fk, in.nf, s);
-          J.g.k = stage(ctx, b, in.gk, in.ng, s);
-        }
-      }
-      if (!pass) {
-        in_need = b.off;
-        ensure(ctx, &ctx->in_arena, &ctx->in_cap, in_need + 1, s);
+  // ---------------- phase A: staged inputs, metadata, range scan
+  Prod* dprods = nullptr;
+  OpRef* dops = nullptr;
+  int32_t* dranges = nullptr;
+  for (int pass = 0; pass < 2; ++pass) {
+    Bump b(pass ? ctx->in_arena : nullptr);
+    for (int p = 0; p < nprod; ++p) {
+      const JobIn& in = ins[p];
+      Job& J = jobs[p];
+      J = Job();
+      J.poisson = in.poisson;
+      J.f64 = in.f64;
+      J.np = in.np;
+      J.nt = in.nt;
+      J.opts = in.opts;
+      J.f.n = in.nf;
+      J.g.n = in.ng;
+      J.f.e = stage(ctx, b, in.fe, (int64_t)in.np * in.nf, s);
+      J.g.e = stage(ctx, b, in.ge, (int64_t)in.np * in.ng, s);
+      J.f.c = (const void*)stage(ctx, b, (const uint64_t*)in.fc, in.nf, s);
+      J.g.c = (const void*)stage(ctx, b, (const uint64_t*)in.gc, in.ng, s);
+      if (in.poisson) {
+        J.f.t = stage(ctx, b, in.ft, (int64_t)in.nt * in.nf, s);
+        J.g.t = stage(ctx, b, in.gt, (int64_t)in.nt * in.ng, s);
+        J.f.k = stage(ctx, b, in.fk, in.nf, s);
+        J.g.k = stage(ctx, b, in.gk, in.ng, s);
       }
     }
-    size_t meta_need;
-    Prod* dprods;
-    OpRef* dops;
-    int32_t* dranges;
-    {
-      Bump m(nullptr);
-      m.take<Prod>(nprod);
-      m.take<OpRef>(nops);
-      m.take<int32_t>((int64_t)nops * RANGE_STRIDE);
-      meta_need = m.off;
-    }
-    ensure_pinned(ctx, meta_need + 4096, s);
-    // The metadata sits at the start of the work arena.  The work arena may be
-    // regrown after planning; the metadata is then re-uploaded.
-    ensure(ctx, &ctx->work, &ctx->work_cap, meta_need, s);
-    {
-      Bump m(ctx->work);
-      dprods = m.take<Prod>(nprod);
-      dops = m.take<OpRef>(nops);
-      dranges = m.take<int32_t>((int64_t)nops * RANGE_STRIDE);
-    }
+    dprods = b.take<Prod>(nprod);
+    dops = b.take<OpRef>(nops);
+    dranges = b.take<int32_t>((int64_t)nops * RANGE_STRIDE);
+    if (!pass) ensure(ctx, &ctx->in_arena, &ctx->in_cap, b.off + 1, s);
+  }
+  ensure_pinned(ctx, (sizeof(Prod) + 2 * sizeof(OpRef) + 2 * RANGE_STRIDE * 4) * (size_t)nprod + 65536, s);
+  {
     Bump hp(ctx->pinned);
     Prod* hprods = hp.take<Prod>(nprod);
     OpRef* hops = hp.take<OpRef>(nops);
@@ -265,291 +252,308 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     ck(ctx, launch_range_scan(dprods, dops, nops, dranges, s), "range scan");
     ctx->launches += 1;
     mark(ctx, s, "range_scan");
-    ck(ctx, cudaMemcpyAsync(hranges, dranges, sizeof(int32_t) * nops * RANGE_STRIDE, cudaMemcpyDeviceToHost, s),
-       "download ranges");
+    ck(ctx, cudaMemcpyAsync(hranges, dranges, sizeof(int32_t) * nops * RANGE_STRIDE,
+                            cudaMemcpyDeviceToHost, s), "download ranges");
     ck(ctx, cudaStreamSynchronize(s), "sync ranges");
     collect_stages(ctx);
     // ---------------- host planning
-    std::vector<Plan> plans(nprod);
+    std::vector<Plan> plans_tmp(nprod);
+    ctx->plans.assign(nprod, Plan());
     for (int p = 0; p < nprod; ++p) {
       plan_product(jobs[p], hranges + (2 * p) * RANGE_STRIDE, hranges + (2 * p + 1) * RANGE_STRIDE,
-                   ctx->num_sms, &plans[p]);
-      res[p].st = plans[p].st;
+                   ctx->num_sms, &ctx->plans[p]);
+      res[p].st = ctx->plans[p].st;
     }
-    // ---------------- phase B: work arena layout (two passes: measure, assign)
-    int64_t dense_tasks_total = 0, nblocks_total = 0, hash_tasks_total = 0, nchunks_total = 0;
-    int64_t out_total = 0, scan_entries = 0, bins_total = 0;
-    int64_t max_S = 0;
-    std::vector<int> dense_ids, hash_ids, live_ids;
-    for (int p = 0; p < nprod; ++p) {
-      if (plans[p].st != KR_OK) continue;
-      const Prod& P = plans[p].p;
-      live_ids.push_back(p);
-      if (P.path == PATH_DENSE) {
-        dense_ids.push_back(p);
-        dense_tasks_total += plans[p].dense_task_cap;
-        nblocks_total += P.nblocks;
-        max_S = std::max(max_S, P.S);
-      } else {
-        hash_ids.push_back(p);
-        hash_tasks_total += P.ntasks;
-        const int64_t nb = order_bins(P.krange);
-        if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, 2 * (nb + 1));
-        else scan_entries = std::max(scan_entries, radix_scan_entries(plans[p].out_cap));
+  }
+  std::vector<Plan>& plans = ctx->plans;
+  std::vector<int> live_ids, dense_ids, hash_ids;
+  for (int p = 0; p < nprod; ++p) {
+    if (plans[p].st != KR_OK) continue;
+    live_ids.push_back(p);
+    (plans[p].p.path == PATH_DENSE ? dense_ids : hash_ids).push_back(p);
+  }
+  const int nlive = (int)live_ids.size();
+  if (nlive == 0) return;
+  std::vector<int> local(nprod, -1);
+  for (int q = 0; q < nlive; ++q) local[live_ids[q]] = q;
+  std::vector<int32_t> h_dense_local, h_hash_local;
+  for (int p : dense_ids) h_dense_local.push_back(local[p]);
+  for (int p : hash_ids) h_hash_local.push_back(local[p]);
+  // ---------------- phase B1 layout (work arena)
+  int64_t dense_tasks_total = 0, nblocks_total = 0, scan_b1 = 0, max_ng_dense = 0, max_S = 0;
+  for (int p : dense_ids) {
+    dense_tasks_total += plans[p].dense_task_cap;
+    nblocks_total += plans[p].p.nblocks;
+    max_ng_dense = std::max(max_ng_dense, plans[p].p.g.n);
+    max_S = std::max(max_S, plans[p].p.S);
+  }
+  for (int p : live_ids) scan_b1 = std::max(scan_b1, radix_scan_entries(plans[p].radix_sort_n));
+  struct B1 {
+    Prod* lprods; OpRef* oplists; int32_t* dense_ids; int64_t* block_begin; int32_t* hash_ids;
+    int64_t* task_begin; int64_t* scan; DenseTask* tasks; uint32_t* hll; size_t hll_bytes;
+  } A{};
+  for (int pass = 0; pass < 2; ++pass) {
+    Bump b(pass ? ctx->work : nullptr);
+    A.lprods = b.take<Prod>(nlive);
+    A.oplists = b.take<OpRef>(3 * (int64_t)nops);
+    A.dense_ids = b.take<int32_t>((int64_t)dense_ids.size() + 1);
+    A.block_begin = b.take<int64_t>((int64_t)dense_ids.size() + 1);
+    A.hash_ids = b.take<int32_t>((int64_t)hash_ids.size() + 1);
+    A.task_begin = b.take<int64_t>((int64_t)hash_ids.size() + 1);
+    A.scan = b.take<int64_t>(scan_b1 + 1);
+    A.tasks = b.take<DenseTask>(dense_tasks_total);
+    A.hll = b.take<uint32_t>((int64_t)hash_ids.size() * HLL_M);
+    A.hll_bytes = sizeof(uint32_t) * hash_ids.size() * HLL_M;
+    for (int q = 0; q < (int)hash_ids.size(); ++q)
+      if (pass) plans[hash_ids[q]].p.hll = A.hll + (int64_t)q * HLL_M;
+    for (int p : live_ids) {
+      Plan& pl = plans[p];
+      for (int which = 0; which < 2; ++which) {
+        Operand& op = which ? pl.p.g : pl.p.f;
+        const int64_t n = op.n;
+        uint64_t* ka = b.take<uint64_t>(n);
+        uint64_t* kb = b.take<uint64_t>(n);
+        uint64_t* ia = b.take<uint64_t>(n);
+        uint64_t* ib = b.take<uint64_t>(n);
+        op.skey = ka;
+        op.sidx = ia;
+        op.skey2 = kb;
+        op.sidx2 = ib;
+        const int passes = which ? pl.passes_g : pl.passes_f;
+        if (op.sort_method == SORT_RADIX && passes % 2 == 0) { op.skey2 = ka; op.sidx2 = ia; }
+        op.code = b.take<int64_t>(n);
+        op.coef = (void*)b.take<uint64_t>(n);
+        if (pl.p.nt > 0) {
+          op.tcode = b.take<int64_t>(n);
+          op.kind = b.take<uint8_t>(n);
+        }
       }
-      nchunks_total += P.nchunks;
-      out_total += plans[p].out_cap;
-      scan_entries = std::max(scan_entries, radix_scan_entries(plans[p].radix_sort_n));
+      if (pl.p.path == PATH_DENSE) {
+        pl.p.gidx = b.take<int32_t>(pl.p.gidx_n + 1);
+        pl.p.g.code32 = b.take<int32_t>(pl.p.g.n);
+      }
     }
-    const int nlive = (int)live_ids.size();
-    size_t work_need = 0;
-    struct Arr {
-      DenseTask* tasks; int64_t* counters; int32_t* dense_ids; int64_t* block_begin;
-      int32_t* hash_ids; int64_t* task_begin; int64_t* chunk_begin; int64_t* counts;
-      int64_t* scan; uint64_t *okey, *oval, *okey2, *oval2; Prod* lprods; OpRef* oplists;
-      int64_t* bins;
-      char* zero; size_t zero_bytes;
-    } A{};
+    if (!pass) ensure(ctx, &ctx->work, &ctx->work_cap, b.off + 1, s);
+  }
+  std::vector<int64_t> h_block_begin(dense_ids.size() + 1, 0), h_task_begin(hash_ids.size() + 1, 0);
+  for (size_t q = 0; q < dense_ids.size(); ++q)
+    h_block_begin[q + 1] = h_block_begin[q] + plans[dense_ids[q]].p.nblocks;
+  for (size_t q = 0; q < hash_ids.size(); ++q) {
+    plans[hash_ids[q]].p.task_begin = h_task_begin[q];
+    h_task_begin[q + 1] = h_task_begin[q] + plans[hash_ids[q]].p.ntasks;
+  }
+  std::vector<OpRef> all, bm, bt;
+  for (int q = 0; q < nlive; ++q) {
+    const Prod& P = plans[live_ids[q]].p;
+    for (int which = 0; which < 2; ++which) {
+      const Operand& op = which ? P.g : P.f;
+      all.push_back(OpRef{q, which});
+      if (op.sort_method == SORT_BITMAP) bm.push_back(OpRef{q, which});
+      if (op.sort_method == SORT_BITONIC) bt.push_back(OpRef{q, which});
+    }
+  }
+  std::vector<OpRef> lists = all;
+  lists.insert(lists.end(), bm.begin(), bm.end());
+  lists.insert(lists.end(), bt.begin(), bt.end());
+  ensure_pinned(ctx, sizeof(Prod) * (size_t)(nlive + 1) * 2 + sizeof(OpRef) * lists.size() +
+                         16 * (h_block_begin.size() + h_task_begin.size() + 4 * (size_t)nlive) + 65536, s);
+  Bump hb(ctx->pinned);
+  Prod* hl = hb.take<Prod>(nlive);
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return;
+    void* st = hb.take<char>((int64_t)bytes);
+    memcpy(st, src, bytes);
+    ck(ctx, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyHostToDevice, s), "upload plan");
+  };
+  for (int q = 0; q < nlive; ++q) hl[q] = plans[live_ids[q]].p;
+  ck(ctx, cudaMemcpyAsync(A.lprods, hl, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
+  up(A.oplists, lists.data(), sizeof(OpRef) * lists.size());
+  up(A.dense_ids, h_dense_local.data(), 4 * h_dense_local.size());
+  up(A.block_begin, h_block_begin.data(), 8 * h_block_begin.size());
+  up(A.hash_ids, h_hash_local.data(), 4 * h_hash_local.size());
+  up(A.task_begin, h_task_begin.data(), 8 * h_task_begin.size());
+  const OpRef* d_all = A.oplists;
+  const OpRef* d_bm = d_all + all.size();
+  const OpRef* d_bt = d_bm + bm.size();
+  // ---------------- phase B1 device work
+  mark(ctx, s, "plan_upload");
+  if (A.hll_bytes) ck(ctx, cudaMemsetAsync(A.hll, 0, A.hll_bytes, s), "memset hll");
+  ck(ctx, launch_encode(A.lprods, d_all, (int)all.size(), s), "encode");
+  ctx->launches += 1;
+  mark(ctx, s, "encode");
+  if (!bm.empty()) {
+    int64_t mx = 0;
+    for (auto& r : bm) {
+      const Prod& P = plans[live_ids[r.prod]].p;
+      mx = std::max(mx, ((r.which ? P.g : P.f).key_range + 1023) / 1024);
+    }
+    ck(ctx, launch_sort_small(A.lprods, d_bm, (int)bm.size(), SORT_BITMAP, (size_t)mx * 33 * 4 + 64, s),
+       "bitmap sort");
+    ctx->launches += 1;
+  }
+  if (!bt.empty()) {
+    int64_t mx = 0;
+    for (auto& r : bt) {
+      const Prod& P = plans[live_ids[r.prod]].p;
+      mx = std::max(mx, (r.which ? P.g : P.f).n);
+    }
+    ck(ctx, launch_sort_small(A.lprods, d_bt, (int)bt.size(), SORT_BITONIC, (size_t)mx * 8, s),
+       "bitonic sort");
+    ctx->launches += 1;
+  }
+  for (int q = 0; q < nlive; ++q) {
+    const Plan& pl = plans[live_ids[q]];
+    for (int which = 0; which < 2; ++which) {
+      const Operand& op = which ? pl.p.g : pl.p.f;
+      if (op.sort_method != SORT_RADIX) continue;
+      const int bits = bits_for((uint64_t)op.key_range);
+      bool in_tmp = false;
+      // keys in skey/sidx; the result ends in skey2/sidx2 (aliases skey when passes are even)
+      uint64_t* tk = op.skey2 == op.skey ? (uint64_t*)op.code : op.skey2;
+      uint64_t* tv = op.sidx2 == op.sidx ? (uint64_t*)op.coef : op.sidx2;
+      ck(ctx, radix_sort_pairs(op.skey, op.sidx, tk, tv, op.n, bits, A.scan, s, &in_tmp),
+         "radix sort operand");
+      ctx->launches += 3 * ((bits + 7) / 8);
+    }
+  }
+  mark(ctx, s, "sort");
+  ck(ctx, launch_gather(A.lprods, d_all, (int)all.size(), s), "gather");
+  ctx->launches += 1;
+  mark(ctx, s, "gather");
+  if (!dense_ids.empty()) {
+    ck(ctx, launch_build_gindex(A.lprods, A.dense_ids, (int)dense_ids.size(), max_ng_dense, s), "g index");
+    ctx->launches += 1;
+  }
+  if (!hash_ids.empty()) {
+    bool need_hll = false;
+    for (int p : hash_ids) need_hll |= ins[p].opts.table_slots <= 0;
+    if (need_hll) {
+      ck(ctx, launch_hll(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(), ctx->num_sms * 8, s),
+         "hll");
+      ck(ctx, launch_hll_estimate(A.lprods, A.hash_ids, (int)hash_ids.size(), s), "hll estimate");
+      ctx->launches += 2;
+      mark(ctx, s, "hll");
+    }
+  }
+  ck(ctx, cudaMemcpyAsync(hl, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
+  ck(ctx, cudaStreamSynchronize(s), "sync b1");
+  collect_stages(ctx);
+  for (int q = 0; q < nlive; ++q) {
+    Plan& pl = plans[live_ids[q]];
+    pl.p.status = hl[q].status;
+    pl.p.hll_est = hl[q].hll_est;
+  }
+  // ---------------- phase B2, repeated for products whose table filled up
+  std::vector<int> regrows(nprod, 0);
+  for (;;) {
+    int64_t out_total = 0, nchunks_total = 0, bins_total = 0, scan_b2 = 0, max_hash_out = 0;
+    for (int p : hash_ids) {
+      Plan& pl = plans[p];
+      finish_hash_sizes(ins[p].opts, &pl);
+      max_hash_out = std::max(max_hash_out, pl.out_cap);
+      const int64_t nb = order_bins(pl.p.krange);
+      if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, 2 * (nb + 1));
+      else scan_b2 = std::max(scan_b2, radix_scan_entries(pl.out_cap));
+    }
+    std::vector<int64_t> h_chunk_begin(nlive + 1, 0);
+    for (int q = 0; q < nlive; ++q) {
+      Plan& pl = plans[live_ids[q]];
+      pl.p.out_cap = pl.out_cap;
+      pl.p.out_begin = out_total;
+      pl.p.chunk_begin = nchunks_total;
+      h_chunk_begin[q] = nchunks_total;
+      out_total += pl.out_cap;
+      nchunks_total += pl.p.nchunks;
+    }
+    h_chunk_begin[nlive] = nchunks_total;
+    struct B2 {
+      int64_t* chunk_begin; int64_t* counts; int64_t* scan; int64_t* bins; uint64_t *okey, *oval, *okey2, *oval2;
+      int64_t* counters; char* zero; size_t zero_bytes;
+    } Z{};
     for (int pass = 0; pass < 2; ++pass) {
-      Bump b(pass ? ctx->work : nullptr);
-      b.take<char>((int64_t)meta_need);
-      A.lprods = b.take<Prod>(nlive);
-      A.oplists = b.take<OpRef>(3 * (int64_t)nops);
-      A.dense_ids = b.take<int32_t>((int64_t)dense_ids.size() + 1);
-      A.block_begin = b.take<int64_t>((int64_t)dense_ids.size() + 1);
-      A.hash_ids = b.take<int32_t>((int64_t)hash_ids.size() + 1);
-      A.task_begin = b.take<int64_t>((int64_t)hash_ids.size() + 1);
-      A.chunk_begin = b.take<int64_t>(nlive + 1);
-      A.counts = b.take<int64_t>(nchunks_total + 1);
-      A.scan = b.take<int64_t>(scan_entries + 1);
-      A.bins = b.take<int64_t>(bins_total);
-      A.tasks = b.take<DenseTask>(dense_tasks_total);
-      A.okey = b.take<uint64_t>(out_total);
-      A.oval = b.take<uint64_t>(out_total);
-      A.okey2 = b.take<uint64_t>(hash_ids.empty() ? 0 : out_total);
-      A.oval2 = b.take<uint64_t>(hash_ids.empty() ? 0 : out_total);
-      for (int p : live_ids) {
-        Plan& pl = plans[p];
-        for (int which = 0; which < 2; ++which) {
-          Operand& op = which ? pl.p.g : pl.p.f;
-          const int64_t n = op.n;
-          uint64_t* ka = b.take<uint64_t>(n);
-          uint64_t* kb = b.take<uint64_t>(n);
-          uint64_t* ia = b.take<uint64_t>(n);
-          uint64_t* ib = b.take<uint64_t>(n);
-          op.skey = ka;
-          op.sidx = ia;
-          op.skey2 = kb;
-          op.sidx2 = ib;
-          const int passes = which ? pl.passes_g : pl.passes_f;
-          if (op.sort_method == SORT_RADIX && passes % 2 == 0) { op.skey2 = ka; op.sidx2 = ia; }
-          op.code = b.take<int64_t>(n);
-          op.coef = (void*)b.take<uint64_t>(n);
-          if (pl.p.nt > 0) {
-            op.tcode = b.take<int64_t>(n);
-            op.kind = b.take<uint8_t>(n);
-          }
-        }
-        if (pl.p.path == PATH_DENSE) {
-          pl.p.gidx = b.take<int32_t>(pl.p.gidx_n + 1);
-          pl.p.g.code32 = b.take<int32_t>(pl.p.g.n);
-        }
-      }
-      // zeroed region: task counters, dense arrays, tables (one memset)
+      Bump b(pass ? ctx->acc : nullptr);
+      Z.chunk_begin = b.take<int64_t>(nlive + 1);
+      Z.counts = b.take<int64_t>(nchunks_total + 1);
+      Z.scan = b.take<int64_t>(scan_b2 + 1);
+      Z.bins = b.take<int64_t>(bins_total);
+      Z.okey = b.take<uint64_t>(out_total);
+      Z.oval = b.take<uint64_t>(out_total);
+      // ordering scratch: one hash product at a time
+      Z.okey2 = b.take<uint64_t>(max_hash_out);
+      Z.oval2 = b.take<uint64_t>(max_hash_out);
       b.off = (b.off + 255) / 256 * 256;
       const size_t zero_start = b.off;
-      A.zero = b.base ? b.base + zero_start : nullptr;
-      A.counters = b.take<int64_t>(4);
+      Z.zero = b.base ? b.base + zero_start : nullptr;
+      Z.counters = b.take<int64_t>(4);
       for (int p : live_ids) {
         Plan& pl = plans[p];
         if (pl.p.path == PATH_DENSE) pl.p.dense = (void*)b.take<uint64_t>(pl.p.krange);
         else pl.p.table = b.take<uint64_t>(2 * pl.p.slots);
       }
-      A.zero_bytes = b.off - zero_start;
-      if (!pass) {
-        work_need = b.off;
-        ensure(ctx, &ctx->work, &ctx->work_cap, work_need + 1, s);
-        // the metadata lived in the old arena: re-upload after a regrowth
-        Bump m(ctx->work);
-        dprods = m.take<Prod>(nprod);
-        dops = m.take<OpRef>(nops);
-      }
+      Z.zero_bytes = b.off - zero_start;
+      if (!pass) ensure(ctx, &ctx->acc, &ctx->acc_cap, b.off + 1, s);
     }
-    // ---------------- finish the plans, upload
-    std::vector<int64_t> h_block_begin(dense_ids.size() + 1, 0), h_task_begin(hash_ids.size() + 1, 0);
-    std::vector<int64_t> h_chunk_begin(nlive + 1, 0);
-    std::vector<int32_t> h_dense_local, h_hash_local;
+    Bump hb2(ctx->pinned);
+    Prod* hl2 = hb2.take<Prod>(nlive);
+    for (int q = 0; q < nlive; ++q) hl2[q] = plans[live_ids[q]].p;
+    ck(ctx, cudaMemcpyAsync(A.lprods, hl2, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
     {
-      int64_t ob = 0, cb = 0;
-      for (int q = 0; q < nlive; ++q) {
-        Plan& pl = plans[live_ids[q]];
-        pl.p.out_cap = pl.out_cap;
-        pl.p.out_begin = ob;
-        pl.p.chunk_begin = cb;
-        h_chunk_begin[q] = cb;
-        ob += pl.out_cap;
-        cb += pl.p.nchunks;
-      }
-      h_chunk_begin[nlive] = cb;
-      int64_t bb = 0, tb = 0;
-      for (size_t q = 0; q < dense_ids.size(); ++q) {
-        h_block_begin[q] = bb;
-        bb += plans[dense_ids[q]].p.nblocks;
-      }
-      h_block_begin[dense_ids.size()] = bb;
-      for (size_t q = 0; q < hash_ids.size(); ++q) {
-        Plan& pl = plans[hash_ids[q]];
-        pl.p.task_begin = tb;
-        h_task_begin[q] = tb;
-        tb += pl.p.ntasks;
-      }
-      h_task_begin[hash_ids.size()] = tb;
-      // local (live) index of each product
-      std::vector<int> local(nprod, -1);
-      for (int q = 0; q < nlive; ++q) local[live_ids[q]] = q;
-      for (int p : dense_ids) h_dense_local.push_back(local[p]);
-      for (int p : hash_ids) h_hash_local.push_back(local[p]);
+      int64_t* st = hb2.take<int64_t>(nlive + 1);
+      memcpy(st, h_chunk_begin.data(), 8 * (size_t)(nlive + 1));
+      ck(ctx, cudaMemcpyAsync(Z.chunk_begin, st, 8 * (size_t)(nlive + 1), cudaMemcpyHostToDevice, s),
+         "upload chunks");
     }
-    size_t pin_need = sizeof(Prod) * (nlive + 1) + 8 * (h_block_begin.size() + h_task_begin.size() +
-                                                      h_chunk_begin.size()) +
-                      4 * (h_dense_local.size() + h_hash_local.size()) +
-                      sizeof(OpRef) * 3 * (size_t)nops + 16 * 256;
-    ensure_pinned(ctx, pin_need, s);
-    Bump hb(ctx->pinned);
-    Prod* hl = hb.take<Prod>(nlive);
-    for (int q = 0; q < nlive; ++q) hl[q] = plans[live_ids[q]].p;
-    auto up = [&](void* dst, const void* src, size_t bytes) {
-      if (bytes == 0) return;
-      void* st = hb.take<char>((int64_t)bytes);
-      memcpy(st, src, bytes);
-      ck(ctx, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyHostToDevice, s), "upload plan");
-    };
-    if (nlive > 0) ck(ctx, cudaMemcpyAsync(A.lprods, hl, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s),
-                      "upload plan");
-    up(A.block_begin, h_block_begin.data(), 8 * h_block_begin.size());
-    up(A.task_begin, h_task_begin.data(), 8 * h_task_begin.size());
-    up(A.chunk_begin, h_chunk_begin.data(), 8 * h_chunk_begin.size());
-    up(A.dense_ids, h_dense_local.data(), 4 * h_dense_local.size());
-    up(A.hash_ids, h_hash_local.data(), 4 * h_hash_local.size());
-    // ---------------- device work
-    if (nlive > 0) {
-      std::vector<OpRef> bm, bt, all;
-      for (int q = 0; q < nlive; ++q) {
-        const Prod& P = plans[live_ids[q]].p;
-        for (int which = 0; which < 2; ++which) {
-          const Operand& op = which ? P.g : P.f;
-          all.push_back(OpRef{q, which});
-          if (op.sort_method == SORT_BITMAP) bm.push_back(OpRef{q, which});
-          if (op.sort_method == SORT_BITONIC) bt.push_back(OpRef{q, which});
-        }
-      }
-      std::vector<OpRef> packed = all;
-      packed.insert(packed.end(), bm.begin(), bm.end());
-      packed.insert(packed.end(), bt.begin(), bt.end());
-      OpRef* dlists = A.oplists;
-      up(dlists, packed.data(), sizeof(OpRef) * packed.size());
-      const OpRef* d_all = dlists;
-      const OpRef* d_bm = dlists + all.size();
-      const OpRef* d_bt = d_bm + bm.size();
-      mark(ctx, s, "plan_upload");
-      ck(ctx, cudaMemsetAsync(A.zero, 0, A.zero_bytes, s), "memset accumulators");
-      mark(ctx, s, "zero_accumulators");
-      ck(ctx, launch_encode(A.lprods, d_all, (int)all.size(), s), "encode");
+    mark(ctx, s, "plan_upload");
+    ck(ctx, cudaMemsetAsync(Z.zero, 0, Z.zero_bytes, s), "memset accumulators");
+    mark(ctx, s, "zero_accumulators");
+    if (!dense_ids.empty()) {
+      ck(ctx, launch_dense_plan(A.lprods, A.dense_ids, A.block_begin, (int)dense_ids.size(),
+                                nblocks_total, A.tasks, dense_tasks_total, Z.counters, s),
+         "dense plan");
       ctx->launches += 1;
-      mark(ctx, s, "encode");
-      if (!bm.empty()) {
-        int64_t mx = 0;
-        for (auto& r : bm) {
-          const Prod& P = plans[live_ids[r.prod]].p;
-          const Operand& op = r.which ? P.g : P.f;
-          mx = std::max(mx, (op.key_range + 1023) / 1024);
-        }
-        const size_t smem = (size_t)mx * 33 * 4 + 64;
-        ck(ctx, launch_sort_small(A.lprods, d_bm, (int)bm.size(), SORT_BITMAP, smem, s), "bitmap sort");
-        ctx->launches += 1;
-      }
-      if (!bt.empty()) {
-        int64_t mx = 0;
-        for (auto& r : bt) {
-          const Prod& P = plans[live_ids[r.prod]].p;
-          mx = std::max(mx, (r.which ? P.g : P.f).n);
-        }
-        ck(ctx, launch_sort_small(A.lprods, d_bt, (int)bt.size(), SORT_BITONIC, (size_t)mx * 8, s),
-           "bitonic sort");
-        ctx->launches += 1;
-      }
-      for (int q = 0; q < nlive; ++q) {
-        const Plan& pl = plans[live_ids[q]];
-        for (int which = 0; which < 2; ++which) {
-          const Operand& op = which ? pl.p.g : pl.p.f;
-          if (op.sort_method != SORT_RADIX) continue;
-          const int bits = bits_for((uint64_t)op.key_range);
-          bool in_tmp = false;
-          // keys in skey/sidx; result must end in skey2/sidx2 (aliases skey when passes are even)
-          uint64_t* tk = op.skey2 == op.skey ? (uint64_t*)nullptr : op.skey2;
-          uint64_t* tv = op.sidx2 == op.sidx ? (uint64_t*)nullptr : op.sidx2;
-          if (!tk) {
-            // even number of passes: ping-pong through the spare buffers after skey/sidx
-            tk = (uint64_t*)op.code;            // n int64, free until the gather
-            tv = (uint64_t*)op.coef;            // n 8-byte values, free until the gather
-          }
-          ck(ctx, radix_sort_pairs(op.skey, op.sidx, tk, tv, op.n, bits, A.scan, s, &in_tmp),
-             "radix sort operand");
-          ctx->launches += 3 * ((bits + 7) / 8);
-        }
-      }
-      mark(ctx, s, "sort");
-      ck(ctx, launch_gather(A.lprods, d_all, (int)all.size(), s), "gather");
+      mark(ctx, s, "dense_plan");
+      ck(ctx, launch_dense_accum(A.lprods, A.tasks, Z.counters, dense_tasks_total, Z.counters + 1,
+                                 ctx->num_sms, max_S, s),
+         "dense accumulate");
       ctx->launches += 1;
-      mark(ctx, s, "gather");
-      if (!dense_ids.empty()) {
-        int64_t max_ng = 0;
-        for (int p : dense_ids) max_ng = std::max(max_ng, plans[p].p.g.n);
-        ck(ctx, launch_build_gindex(A.lprods, A.dense_ids, (int)dense_ids.size(), max_ng, s),
-           "g index");
-        ctx->launches += 1;
-        ck(ctx, launch_dense_plan(A.lprods, A.dense_ids, A.block_begin, (int)dense_ids.size(),
-                                  nblocks_total, A.tasks, dense_tasks_total, A.counters, s),
-           "dense plan");
-        ctx->launches += 1;
-        mark(ctx, s, "dense_plan");
-        ck(ctx, launch_dense_accum(A.lprods, A.tasks, A.counters, dense_tasks_total, A.counters + 1,
-                                   ctx->num_sms, max_S, s),
-           "dense accumulate");
-        ctx->launches += 1;
-        mark(ctx, s, "dense_accum");
-      }
-      if (!hash_ids.empty()) {
-        ck(ctx, launch_hash_insert(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(),
-                                   ctx->num_sms * 8, s),
-           "hash insert");
-        ctx->launches += 1;
-        mark(ctx, s, "hash_insert");
-      }
-      ck(ctx, launch_compact(A.lprods, nlive, A.chunk_begin, h_chunk_begin[nlive], A.counts, A.okey,
-                             A.oval, s),
-         "compaction");
-      ctx->launches += h_chunk_begin[nlive] > 0 ? 4 : 1;
-      mark(ctx, s, "compact");
-      ck(ctx, cudaMemcpyAsync(hl, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
+      mark(ctx, s, "dense_accum");
     }
+    if (!hash_ids.empty()) {
+      ck(ctx, launch_hash_insert(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(),
+                                 ctx->num_sms * 8, s),
+         "hash insert");
+      ctx->launches += 1;
+      mark(ctx, s, "hash_insert");
+    }
+    ck(ctx, launch_compact(A.lprods, nlive, Z.chunk_begin, nchunks_total, Z.counts, Z.okey, Z.oval,
+                           out_total, s),
+       "compaction");
+    ctx->launches += nchunks_total > 0 ? 4 : 1;
+    mark(ctx, s, "compact");
+    ck(ctx, cudaMemcpyAsync(hl2, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
     ck(ctx, cudaStreamSynchronize(s), "sync results");
     collect_stages(ctx);
-    // ---------------- statuses; regrow full tables
     bool retry = false;
     for (int q = 0; q < nlive; ++q) {
       const int p = live_ids[q];
-      const Prod& P = hl[q];
+      Prod& P = hl2[q];
+      plans[p].p.nout = P.nout;
+      plans[p].p.out_start = P.out_start;
+      if ((P.status & ST_OUTCAP) && !(P.status & ~ST_OUTCAP) && !plans[p].outcap_full) {
+        // the estimate fell short: rerun with room for a full table
+        plans[p].outcap_full = true;
+        plans[p].p.status = 0;
+        retry = true;
+        continue;
+      }
       if (P.status & ST_TABLE_FULL) {
         const int mr = ins[p].opts.max_regrow;
         const int allowed = mr > 0 ? mr : (mr < 0 ? 0 : 4);
-        // grow x4; the last allowed regrowth goes straight to the table the
-        // term-product bound asks for (a full table of that size means the
-        // probe limit, not the size, failed)
         const int64_t bound = plans[p].bound_slots;
         if (regrows[p] < allowed && P.slots < bound) {
           regrows[p]++;
-          hints[p] = regrows[p] == allowed ? bound : std::min(P.slots * 4, bound);
+          plans[p].slots_override = regrows[p] == allowed ? bound : std::min(P.slots * 4, bound);
+          plans[p].p.status = 0;
           retry = true;
           continue;
         }
@@ -558,30 +562,33 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       res[p].n = P.nout;
       res[p].prod = P;
       res[p].dprod = A.lprods + q;
-      res[p].key = A.okey + P.out_start;
-      res[p].val = A.oval + P.out_start;
+      res[p].key = Z.okey + P.out_start;
+      res[p].val = Z.oval + P.out_start;
       if (P.nout > P.out_cap) res[p].st = KR_ERR_CUDA;
     }
-    if (retry) continue;
-    // ---------------- hash outputs: sort by key
+    if (retry) continue;   // phase B2 again, with the grown tables
+    // ---------------- hash outputs: order by key
     mark(ctx, s, "begin");
     for (int q = 0; q < nlive; ++q) {
       const int p = live_ids[q];
       ProdResult& r = res[p];
       if (r.st != KR_OK || r.prod.path != PATH_HASH || r.n < 2 || ins[p].opts.unsorted) continue;
-      const int bits = bits_for((uint64_t)r.prod.krange);
-      bool in_tmp = false;
-      uint64_t* k = A.okey + r.prod.out_start;
-      uint64_t* v = A.oval + r.prod.out_start;
-      uint64_t* k2 = A.okey2 + r.prod.out_start;
-      uint64_t* v2 = A.oval2 + r.prod.out_start;
+      uint64_t* k = Z.okey + r.prod.out_start;
+      uint64_t* v = Z.oval + r.prod.out_start;
+      uint64_t* k2 = Z.okey2;
+      uint64_t* v2 = Z.oval2;
       if (order_bins(r.prod.krange) <= ORDER_MAX_BINS) {
-        ck(ctx, order_by_bins(k, v, k2, v2, r.n, r.prod.krange, A.bins, s), "output order");
+        ck(ctx, order_by_bins(k, v, k2, v2, r.n, r.prod.krange, Z.bins, s), "output order");
         ctx->launches += 4;
       } else {
-        ck(ctx, radix_sort_pairs(k, v, k2, v2, r.n, bits, A.scan, s, &in_tmp), "output sort");
+        const int bits = bits_for((uint64_t)r.prod.krange);
+        bool in_tmp = false;
+        ck(ctx, radix_sort_pairs(k, v, k2, v2, r.n, bits, Z.scan, s, &in_tmp), "output sort");
         ctx->launches += 3 * ((bits + 7) / 8);
-        if (in_tmp) { r.key = k2; r.val = v2; }
+        if (in_tmp) {
+          ck(ctx, cudaMemcpyAsync(k, k2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
+          ck(ctx, cudaMemcpyAsync(v, v2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
+        }
       }
     }
     mark(ctx, s, "output_sort");
@@ -746,6 +753,8 @@ void kr_ctx_destroy(kr_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->in_arena) cudaFree(ctx->in_arena);
   if (ctx->work) cudaFree(ctx->work);
+  if (ctx->acc) cudaFree(ctx->acc);
+  for (void* b : ctx->batch_blocks) cudaFree(b);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   cudaSetDevice(prev);
@@ -755,7 +764,7 @@ void kr_ctx_destroy(kr_ctx* ctx) {
 const char* kr_last_error(const kr_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
 
 int64_t kr_ctx_scratch_bytes(const kr_ctx* ctx) {
-  return ctx ? (int64_t)(ctx->in_cap + ctx->work_cap) : 0;
+  return ctx ? (int64_t)(ctx->in_cap + ctx->work_cap + ctx->acc_cap) : 0;
 }
 
 kr_status kr_ctx_set_profiling(kr_ctx* ctx, int32_t enable) {
@@ -954,6 +963,194 @@ kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g, kr_
     if (res[0].st != KR_OK) return res[0].st;
     keep_result(ctx, res[0], true);
     return emit_pseries(ctx, h, s);
+  });
+}
+
+namespace {
+
+bool poly_job_ok(const kr_poly* f, const kr_poly* g) {
+  if (f->nvars < 1 || f->nvars > KR_MAXV || g->nvars != f->nvars) return false;
+  if (f->type != g->type || (f->type != KR_I64 && f->type != KR_F64)) return false;
+  if (f->nterms < 0 || g->nterms < 0 || f->nterms >= INT32_MAX || g->nterms >= INT32_MAX) return false;
+  if ((f->nterms > 0 && (!f->exps || !f->coef)) || (g->nterms > 0 && (!g->exps || !g->coef))) return false;
+  return true;
+}
+
+bool pseries_job_ok(const kr_pseries* f, const kr_pseries* g) {
+  if (f->ntrig < 1 || f->npoly < 0 || f->npoly + f->ntrig > KR_MAXV) return false;
+  if (g->npoly != f->npoly || g->ntrig != f->ntrig) return false;
+  if (f->nterms < 0 || g->nterms < 0 || f->nterms >= INT32_MAX || g->nterms >= INT32_MAX) return false;
+  auto bad = [](const kr_pseries* p) {
+    return p->nterms > 0 && ((p->npoly > 0 && !p->exps) || !p->trig || !p->kind || !p->coef);
+  };
+  return !bad(f) && !bad(g);
+}
+
+// One wave of a batch: pipeline, then one batched decode into a fresh block.
+kr_status run_wave(kr_ctx* ctx, const std::vector<JobIn>& ins, const std::vector<int>& idx,
+                   kr_result* res, cudaStream_t s) {
+  std::vector<ProdResult> pr;
+  try {
+    run_pipeline(ctx, ins, s, pr);
+  } catch (const CudaFail& f) {
+    if (f.e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      return KR_ERR_OOM;
+    }
+    throw;
+  }
+  // live products in device order
+  std::vector<int> order;
+  for (int p = 0; p < (int)ins.size(); ++p)
+    if (pr[p].dprod) order.push_back(p);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return pr[a].dprod < pr[b].dprod; });
+  size_t bytes = 0;
+  for (int p : order) {
+    const int nv = pr[p].prod.np + pr[p].prod.nt;
+    bytes += (size_t)pr[p].n * (4 * nv + 1 + 8) + 4 * 256;
+  }
+  void* block = nullptr;
+  if (bytes > 0) {
+    cudaError_t e = cudaMalloc(&block, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return KR_ERR_OOM;
+    }
+    ctx->batch_blocks.push_back(block);
+  }
+  const int nl = (int)order.size();
+  std::vector<ResDesc> rd(nl);
+  std::vector<int64_t> ostart(nl + 1, 0);
+  Bump b(block);
+  int64_t total = 0;
+  for (int q = 0; q < nl; ++q) {
+    const ProdResult& r = pr[order[q]];
+    const int64_t n = r.st == KR_OK ? r.n : 0;
+    rd[q].n = n;
+    rd[q].coef = (void*)b.take<uint64_t>(n);
+    rd[q].exps = b.take<int32_t>(n * r.prod.np);
+    rd[q].trig = r.prod.nt ? b.take<int32_t>(n * r.prod.nt) : nullptr;
+    rd[q].kind = r.prod.nt ? b.take<uint8_t>(n) : nullptr;
+    ostart[q] = r.prod.out_start;
+    total = r.prod.out_start + r.n;
+  }
+  if (nl > 0) ostart[nl] = total;
+  for (int q = 0; q < nl; ++q) {
+    const int p = order[q];
+    kr_result& R = res[idx[p]];
+    R.status = pr[p].st;
+    R.path = pr[p].prod.path == PATH_DENSE ? KR_PATH_DENSE : KR_PATH_HASH;
+    R.nterms = pr[p].st == KR_OK ? pr[p].n : 0;
+    R.exps = rd[q].exps;
+    R.trig = rd[q].trig;
+    R.kind = rd[q].kind;
+    R.coef = rd[q].coef;
+  }
+  for (int p = 0; p < (int)ins.size(); ++p)
+    if (!pr[p].dprod) {
+      kr_result& R = res[idx[p]];
+      R.status = pr[p].st;
+      R.nterms = 0;
+    }
+  if (nl == 0 || total == 0) return KR_OK;
+  // the decode reads every live product's Prod from the contiguous device array
+  const Prod* dbase = pr[order[0]].dprod;
+  ensure_pinned(ctx, sizeof(ResDesc) * nl + 8 * (nl + 1) + 1024, s);
+  Bump hp(ctx->pinned);
+  ResDesc* hrd = hp.take<ResDesc>(nl);
+  int64_t* host = hp.take<int64_t>(nl + 1);
+  memcpy(hrd, rd.data(), sizeof(ResDesc) * nl);
+  memcpy(host, ostart.data(), 8 * (size_t)(nl + 1));
+  ensure(ctx, &ctx->in_arena, &ctx->in_cap, sizeof(ResDesc) * nl + 8 * (nl + 1) + 1024, s);
+  Bump db(ctx->in_arena);
+  ResDesc* drd = db.take<ResDesc>(nl);
+  int64_t* dost = db.take<int64_t>(nl + 1);
+  ck(ctx, cudaMemcpyAsync(drd, hrd, sizeof(ResDesc) * nl, cudaMemcpyHostToDevice, s), "upload");
+  ck(ctx, cudaMemcpyAsync(dost, host, 8 * (size_t)(nl + 1), cudaMemcpyHostToDevice, s), "upload");
+  ck(ctx, launch_decode_batch(dbase, nl, dost, drd, pr[order[0]].key - pr[order[0]].prod.out_start,
+                              pr[order[0]].val - pr[order[0]].prod.out_start, total, s),
+     "batched decode");
+  ctx->launches += 1;
+  ck(ctx, cudaStreamSynchronize(s), "sync decode");
+  return KR_OK;
+}
+
+}  // namespace
+
+kr_status kron_mul_batch(kr_ctx* ctx, const kr_job* jobs, int32_t njobs, kr_result* res,
+                         int64_t wave_pairs, kr_stream stream) {
+  if (!ctx || njobs < 0 || (njobs > 0 && (!jobs || !res))) return KR_ERR_INVALID;
+  return guarded(ctx, [&]() -> kr_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    ck(ctx, cudaStreamSynchronize(s), "sync");
+    for (void* b : ctx->batch_blocks) cudaFree(b);
+    ctx->batch_blocks.clear();
+    ctx->has_result = false;
+    ctx->stage_ms.clear();
+    ctx->stage_name.clear();
+    ctx->nev = 0;
+    const double budget = wave_pairs > 0 ? (double)wave_pairs : 8589934592.0;
+    std::vector<JobIn> wave;
+    std::vector<int> idx;
+    double wave_tp = 0.0;
+    std::vector<std::pair<std::vector<JobIn>, std::vector<int>>> waves;
+    for (int i = 0; i < njobs; ++i) {
+      const kr_job& J = jobs[i];
+      kr_result& R = res[i];
+      R = kr_result{};
+      JobIn in;
+      if (J.kind == 0) {
+        if (!poly_job_ok(&J.f, &J.g)) { R.status = KR_ERR_INVALID; continue; }
+        if (J.f.nterms == 0 || J.g.nterms == 0) { R.status = KR_OK; continue; }
+        in.poisson = false;
+        in.f64 = J.f.type == KR_F64;
+        in.np = J.f.nvars;
+        in.fe = J.f.exps; in.fc = J.f.coef; in.nf = J.f.nterms;
+        in.ge = J.g.exps; in.gc = J.g.coef; in.ng = J.g.nterms;
+      } else if (J.kind == 1) {
+        if (!pseries_job_ok(&J.pf, &J.pg) || J.opts.path == KR_PATH_DENSE) { R.status = KR_ERR_INVALID; continue; }
+        if (J.pf.nterms == 0 || J.pg.nterms == 0) { R.status = KR_OK; continue; }
+        in.poisson = true;
+        in.f64 = true;
+        in.np = J.pf.npoly;
+        in.nt = J.pf.ntrig;
+        in.fe = J.pf.exps; in.ft = J.pf.trig; in.fk = J.pf.kind; in.fc = J.pf.coef; in.nf = J.pf.nterms;
+        in.ge = J.pg.exps; in.gt = J.pg.trig; in.gk = J.pg.kind; in.gc = J.pg.coef; in.ng = J.pg.nterms;
+      } else {
+        R.status = KR_ERR_INVALID;
+        continue;
+      }
+      in.opts = J.opts;
+      const double tp = (double)in.nf * (double)in.ng;
+      if (!wave.empty() && (wave_tp + tp > budget || wave.size() >= 8192)) {
+        waves.emplace_back(std::move(wave), std::move(idx));
+        wave.clear();
+        idx.clear();
+        wave_tp = 0.0;
+      }
+      wave.push_back(in);
+      idx.push_back(i);
+      wave_tp += tp;
+    }
+    if (!wave.empty()) waves.emplace_back(std::move(wave), std::move(idx));
+    // run the waves; a wave that runs out of memory is split in two
+    for (size_t w = 0; w < waves.size(); ++w) {
+      kr_status st = run_wave(ctx, waves[w].first, waves[w].second, res, s);
+      if (st == KR_ERR_OOM) {
+        const size_t n = waves[w].first.size();
+        if (n <= 1) return KR_ERR_OOM;
+        std::vector<JobIn> a(waves[w].first.begin(), waves[w].first.begin() + n / 2);
+        std::vector<JobIn> b2(waves[w].first.begin() + n / 2, waves[w].first.end());
+        std::vector<int> ia(waves[w].second.begin(), waves[w].second.begin() + n / 2);
+        std::vector<int> ib(waves[w].second.begin() + n / 2, waves[w].second.end());
+        waves.insert(waves.begin() + w + 1, {std::move(b2), std::move(ib)});
+        waves[w] = {std::move(a), std::move(ia)};
+        --w;
+        continue;
+      }
+      if (st != KR_OK) return st;
+    }
+    return KR_OK;
   });
 }
 

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_count(const Prod* __rest
 __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(const Prod* __restrict__ prods, int nprod,
                                                                 const int64_t* __restrict__ chunk_begin,
                                                                 const int64_t* __restrict__ offs,
+                                                                int64_t cap,
                                                                 uint64_t* __restrict__ okey,
                                                                 uint64_t* __restrict__ oval) {
   const int64_t nchunks = chunk_begin[nprod];
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(const Prod* __re
       const bool live = s < s1 && slot_live(P, s, &k, &v);
       int tot;
       const int pos = block_excl_scan_int<CP_THREADS>(live ? 1 : 0, &tot);
-      if (live) {
+      if (live && run + pos < cap) {
         okey[run + pos] = k;
         oval[run + pos] = v;
       }
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(const Prod* __re
 // per product: where its terms start in the output arrays and how many there are
 __global__ void k_finish_counts(Prod* __restrict__ prods, int nprod,
                                 const int64_t* __restrict__ chunk_begin,
-                                const int64_t* __restrict__ offs, const int64_t* __restrict__ total) {
+                                const int64_t* __restrict__ offs, const int64_t* __restrict__ total,
+                                int64_t cap) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprod) return;
   Prod& P = prods[p];
@@ -134,21 +136,22 @@ __global__ void k_finish_counts(Prod* __restrict__ prods, int nprod,
   const int64_t end = b < nch ? offs[b] : *total;
   P.out_start = start;
   P.nout = P.status ? 0 : end - start;
+  if (end > cap) P.status |= ST_OUTCAP;   // terms beyond the output arrays were not written
 }
 
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
-                           int64_t* dcounts, uint64_t* okey, uint64_t* oval, cudaStream_t s) {
+                           int64_t* dcounts, uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s) {
   if (nchunks > 0) {
     const int grid = (int)(nchunks < 152 * 8 ? nchunks : 152 * 8);
     k_compact_count<<<grid, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts);
     cudaError_t e = launch_scan_exclusive(dcounts, nchunks, dcounts + nchunks, s);
     if (e != cudaSuccess) return e;
-    k_compact_scatter<<<grid, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts, okey, oval);
+    k_compact_scatter<<<grid, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts, cap, okey, oval);
   } else {
     cudaMemsetAsync(dcounts, 0, sizeof(int64_t), s);
   }
   k_finish_counts<<<(nprod + 127) / 128, 128, 0, s>>>(dprods, nprod, dchunk_begin, dcounts,
-                                                      dcounts + nchunks);
+                                                      dcounts + nchunks, cap);
   return cudaGetLastError();
 }
 

@@ -276,6 +276,65 @@ cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* 
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_decode_batch(const Prod* __restrict__ prods, int nprod,
+                                                      const int64_t* __restrict__ ostart,
+                                                      const ResDesc* __restrict__ rd,
+                                                      const uint64_t* __restrict__ okey,
+                                                      const uint64_t* __restrict__ oval, int64_t total) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nprod - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ostart[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const Prod& P = prods[lo];
+    const ResDesc& R = rd[lo];
+    const int64_t t = q - ostart[lo];
+    if (t >= R.n) continue;
+    const int64_t key = (int64_t)okey[q];
+    ((uint64_t*)R.coef)[t] = oval[q];
+    if (P.nt == 0) {
+      int64_t rem = key;
+      for (int k = 0; k < P.np; ++k) {
+        const int64_t d = (k + 1 < P.np) ? rem % P.w[k] : rem;
+        rem = (k + 1 < P.np) ? rem / P.w[k] : 0;
+        R.exps[(int64_t)k * R.n + t] = (int32_t)(d + P.omin[k]);
+      }
+    } else {
+      const int64_t per_kind = P.T2 * P.Wp;
+      const int64_t kd = key / per_kind;
+      const int64_t r2 = key - kd * per_kind;
+      const int64_t T = r2 / P.Wp;
+      int64_t pc = r2 - T * P.Wp;
+      R.kind[t] = (uint8_t)kd;
+      for (int k = 0; k < P.np; ++k) {
+        const int64_t d = (k + 1 < P.np) ? pc % P.w[k] : pc;
+        pc = (k + 1 < P.np) ? pc / P.w[k] : 0;
+        R.exps[(int64_t)k * R.n + t] = (int32_t)(d + P.omin[k]);
+      }
+      int64_t u = T + (P.T2 - 1);
+      for (int k = 0; k < P.nt; ++k) {
+        const int32_t wk = P.w[P.np + k];
+        const int64_t d = (k + 1 < P.nt) ? u % wk : u;
+        u = (k + 1 < P.nt) ? u / wk : 0;
+        R.trig[(int64_t)k * R.n + t] = (int32_t)(d + P.omin[P.np + k]);
+      }
+    }
+  }
+}
+
+cudaError_t launch_decode_batch(const Prod* dprods, int nprod, const int64_t* dostart,
+                                const ResDesc* drd, const uint64_t* okey, const uint64_t* oval,
+                                int64_t total, cudaStream_t s) {
+  if (total > 0 && nprod > 0) {
+    int64_t grid = (total + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    k_decode_batch<<<(unsigned)grid, 256, 0, s>>>(dprods, nprod, dostart, drd, okey, oval, total);
+  }
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // standalone coding of a box (kron_encode / kron_decode entry points)
 // ---------------------------------------------------------------------------

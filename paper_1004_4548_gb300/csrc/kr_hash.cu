@@ -185,6 +185,119 @@ __device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
   return ok;
 }
 
+// ---------------------------------------------------------------------------
+// HyperLogLog pass: same tiles and keys as the inserts, no table traffic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void hll_add(uint32_t* reg, uint64_t key) {
+  const uint64_t h = mix64(key);
+  const uint32_t idx = (uint32_t)(h >> (64 - HLL_B));
+  const uint64_t w = h << HLL_B;
+  const uint32_t rho = w == 0 ? (uint32_t)(64 - HLL_B + 1) : (uint32_t)__clzll((long long)w) + 1;
+  if (reg[idx] < rho) atomicMax(&reg[idx], rho);
+}
+
+__device__ __forceinline__ void hll_tile(const Prod& P, const HashTile& h, uint32_t* reg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = HASH_THREADS / 32;
+  const int64_t* __restrict__ F = P.f.code;
+  const int64_t* __restrict__ G = P.g.code;
+  const int64_t* __restrict__ TF = P.f.tcode;
+  const int64_t* __restrict__ TG = P.g.tcode;
+  const uint8_t* __restrict__ KF = P.f.kind;
+  const uint8_t* __restrict__ KG = P.g.kind;
+  const int64_t T2Wp = P.T2 * P.Wp;
+  for (int64_t i = h.i0 + warp; i < h.i1; i += NW) {
+    const int64_t fi = F[i];
+    if (P.nt == 0) {
+      for (int64_t j = h.j0 + lane; j < h.j1; j += 32) hll_add(reg, (uint64_t)(fi + G[j]));
+    } else {
+      const int64_t ti = TF[i];
+      const int ki = KF[i];
+      for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
+        const int64_t pc = fi + G[j];
+        const int kd = ki ^ KG[j];
+        int64_t T = ti + TG[j];
+        if (T < 0) T = -T;
+        if (!(T == 0 && kd)) hll_add(reg, (uint64_t)(kd * T2Wp + T * P.Wp + pc));
+        T = ti - TG[j];
+        if (T < 0) T = -T;
+        if (!(T == 0 && kd)) hll_add(reg, (uint64_t)(kd * T2Wp + T * P.Wp + pc));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(HASH_THREADS) k_hll(Prod* __restrict__ prods,
+                                                      const int32_t* __restrict__ hash_prods,
+                                                      const int64_t* __restrict__ task_begin, int nhash) {
+  __shared__ uint32_t reg[HLL_M];
+  const int64_t ntasks = task_begin[nhash];
+  int cur = -1;
+  for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const HashTile h = find_tile(prods, hash_prods, task_begin, nhash, t);
+    if (h.pid != cur) {
+      // flush the registers of the previous product, start the next
+      __syncthreads();
+      if (cur >= 0)
+        for (int r = threadIdx.x; r < HLL_M; r += blockDim.x)
+          if (reg[r]) atomicMax(&prods[cur].hll[r], reg[r]);
+      for (int r = threadIdx.x; r < HLL_M; r += blockDim.x) reg[r] = 0;
+      __syncthreads();
+      cur = h.pid;
+    }
+    if (prods[h.pid].status == 0) hll_tile(prods[h.pid], h, reg);
+  }
+  __syncthreads();
+  if (cur >= 0)
+    for (int r = threadIdx.x; r < HLL_M; r += blockDim.x)
+      if (reg[r]) atomicMax(&prods[cur].hll[r], reg[r]);
+}
+
+// One CTA per hash product: E = alpha_m m^2 / sum 2^-M_j, with linear counting
+// m ln(m / V) when E <= 5m/2 and V registers are zero.
+__global__ void __launch_bounds__(256) k_hll_estimate(Prod* __restrict__ prods,
+                                                      const int32_t* __restrict__ hash_prods) {
+  Prod& P = prods[hash_prods[blockIdx.x]];
+  __shared__ double ssum[8];
+  __shared__ int szero[8];
+  double sum = 0.0;
+  int zeros = 0;
+  for (int r = threadIdx.x; r < HLL_M; r += blockDim.x) {
+    const uint32_t v = P.hll[r];
+    sum += ldexp(1.0, -(int)v);
+    zeros += v == 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+  }
+  if ((threadIdx.x & 31) == 0) { ssum[threadIdx.x >> 5] = sum; szero[threadIdx.x >> 5] = zeros; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0;
+    int V = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { S += ssum[w]; V += szero[w]; }
+    const double m = (double)HLL_M;
+    const double alpha = 0.7213 / (1.0 + 1.079 / m);
+    double E = alpha * m * m / S;
+    if (E <= 2.5 * m && V > 0) E = m * log(m / (double)V);
+    P.hll_est = E;
+  }
+}
+
+cudaError_t launch_hll(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin, int nhash,
+                       int grid, cudaStream_t s) {
+  if (nhash <= 0) return cudaSuccess;
+  k_hll<<<grid, HASH_THREADS, 0, s>>>(dprods, dhash_prods, dtask_begin, nhash);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hll_estimate(Prod* dprods, const int32_t* dhash_prods, int nhash, cudaStream_t s) {
+  if (nhash <= 0) return cudaSuccess;
+  k_hll_estimate<<<nhash, 256, 0, s>>>(dprods, dhash_prods);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(HASH_THREADS) k_hash_insert(Prod* __restrict__ prods,
                                                               const int32_t* __restrict__ hash_prods,
                                                               const int64_t* __restrict__ task_begin,

@@ -75,6 +75,8 @@ struct Prod {
   int64_t gidx_n;       // buckets (the last entry gidx[gidx_n] = g.n)
   int32_t gshift;
   // hash path
+  uint32_t* hll;        // HyperLogLog registers of the product's output keys (HLL_M)
+  double hll_est;       // estimated distinct output keys
   uint64_t* table;      // [slots][2] = (key + 1, value); key 0 = empty
   int64_t slots;        // power of two
   int32_t probe_limit;
@@ -165,10 +167,19 @@ cudaError_t launch_dense_accum(const Prod* dprods, const DenseTask* dtasks,
                                const int64_t* dtask_count, int64_t task_cap, int64_t* dtask_next,
                                int grid, int64_t max_S, cudaStream_t s);
 int dense_accum_threads();
+// HyperLogLog cardinality estimate of every hash product's output keys
+// (Flajolet, Fusy, Gandouet, Meunier 2007), from a pass over all term pairs
+// that computes keys only.  2^HLL_B registers per product.
+constexpr int HLL_B = 12;
+constexpr int HLL_M = 1 << HLL_B;
+cudaError_t launch_hll(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin, int nhash,
+                       int grid, cudaStream_t s);
+cudaError_t launch_hll_estimate(Prod* dprods, const int32_t* dhash_prods, int nhash, cudaStream_t s);
 cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
                                int nhash, int grid, cudaStream_t s);
+// Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
-                           int64_t* dcounts, uint64_t* okey, uint64_t* oval, cudaStream_t s);
+                           int64_t* dcounts, uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s);
 cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, cudaStream_t s);
 
 // Device-wide LSD radix sort of (key, 8-byte payload) pairs over the low
@@ -194,6 +205,19 @@ cudaError_t launch_decode_poly(const Prod* dprods, int prod, const uint64_t* oke
 cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
                                   int32_t* exps, int32_t* trig, uint8_t* kind, int64_t ld,
                                   int64_t* codes, cudaStream_t s);
+// Where a batched decode writes one product's terms ([nvars][n] layouts).
+struct ResDesc {
+  int32_t* exps;
+  int32_t* trig;
+  uint8_t* kind;
+  void* coef;
+  int64_t n;
+};
+// Decodes the sorted terms of many products in one launch: output q belongs to
+// the product p with ostart[p] <= q < ostart[p + 1] (products contiguous).
+cudaError_t launch_decode_batch(const Prod* dprods, int nprod, const int64_t* dostart,
+                                const ResDesc* drd, const uint64_t* okey, const uint64_t* oval,
+                                int64_t total, cudaStream_t s);
 cudaError_t launch_encode_box(const int32_t* exps, int64_t n, int nvars, const int32_t* emin,
                               const int32_t* emax, const int64_t* cvec, int64_t* codes,
                               uint32_t* dstatus, cudaStream_t s);

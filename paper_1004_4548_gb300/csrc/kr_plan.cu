@@ -159,23 +159,42 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     pl.out_cap = std::min((double)P.krange, pairs) > 0 ? (int64_t)std::min((double)P.krange, pairs) : 0;
   } else {
     const double m = job.poisson ? 2.0 : 1.0;
-    const double est = std::min(m * pairs, (double)P.krange);
-    double alpha = o.load_factor > 0.0 && o.load_factor <= 0.9 ? o.load_factor : DEFAULT_LOAD;
-    int64_t slots = next_pow2(std::max<int64_t>(1024, (int64_t)std::ceil(est / alpha)));
-    pl.bound_slots = slots;
-    if (o.table_slots > 0) slots = next_pow2(o.table_slots);
-    if (job.slots_hint > 0) slots = job.slots_hint;
-    P.slots = slots;
+    const double upper = std::min(m * pairs, (double)P.krange);
+    const double alpha = o.load_factor > 0.0 && o.load_factor <= 0.9 ? o.load_factor : DEFAULT_LOAD;
+    pl.bound_slots = next_pow2(std::max<int64_t>(1024, (int64_t)std::ceil(upper / alpha)));
     P.probe_limit = o.probe_limit > 0 ? o.probe_limit : DEFAULT_PROBES;
     P.tile_i = HASH_TILE_I;
     P.tile_j = HASH_TILE_J;
     P.tiles_j = ceil_div(ng, HASH_TILE_J);
     P.ntasks = ceil_div(nf, HASH_TILE_I) * P.tiles_j;
-    pl.accum_bytes = slots * 16;
     P.chunk = COMPACT_CHUNK;
-    P.nchunks = ceil_div(slots, P.chunk);
-    pl.out_cap = (int64_t)std::min((double)slots, est);
+    // table size, chunks and output capacity follow in finish_hash_sizes
   }
+}
+
+void finish_hash_sizes(const kr_opts& o, Plan* pl) {
+  Prod& P = pl->p;
+  const double m = P.nt > 0 ? 2.0 : 1.0;
+  const double upper = std::min(m * (double)P.f.n * (double)P.g.n, (double)P.krange);
+  const double alpha = o.load_factor > 0.0 && o.load_factor <= 0.9 ? o.load_factor : DEFAULT_LOAD;
+  int64_t slots;
+  if (pl->slots_override > 0) {
+    slots = pl->slots_override;
+  } else if (o.table_slots > 0) {
+    slots = next_pow2(o.table_slots);
+  } else {
+    const double est = P.hll_est > 0.0 ? std::min(P.hll_est * 1.05, upper) : upper;
+    slots = next_pow2(std::max<int64_t>(1024, (int64_t)std::ceil(est / alpha)));
+  }
+  P.slots = slots;
+  P.nchunks = ceil_div(slots, P.chunk);
+  pl->accum_bytes = slots * 16;
+  double cap = std::min((double)slots, upper);
+  // output room from the estimate (+10%, about six standard errors of the
+  // 4096-register HyperLogLog); the compaction flags an overflow and the
+  // product is rerun with room for a full table
+  if (P.hll_est > 0.0 && !pl->outcap_full) cap = std::min(cap, P.hll_est * 1.1 + 4096.0);
+  pl->out_cap = (int64_t)cap;
 }
 
 }  // namespace kr

@@ -34,7 +34,6 @@ struct Job {
   int np = 0, nt = 0;
   Operand f{}, g{};
   kr_opts opts{};
-  int64_t slots_hint = 0;   // hash table size forced by a regrow
 };
 
 // The result of planning: Prod filled except scratch pointers, plus sizes.
@@ -47,6 +46,8 @@ struct Plan {
   int64_t dense_task_cap = 0;
   int64_t radix_sort_n = 0;  // largest radix sort this product needs
   int64_t bound_slots = 0;   // hash: table size for the term-product bound at the load factor
+  int64_t slots_override = 0;  // hash: table size forced by a regrowth
+  bool outcap_full = false;    // hash: output room for a full table (after an overflow)
   int passes_f = 0, passes_g = 0;
 };
 
@@ -58,5 +59,9 @@ void plan_product(const Job& job, const int32_t* ranges_f, const int32_t* ranges
                   Plan* out);
 
 int bits_for(uint64_t range);   // bits needed for values in [0, range)
+
+// Hash path: table size and output capacity from the HyperLogLog estimate of
+// the distinct output keys (or a forced size), capped by the term-product bound.
+void finish_hash_sizes(const kr_opts& o, Plan* pl);
 
 }  // namespace kr

@@ -1,0 +1,204 @@
+"""Continuous-batching request loop over kron_mul_batch.
+
+Requests (pairs of series to multiply) arrive over time.  A dispatcher keeps a
+FIFO of arrived requests and, whenever a worker is free, admits the oldest
+ones into a batch as long as the batch's predicted scratch and output memory
+stays within the memory still free (the budget minus what batches already on
+the GPU hold).  Each worker owns a library context and a CUDA stream and runs
+its batch with one kron_mul_batch call; while it runs (the call releases the
+interpreter lock) the dispatcher forms and starts the next batch on another
+worker, so the batches' work overlaps on the device.  Results stay on the
+device: each request gets its own copy of its product (torch tensors).
+
+The memory prediction per product is the term-product count times 16 bytes
+times the observed ratio of output terms to term-products (updated after
+every batch, separately for polynomials and Poisson series), plus the dense
+array or hash table it needs.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import binding as B
+
+
+@dataclass
+class Request:
+    f: object
+    g: object
+    arrival: float            # seconds after the start of the run
+    start: float = -1.0
+    done: float = -1.0
+    result: dict | None = None
+    status: int = -1
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+    @property
+    def pairs(self) -> int:
+        return int(self.f.coef.shape[0]) * int(self.g.coef.shape[0])
+
+    @property
+    def poisson(self) -> bool:
+        return hasattr(self.f, "trig")
+
+
+@dataclass
+class ServeStats:
+    completed: int
+    wall_s: float
+    products_per_s: float
+    p50_ms: float
+    p99_ms: float
+    mean_batch: float
+    batches: int
+    rejected: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+class _Worker:
+    def __init__(self, device: int):
+        import torch
+        self.ctx = B.Context(device)
+        self.stream = torch.cuda.Stream(device=device)
+        self.busy = False
+        self.thread = None
+
+
+class Server:
+    """Continuous batching over `workers` contexts on one GPU."""
+
+    def __init__(self, device: int = 0, workers: int = 2, mem_budget: float = 64e9,
+                 max_batch: int = 256, wave_pairs: int = 0):
+        self.device = device
+        self.workers = [_Worker(device) for _ in range(workers)]
+        self.mem_budget = mem_budget
+        self.max_batch = max_batch
+        self.wave_pairs = wave_pairs
+        self.ratio = {False: 0.3, True: 1.0}   # output terms per term-product, learned
+        self.lock = threading.Lock()
+        self.in_flight_bytes = 0.0
+
+    def predict_bytes(self, r: Request) -> float:
+        out_terms = r.pairs * self.ratio[r.poisson]
+        # output (16 B) + ordering scratch (16 B) + table at load 0.5 (32 B) per term
+        return 64.0 * out_terms + 1e6
+
+    def _run_batch(self, w: _Worker, batch: list[Request], t0: float, bytes_: float):
+        import torch
+        try:
+            with torch.cuda.stream(w.stream):
+                now = time.perf_counter() - t0
+                for r in batch:
+                    r.start = now
+                out = B.kron_mul_batch([(r.f, r.g) for r in batch], ctx=w.ctx, stream=w.stream,
+                                       wave_pairs=self.wave_pairs)
+                # results are library-owned until the context's next batch: copy them out
+                for r, o in zip(batch, out):
+                    r.status = o["status"]
+                    r.result = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in o.items()}
+                w.stream.synchronize()
+            done = time.perf_counter() - t0
+            obs = {False: [0, 0], True: [0, 0]}
+            for r, o in zip(batch, out):
+                r.done = done
+                obs[r.poisson][0] += o["nterms"]
+                obs[r.poisson][1] += r.pairs
+            with self.lock:
+                for k, (n, p) in obs.items():
+                    if p > 0:
+                        self.ratio[k] = 0.7 * self.ratio[k] + 0.3 * max(n / p, 1e-4)
+        finally:
+            with self.lock:
+                self.in_flight_bytes -= bytes_
+                w.busy = False
+
+    def run(self, requests: list[Request], time_limit: float = 120.0) -> ServeStats:
+        """Serve requests (sorted by arrival) until all are done or time_limit passes."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        pending: list[Request] = []
+        nxt = 0
+        batches = 0
+        sizes = []
+        t0 = time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt].arrival <= now:
+                pending.append(reqs[nxt])
+                nxt += 1
+            if nxt >= len(reqs) and not pending and all(not w.busy for w in self.workers):
+                break
+            if now > time_limit:
+                break
+            free = [w for w in self.workers if not w.busy]
+            if pending and free:
+                with self.lock:
+                    room = self.mem_budget - self.in_flight_bytes
+                batch, used = [], 0.0
+                for r in pending:
+                    b = self.predict_bytes(r)
+                    if batch and (used + b > room or len(batch) >= self.max_batch):
+                        break
+                    if not batch and b > room and self.in_flight_bytes > 0:
+                        break   # wait for memory to come back
+                    batch.append(r)
+                    used += b
+                if batch:
+                    pending = pending[len(batch):]
+                    w = free[0]
+                    with self.lock:
+                        w.busy = True
+                        self.in_flight_bytes += used
+                    w.thread = threading.Thread(target=self._run_batch, args=(w, batch, t0, used))
+                    w.thread.start()
+                    batches += 1
+                    sizes.append(len(batch))
+                    continue
+            if not pending and nxt < len(reqs):
+                time.sleep(max(0.0, min(reqs[nxt].arrival - now, 0.002)))
+            else:
+                time.sleep(0.0002)
+        for w in self.workers:
+            if w.thread is not None:
+                w.thread.join()
+        wall = time.perf_counter() - t0
+        done = [r for r in reqs if r.done >= 0]
+        lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+        return ServeStats(completed=len(done), wall_s=wall,
+                          products_per_s=len(done) / wall if wall > 0 else 0.0,
+                          p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                          mean_batch=float(np.mean(sizes)) if sizes else 0.0, batches=batches,
+                          rejected=len(reqs) - len(done))
+
+
+def serve_one_by_one(requests: list[Request], device: int = 0, time_limit: float = 120.0) -> ServeStats:
+    """The baseline: one poly_mul / poisson_mul call per request, in arrival order."""
+    ctx = B.Context(device)
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    t0 = time.perf_counter()
+    for r in reqs:
+        now = time.perf_counter() - t0
+        if now > time_limit:
+            break
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        r.start = time.perf_counter() - t0
+        if r.poisson:
+            out = B.poisson_mul(r.f, r.g, ctx=ctx)
+        else:
+            out = B.poly_mul(r.f.exps, r.f.coef, r.g.exps, r.g.coef, ctx=ctx)
+        r.result = out
+        r.status = 0
+        r.done = time.perf_counter() - t0
+    wall = time.perf_counter() - t0
+    done = [r for r in reqs if r.done >= 0]
+    lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+    return ServeStats(completed=len(done), wall_s=wall, products_per_s=len(done) / wall if wall > 0 else 0.0,
+                      p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
+                      mean_batch=1.0, batches=len(done), rejected=len(reqs) - len(done))

@@ -1,0 +1,115 @@
+"""The batched entry point: every product of a mixed batch equals the same
+product multiplied alone (int64 bit-exact; float64 Poisson products within
+1e-12 of the summed magnitudes against the oracle), across wave splits and
+with invalid or empty jobs in the mix."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_compare import assert_poly_equal, assert_pseries_close, to_np
+from workloads import PSeries, Poly, batch_mix, random_poly
+
+pytestmark = pytest.mark.gpu
+NT = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def kron():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1004_4548_gb300 as k
+    k.load()
+    return k
+
+
+@pytest.fixture(scope="module")
+def mix():
+    return batch_mix(96, seed_base=5000, max_terms=700)
+
+
+def _alone(kron, f, g):
+    if isinstance(f, PSeries):
+        e, t, k, c, _ = kron.poisson_mul(f, g, host_out=True)
+        return to_np(e), to_np(t), to_np(k), to_np(c)
+    e, c, _, _ = kron.poly_mul(f.exps, f.coef, g.exps, g.coef, host_out=True)
+    return to_np(e), to_np(c)
+
+
+def _check_batch(kron, mix, out, what):
+    for i, ((f, g), r) in enumerate(zip(mix, out)):
+        assert r["status"] == 0, f"{what}: product {i} status {r['status']}"
+        if isinstance(f, PSeries):
+            ro = oracle.poisson_mul(f, g, nthreads=NT, keep_zero=True)
+            assert_pseries_close((r["exps"], r["trig"], r["kind"], r["coef"]), ro, 1e-12,
+                                 f"{what} product {i}")
+        else:
+            e, c = _alone(kron, f, g)
+            assert np.array_equal(to_np(r["exps"]), e) and np.array_equal(to_np(r["coef"]), c), \
+                f"{what}: product {i} differs from the product alone"
+
+
+def test_batch_equals_alone(kron, mix):
+    out = kron.kron_mul_batch(mix)
+    _check_batch(kron, mix, out, "one wave")
+
+
+def test_batch_waves(kron, mix):
+    out = kron.kron_mul_batch(mix, wave_pairs=2_000_000)
+    _check_batch(kron, mix[:48], out[:48], "small waves")
+
+
+def test_batch_arrival_order_does_not_matter(kron, mix):
+    perm = np.random.default_rng(5).permutation(len(mix))
+    a = kron.kron_mul_batch(mix)
+    a = [(to_np(r["exps"]), to_np(r["coef"])) for r in a]
+    b = kron.kron_mul_batch([mix[i] for i in perm])
+    for j, i in enumerate(perm):
+        f, _ = mix[i]
+        if isinstance(f, Poly):
+            assert np.array_equal(to_np(b[j]["exps"]), a[i][0])
+            assert np.array_equal(to_np(b[j]["coef"]), a[i][1])
+
+
+def test_batch_per_job_errors(kron):
+    f = random_poly(3, 200, -4, 4, 71)
+    g = random_poly(3, 150, -4, 4, 72)
+    bad = Poly(np.concatenate([f.exps, f.exps[:, :1]], axis=1), np.concatenate([f.coef, f.coef[:1]]))
+    empty = Poly(np.zeros((3, 0), np.int32), np.zeros(0, np.int64))
+    out = kron.kron_mul_batch([(f, g), (bad, g), (empty, g), (g, f)])
+    assert out[0]["status"] == 0 and out[3]["status"] == 0
+    assert out[1]["status"] == kron.KR_ERR_DUP
+    assert out[2]["status"] == 0 and out[2]["nterms"] == 0
+    r = oracle.poly_mul(f, g)
+    assert_poly_equal(out[0]["exps"], out[0]["coef"], r, "beside failing jobs")
+    assert_poly_equal(out[3]["exps"], out[3]["coef"], r, "commuted")
+
+
+def test_served_results_equal_alone(kron):
+    """Requests served by the continuous-batching loop (two workers, batches
+    overlapping on the GPU) return the same products as one call each."""
+    import torch
+    from paper_1004_4548_gb300.serve import Request, Server
+    from workloads import arrival_times
+    mix = batch_mix(40, seed_base=7000, max_terms=400)
+
+    def dev(p):
+        if isinstance(p, PSeries):
+            return PSeries(*(torch.from_numpy(x).cuda() for x in (p.exps, p.trig, p.kind, p.coef)))
+        return Poly(torch.from_numpy(p.exps).cuda(), torch.from_numpy(p.coef).cuda())
+
+    t = arrival_times(len(mix), rate=400.0, seed=11)
+    reqs = [Request(dev(f), dev(g), float(a)) for (f, g), a in zip(mix, t)]
+    stats = Server(workers=2, max_batch=8, mem_budget=8e9).run(reqs, time_limit=60.0)
+    assert stats.completed == len(mix) and stats.batches >= 2
+    for i, ((f, g), r) in enumerate(zip(mix, reqs)):
+        assert r.status == 0
+        if isinstance(f, PSeries):
+            ro = oracle.poisson_mul(f, g, nthreads=NT, keep_zero=True)
+            o = r.result
+            assert_pseries_close((o["exps"], o["trig"], o["kind"], o["coef"]), ro, 1e-12, f"served {i}")
+        else:
+            e, c = _alone(kron, f, g)
+            assert np.array_equal(to_np(r.result["exps"]), e) and np.array_equal(to_np(r.result["coef"]), c)
