@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary hash/Poisson lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiler runs)")
     ap.add_argument("--block-slots", type=int, default=0, help="dense output block size (0 = library default)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched / served measurements")
+    ap.add_argument("--batch-products", type=int, default=4096, help="products in the uneven batch")
     return ap.parse_args()
 
 
@@ -304,6 +306,10 @@ def main():
         paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3)
         ctx.set_profiling(False)
 
+    batched = None
+    if not args.no_batch:
+        batched = time_batched(kron, ctx, dev, args.batch_products)
+
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -319,12 +325,114 @@ def main():
                 "wall_s_timed": wall,
                 "sm_cycles_per_term_product": (clk["sm_mhz"] * 1e6 * ms * 1e-3 / tp * 152)
                 if clk.get("sm_mhz") else None,
-                "paths": paths}
+                "paths": paths,
+                "batched": batched}
         line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(f, g)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def time_batched(kron, ctx, dev, nprod):
+    """The uneven batch (BASELINE configs[4]): batched in chunks vs one call per
+    product, and the continuous-batching server vs one-by-one service under
+    Poisson arrivals."""
+    import torch
+    from paper_1004_4548_gb300.serve import Request, Server, serve_one_by_one
+    from workloads import PSeries, Poly, arrival_times, batch_mix
+    mix = batch_mix(nprod)
+
+    def todev(p):
+        if isinstance(p, PSeries):
+            return PSeries(*(torch.from_numpy(x).to(dev) for x in (p.exps, p.trig, p.kind, p.coef)))
+        return Poly(torch.from_numpy(p.exps).to(dev), torch.from_numpy(p.coef).to(dev))
+
+    D = [(todev(f), todev(g)) for f, g in mix]
+    tp = sum(f.n * g.n for f, g in mix)
+    chunk = 128
+    kron.kron_mul_batch(D[:chunk], ctx=ctx)          # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    outputs = 0
+    launches0 = ctx.launch_count()
+    for a in range(0, nprod, chunk):
+        out = kron.kron_mul_batch(D[a:a + chunk], ctx=ctx)
+        outputs += sum(r["nterms"] for r in out)
+        assert all(r["status"] == 0 for r in out)
+    torch.cuda.synchronize()
+    bt = time.perf_counter() - t
+    b_launches = ctx.launch_count() - launches0
+    # one call per product
+    t = time.perf_counter()
+    lat = []
+    launches0 = ctx.launch_count()
+    for f, g in D:
+        t0 = time.perf_counter()
+        if isinstance(f, PSeries):
+            kron.poisson_mul(f, g, ctx=ctx)
+        else:
+            kron.poly_mul(f.exps, f.coef, g.exps, g.coef, ctx=ctx)
+        lat.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    pt = time.perf_counter() - t
+    p_launches = ctx.launch_count() - launches0
+    res = {"workload": f"{nprod} products, operands log-uniform 50-20000 terms, 2-6 variables, "
+                       "dense or weighted total-degree structure, half int64 polynomials and half "
+                       "float64 Poisson series (seeds 5000+k)",
+           "term_products": tp, "output_terms": outputs,
+           "batched": {"products_per_s": nprod / bt, "M_term_products_per_s": tp / bt / 1e6,
+                       "wall_s": bt, "chunk": chunk, "gpu_launches": b_launches},
+           "one_call_per_product": {"products_per_s": nprod / pt, "M_term_products_per_s": tp / pt / 1e6,
+                                    "wall_s": pt, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                                    "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                                    "gpu_launches": p_launches}}
+    # CUDA graph replay of prepared batches against kron_mul_batch, same chunks
+    graph = {"chunks": 0, "replay_s": 0.0, "batch_call_s": 0.0, "products": 0}
+    for a in range(0, min(nprod, 512), chunk):
+        part = D[a:a + chunk]
+        pb = kron.PreparedBatch(part, device=dev.index or 0)
+        pb.launch()
+        torch.cuda.synchronize()
+        reps = 3
+        t = time.perf_counter()
+        for _ in range(reps):
+            pb.launch()
+        torch.cuda.synchronize()
+        graph["replay_s"] += (time.perf_counter() - t) / reps
+        assert all(r["status"] == 0 for r in pb.results())
+        pb.close()
+        t = time.perf_counter()
+        for _ in range(reps):
+            kron.kron_mul_batch(part, ctx=ctx)
+        torch.cuda.synchronize()
+        graph["batch_call_s"] += (time.perf_counter() - t) / reps
+        graph["chunks"] += 1
+        graph["products"] += len(part)
+    graph["replay_products_per_s"] = graph["products"] / graph["replay_s"]
+    graph["batch_call_products_per_s"] = graph["products"] / graph["batch_call_s"]
+    res["cuda_graph"] = graph
+    # serving: Poisson arrivals at 0.5 and 0.8 of the batched throughput
+    serve = {}
+    cap = nprod / bt
+    nreq = min(nprod, 2048)
+    for frac in (0.5, 0.8):
+        rate = frac * cap
+        t_arr = arrival_times(nreq, rate, seed=99)
+        reqs = [Request(f, g, float(a)) for (f, g), a in zip(D[:nreq], t_arr)]
+        st = Server(device=dev.index or 0, workers=2, max_batch=chunk, mem_budget=60e9).run(reqs, time_limit=60.0)
+        reqs1 = [Request(f, g, float(a)) for (f, g), a in zip(D[:nreq], t_arr)]
+        st1 = serve_one_by_one(reqs1, device=dev.index or 0, time_limit=min(60.0, float(t_arr[-1]) * 1.5 + 5))
+        serve[f"rate_{frac}"] = {
+            "arrival_rate_per_s": rate, "requests": nreq,
+            "continuous_batching": {"completed": st.completed, "products_per_s": st.products_per_s,
+                                    "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_batch": st.mean_batch,
+                                    "batches": st.batches, "failed": st.extra.get("failed", 0)},
+            "one_by_one": {"completed": st1.completed, "products_per_s": st1.products_per_s,
+                           "p50_ms": st1.p50_ms, "p99_ms": st1.p99_ms,
+                           "note": "requests still queued at the time limit are not counted"}}
+    res["serving"] = serve
+    return res
 
 
 def time_poly(kron, ctx, f, g, dev, stream, flush, kernel, steps):

@@ -242,6 +242,28 @@ typedef struct {
 kr_status kron_mul_batch(kr_ctx* ctx, const kr_job* jobs, int32_t njobs, kr_result* res,
                          int64_t wave_pairs, kr_stream stream);
 
+/* A batch prepared for repeated execution with a CUDA graph.  The first run
+ * plans every product (coding boxes, paths, table sizes from the distinct-key
+ * estimates, output counts) with scratch owned by the batch; the complete
+ * device work of a run (encode, sorts, accumulation, compaction, ordering,
+ * decode) is then captured into one CUDA graph.  Launching the batch replays
+ * the graph without host planning or synchronisation.  Inputs must be device
+ * buffers that keep their exponents, kinds and sizes between launches; the
+ * coefficients may change.  res (optional, njobs entries) receives the first
+ * run's results; result arrays are owned by the batch and overwritten by
+ * every launch.  The batch holds its scratch until destroyed. */
+typedef struct kr_batch kr_batch;
+kr_status kron_batch_prepare(int32_t device, const kr_job* jobs, int32_t njobs, kr_batch** out,
+                             kr_result* res, kr_stream stream);
+/* Replays the batch on `stream` (asynchronous). */
+kr_status kron_batch_launch(kr_batch* b, kr_stream stream);
+/* After the launch's stream has been synchronised: statuses and result
+ * pointers.  A product whose term count differs from the prepared run (its
+ * coefficients now cancel differently) reports KR_ERR_CAPACITY; prepare the
+ * batch again for it. */
+kr_status kron_batch_results(kr_batch* b, kr_result* res, int32_t njobs);
+void kron_batch_destroy(kr_batch* b);
+
 /* Copy the product kept by the last poly_mul / poisson_mul of this context
  * (after KR_ERR_CAPACITY) into h.  KR_ERR_INVALID if there is none. */
 kr_status kron_fetch_poly(kr_ctx* ctx, kr_poly_out* h, kr_stream stream);

@@ -84,6 +84,11 @@ SIGNATURES = {
                                    ctypes.POINTER(kr_pseries_out), ctypes.POINTER(kr_opts), _vp]),
     "kron_fetch_poly": (ctypes.c_int, [_vp, ctypes.POINTER(kr_poly_out), _vp]),
     "kron_mul_batch": (ctypes.c_int, [_vp, ctypes.POINTER(kr_job), _i32, ctypes.POINTER(kr_result), _i64, _vp]),
+    "kron_batch_prepare": (ctypes.c_int, [_i32, ctypes.POINTER(kr_job), _i32, ctypes.POINTER(_vp),
+                                          ctypes.POINTER(kr_result), _vp]),
+    "kron_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "kron_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(kr_result), _i32]),
+    "kron_batch_destroy": (None, [_vp]),
     "kron_fetch_pseries": (ctypes.c_int, [_vp, ctypes.POINTER(kr_pseries_out), _vp]),
 }
 
@@ -414,8 +419,16 @@ def kron_mul_batch(pairs, ctx: Context | None = None, stream=None, wave_pairs: i
     """
     ctx = ctx or context()
     n = len(pairs)
-    jobs = (kr_job * max(1, n))()
+    jobs, keep = _make_jobs(pairs, opts)
     res = (kr_result * max(1, n))()
+    st = ctx.L.kron_mul_batch(ctx.h, jobs, n, res, int(wave_pairs), _stream_ptr(stream))
+    _check(ctx.L, ctx.h, st, "kron_mul_batch")
+    return _results(jobs, res, n, ctx.device)
+
+
+def _make_jobs(pairs, opts):
+    n = len(pairs)
+    jobs = (kr_job * max(1, n))()
     keep = []
     for i, (f, g) in enumerate(pairs):
         o = opts[i] if isinstance(opts, (list, tuple)) else (opts or {})
@@ -443,22 +456,66 @@ def kron_mul_batch(pairs, ctx: Context | None = None, stream=None, wave_pairs: i
             jobs[i].kind = 0
             jobs[i].f = desc(f)
             jobs[i].g = desc(g)
-    st = ctx.L.kron_mul_batch(ctx.h, jobs, n, res, int(wave_pairs), _stream_ptr(stream))
-    _check(ctx.L, ctx.h, st, "kron_mul_batch")
+    return jobs, keep
+
+
+def _results(jobs, res, n, device):
     out = []
-    for i, (f, g) in enumerate(pairs):
+    for i in range(n):
         r = res[i]
         m = int(r.nterms)
         d = {"status": int(r.status), "path": int(r.path), "nterms": m}
         if jobs[i].kind == 1:
             npl, nt = jobs[i].pf.npoly, jobs[i].pf.ntrig
-            d["exps"] = _view(r.exps, (npl, m), "<i4", ctx.device)
-            d["trig"] = _view(r.trig, (nt, m), "<i4", ctx.device)
-            d["kind"] = _view(r.kind, (m,), "|u1", ctx.device)
-            d["coef"] = _view(r.coef, (m,), "<f8", ctx.device)
+            d["exps"] = _view(r.exps, (npl, m), "<i4", device)
+            d["trig"] = _view(r.trig, (nt, m), "<i4", device)
+            d["kind"] = _view(r.kind, (m,), "|u1", device)
+            d["coef"] = _view(r.coef, (m,), "<f8", device)
         else:
             nv = jobs[i].f.nvars
-            d["exps"] = _view(r.exps, (nv, m), "<i4", ctx.device)
-            d["coef"] = _view(r.coef, (m,), "<f8" if jobs[i].f.type == KR_F64 else "<i8", ctx.device)
+            d["exps"] = _view(r.exps, (nv, m), "<i4", device)
+            d["coef"] = _view(r.coef, (m,), "<f8" if jobs[i].f.type == KR_F64 else "<i8", device)
         out.append(d)
     return out
+
+
+class PreparedBatch:
+    """A batch captured into a CUDA graph (kron_batch_prepare).
+
+    The operands must be CUDA tensors whose exponents stay fixed; their
+    coefficients may be changed in place between launches.
+    """
+
+    def __init__(self, pairs, device: int = 0, stream=None, opts=None):
+        self.L = load()
+        self.n = len(pairs)
+        self.device = device
+        self.jobs, self._keep = _make_jobs(pairs, opts)
+        self._res = (kr_result * max(1, self.n))()
+        h = _vp()
+        st = self.L.kron_batch_prepare(device, self.jobs, self.n, ctypes.byref(h), self._res, _stream_ptr(stream))
+        _check(self.L, None, st, "kron_batch_prepare")
+        self.h = h
+
+    def first_results(self):
+        return _results(self.jobs, self._res, self.n, self.device)
+
+    def launch(self, stream=None):
+        _check(self.L, None, self.L.kron_batch_launch(self.h, _stream_ptr(stream)), "kron_batch_launch")
+
+    def results(self):
+        """Statuses and device views after the launch's stream has been synchronised."""
+        res = (kr_result * max(1, self.n))()
+        _check(self.L, None, self.L.kron_batch_results(self.h, res, self.n), "kron_batch_results")
+        return _results(self.jobs, res, self.n, self.device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.kron_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -30,6 +30,9 @@ struct kr_ctx {
   size_t acc_cap = 0;
   std::vector<Plan> plans;   // plans of the last pipeline run
   std::vector<void*> batch_blocks;   // result memory of the last kron_mul_batch
+  // replay (prepared batches): run the device work of the saved plans again,
+  // without host planning or synchronisation, so that it can be captured
+  bool replay = false;
   void* pinned = nullptr;
   size_t pinned_cap = 0;
   // product kept after the last multiplication (for kron_fetch_*)
@@ -197,6 +200,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   const int nops = 2 * nprod;
   std::vector<Job> jobs(nprod);
   // ---------------- phase A: staged inputs, metadata, range scan
+  if (ctx->replay) {
+    for (int p = 0; p < nprod; ++p) res[p].st = ctx->plans[p].st;
+  } else {
   Prod* dprods = nullptr;
   OpRef* dops = nullptr;
   int32_t* dranges = nullptr;
@@ -265,6 +271,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       res[p].st = ctx->plans[p].st;
     }
   }
+  }   // phase A
   std::vector<Plan>& plans = ctx->plans;
   std::vector<int> live_ids, dense_ids, hash_ids;
   for (int p = 0; p < nprod; ++p) {
@@ -427,6 +434,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   if (!hash_ids.empty()) {
     bool need_hll = false;
     for (int p : hash_ids) need_hll |= ins[p].opts.table_slots <= 0;
+    if (ctx->replay) need_hll = false;   // table sizes are fixed by the prepared run
     if (need_hll) {
       ck(ctx, launch_hll(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(), ctx->num_sms * 8, s),
          "hll");
@@ -435,13 +443,15 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       mark(ctx, s, "hll");
     }
   }
-  ck(ctx, cudaMemcpyAsync(hl, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
-  ck(ctx, cudaStreamSynchronize(s), "sync b1");
-  collect_stages(ctx);
-  for (int q = 0; q < nlive; ++q) {
-    Plan& pl = plans[live_ids[q]];
-    pl.p.status = hl[q].status;
-    pl.p.hll_est = hl[q].hll_est;
+  if (!ctx->replay) {
+    ck(ctx, cudaMemcpyAsync(hl, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
+    ck(ctx, cudaStreamSynchronize(s), "sync b1");
+    collect_stages(ctx);
+    for (int q = 0; q < nlive; ++q) {
+      Plan& pl = plans[live_ids[q]];
+      pl.p.status = hl[q].status;
+      pl.p.hll_est = hl[q].hll_est;
+    }
   }
   // ---------------- phase B2, repeated for products whose table filled up
   std::vector<int> regrows(nprod, 0);
@@ -452,7 +462,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       finish_hash_sizes(ins[p].opts, &pl);
       max_hash_out = std::max(max_hash_out, pl.out_cap);
       const int64_t nb = order_bins(pl.p.krange);
-      if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, 2 * (nb + 1));
+      if (pl.p.krange <= ORDER_BITMAP_MAX)
+        bins_total = std::max(bins_total, (order_bitmap_bytes(pl.p.krange) + 7) / 8);
+      else if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, 2 * (nb + 1));
       else scan_b2 = std::max(scan_b2, radix_scan_entries(pl.out_cap));
     }
     std::vector<int64_t> h_chunk_begin(nlive + 1, 0);
@@ -493,7 +505,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Z.zero_bytes = b.off - zero_start;
       if (!pass) ensure(ctx, &ctx->acc, &ctx->acc_cap, b.off + 1, s);
     }
-    Bump hb2(ctx->pinned);
+    // a replay is captured without synchronisation: its B2 staging must not
+    // overwrite B1's, so it continues after it
+    Bump hb2 = ctx->replay ? hb : Bump(ctx->pinned);
     Prod* hl2 = hb2.take<Prod>(nlive);
     for (int q = 0; q < nlive; ++q) hl2[q] = plans[live_ids[q]].p;
     ck(ctx, cudaMemcpyAsync(A.lprods, hl2, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
@@ -530,23 +544,29 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
        "compaction");
     ctx->launches += nchunks_total > 0 ? 4 : 1;
     mark(ctx, s, "compact");
-    ck(ctx, cudaMemcpyAsync(hl2, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
-    ck(ctx, cudaStreamSynchronize(s), "sync results");
-    collect_stages(ctx);
+    if (ctx->replay) {
+      // counts and positions of the prepared run (the replayed compaction
+      // writes the same ones; the caller verifies after the launch)
+      for (int q = 0; q < nlive; ++q) hl2[q] = plans[live_ids[q]].p;
+    } else {
+      ck(ctx, cudaMemcpyAsync(hl2, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
+      ck(ctx, cudaStreamSynchronize(s), "sync results");
+      collect_stages(ctx);
+    }
     bool retry = false;
     for (int q = 0; q < nlive; ++q) {
       const int p = live_ids[q];
       Prod& P = hl2[q];
       plans[p].p.nout = P.nout;
       plans[p].p.out_start = P.out_start;
-      if ((P.status & ST_OUTCAP) && !(P.status & ~ST_OUTCAP) && !plans[p].outcap_full) {
+      if (!ctx->replay && (P.status & ST_OUTCAP) && !(P.status & ~ST_OUTCAP) && !plans[p].outcap_full) {
         // the estimate fell short: rerun with room for a full table
         plans[p].outcap_full = true;
         plans[p].p.status = 0;
         retry = true;
         continue;
       }
-      if (P.status & ST_TABLE_FULL) {
+      if (!ctx->replay && (P.status & ST_TABLE_FULL)) {
         const int mr = ins[p].opts.max_regrow;
         const int allowed = mr > 0 ? mr : (mr < 0 ? 0 : 4);
         const int64_t bound = plans[p].bound_slots;
@@ -577,7 +597,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       uint64_t* v = Z.oval + r.prod.out_start;
       uint64_t* k2 = Z.okey2;
       uint64_t* v2 = Z.oval2;
-      if (order_bins(r.prod.krange) <= ORDER_MAX_BINS) {
+      if (r.prod.krange <= ORDER_BITMAP_MAX) {
+        ck(ctx, order_by_bitmap(k, v, k2, v2, r.n, r.prod.krange, Z.bins, s), "output order");
+        ck(ctx, cudaMemcpyAsync(k, k2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
+        ck(ctx, cudaMemcpyAsync(v, v2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
+        ctx->launches += 4;
+      } else if (order_bins(r.prod.krange) <= ORDER_MAX_BINS) {
         ck(ctx, order_by_bins(k, v, k2, v2, r.n, r.prod.krange, Z.bins, s), "output order");
         ctx->launches += 4;
       } else {
@@ -1152,6 +1177,194 @@ kr_status kron_mul_batch(kr_ctx* ctx, const kr_job* jobs, int32_t njobs, kr_resu
     }
     return KR_OK;
   });
+}
+
+}  // extern "C"
+
+// A prepared batch: its own context (scratch that never moves), the plans of
+// its first run, the result memory, and the CUDA graph of the device work.
+struct kr_batch {
+  kr_ctx* ctx = nullptr;
+  std::vector<JobIn> ins;
+  std::vector<int> idx;
+  std::vector<kr_result> res;     // per job, from the prepared run
+  std::vector<int> live;          // JobIn index of each decoded product, device order
+  std::vector<int64_t> nout;      // expected terms per decoded product
+  void* block = nullptr;          // decoded results, ResDesc array, offsets
+  const Prod* dprods = nullptr;
+  ResDesc* d_rd = nullptr;
+  int64_t* d_ost = nullptr;
+  const uint64_t* okey = nullptr;
+  const uint64_t* oval = nullptr;
+  int64_t total = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+kr_status kron_batch_prepare(int32_t device, const kr_job* jobs, int32_t njobs, kr_batch** out,
+                             kr_result* res, kr_stream stream) {
+  if (!out || njobs < 1 || !jobs) return KR_ERR_INVALID;
+  *out = nullptr;
+  kr_ctx* ictx = nullptr;
+  kr_status st = kr_ctx_create(device, &ictx);
+  if (st != KR_OK) return st;
+  kr_batch* b = new (std::nothrow) kr_batch;
+  if (!b) { kr_ctx_destroy(ictx); return KR_ERR_OOM; }
+  b->ctx = ictx;
+  b->res.assign(njobs, kr_result{});
+  st = guarded(ictx, [&]() -> kr_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    // inputs: device buffers only (the graph reads them in place)
+    for (int i = 0; i < njobs; ++i) {
+      const kr_job& J = jobs[i];
+      JobIn in;
+      auto dev_or_null = [](const void* p) { return !p || is_device_ptr(p); };
+      if (J.kind == 0 && poly_job_ok(&J.f, &J.g) && J.f.nterms > 0 && J.g.nterms > 0) {
+        if (!dev_or_null(J.f.exps) || !dev_or_null(J.f.coef) || !dev_or_null(J.g.exps) || !dev_or_null(J.g.coef))
+          return KR_ERR_INVALID;
+        in.f64 = J.f.type == KR_F64;
+        in.np = J.f.nvars;
+        in.fe = J.f.exps; in.fc = J.f.coef; in.nf = J.f.nterms;
+        in.ge = J.g.exps; in.gc = J.g.coef; in.ng = J.g.nterms;
+      } else if (J.kind == 1 && pseries_job_ok(&J.pf, &J.pg) && J.pf.nterms > 0 && J.pg.nterms > 0 &&
+                 J.opts.path != KR_PATH_DENSE) {
+        for (const void* p : {(const void*)J.pf.exps, (const void*)J.pf.trig, (const void*)J.pf.kind,
+                              (const void*)J.pf.coef, (const void*)J.pg.exps, (const void*)J.pg.trig,
+                              (const void*)J.pg.kind, (const void*)J.pg.coef})
+          if (!dev_or_null(p)) return KR_ERR_INVALID;
+        in.poisson = true;
+        in.f64 = true;
+        in.np = J.pf.npoly;
+        in.nt = J.pf.ntrig;
+        in.fe = J.pf.exps; in.ft = J.pf.trig; in.fk = J.pf.kind; in.fc = J.pf.coef; in.nf = J.pf.nterms;
+        in.ge = J.pg.exps; in.gt = J.pg.trig; in.gk = J.pg.kind; in.gc = J.pg.coef; in.ng = J.pg.nterms;
+      } else {
+        b->res[i].status = KR_ERR_INVALID;   // empty or invalid: nothing to replay
+        if ((J.kind == 0 && poly_job_ok(&J.f, &J.g)) || (J.kind == 1 && pseries_job_ok(&J.pf, &J.pg)))
+          b->res[i].status = KR_OK;
+        continue;
+      }
+      in.opts = J.opts;
+      b->ins.push_back(in);
+      b->idx.push_back(i);
+    }
+    if (b->ins.empty()) return KR_OK;
+    // the prepared run
+    std::vector<ProdResult> pr;
+    run_pipeline(ictx, b->ins, s, pr);
+    std::vector<int> order;
+    for (int p = 0; p < (int)b->ins.size(); ++p)
+      if (pr[p].dprod) order.push_back(p);
+    std::sort(order.begin(), order.end(), [&](int a, int c) { return pr[a].dprod < pr[c].dprod; });
+    const int nl = (int)order.size();
+    size_t bytes = sizeof(ResDesc) * (nl + 1) + 8 * (nl + 2) + 512;
+    for (int p : order) bytes += (size_t)pr[p].n * (4 * (pr[p].prod.np + pr[p].prod.nt) + 1 + 8) + 4 * 256;
+    ck(ictx, cudaMalloc(&b->block, bytes), "cudaMalloc results");
+    Bump bb(b->block);
+    b->d_rd = bb.take<ResDesc>(nl);
+    b->d_ost = bb.take<int64_t>(nl + 1);
+    std::vector<ResDesc> rd(nl);
+    std::vector<int64_t> ost(nl + 1, 0);
+    for (int q = 0; q < nl; ++q) {
+      const ProdResult& r = pr[order[q]];
+      const int64_t n = r.st == KR_OK ? r.n : 0;
+      rd[q].n = n;
+      rd[q].coef = (void*)bb.take<uint64_t>(n);
+      rd[q].exps = bb.take<int32_t>(n * r.prod.np);
+      rd[q].trig = r.prod.nt ? bb.take<int32_t>(n * r.prod.nt) : nullptr;
+      rd[q].kind = r.prod.nt ? bb.take<uint8_t>(n) : nullptr;
+      ost[q] = r.prod.out_start;
+      b->total = r.prod.out_start + r.n;
+      b->live.push_back(order[q]);
+      b->nout.push_back(r.n);
+      kr_result& R = b->res[b->idx[order[q]]];
+      R.status = r.st;
+      R.path = r.prod.path == PATH_DENSE ? KR_PATH_DENSE : KR_PATH_HASH;
+      R.nterms = n;
+      R.exps = rd[q].exps; R.trig = rd[q].trig; R.kind = rd[q].kind; R.coef = rd[q].coef;
+    }
+    ost[nl] = b->total;
+    for (int p = 0; p < (int)b->ins.size(); ++p)
+      if (!pr[p].dprod) b->res[b->idx[p]].status = pr[p].st;
+    if (nl == 0) return KR_OK;
+    ck(ictx, cudaMemcpy(b->d_rd, rd.data(), sizeof(ResDesc) * nl, cudaMemcpyHostToDevice), "upload");
+    ck(ictx, cudaMemcpy(b->d_ost, ost.data(), 8 * (size_t)(nl + 1), cudaMemcpyHostToDevice), "upload");
+    b->dprods = pr[order[0]].dprod;
+    b->okey = pr[order[0]].key - pr[order[0]].prod.out_start;
+    b->oval = pr[order[0]].val - pr[order[0]].prod.out_start;
+    ck(ictx, launch_decode_batch(b->dprods, nl, b->d_ost, b->d_rd, b->okey, b->oval, b->total, s),
+       "batched decode");
+    ck(ictx, cudaStreamSynchronize(s), "sync");
+    // capture the device work of a replay into a graph
+    ensure_pinned(ictx, ictx->pinned_cap * 2 + (1 << 20), s);
+    ck(ictx, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream");
+    ck(ictx, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture");
+    ictx->replay = true;
+    try {
+      std::vector<ProdResult> pr2;
+      run_pipeline(ictx, b->ins, b->cap_stream, pr2);
+      ck(ictx, launch_decode_batch(b->dprods, nl, b->d_ost, b->d_rd, b->okey, b->oval, b->total,
+                                   b->cap_stream), "batched decode");
+    } catch (...) {
+      ictx->replay = false;
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(b->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    ictx->replay = false;
+    ck(ictx, cudaStreamEndCapture(b->cap_stream, &b->graph), "end capture");
+    ck(ictx, cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+    return KR_OK;
+  });
+  if (st != KR_OK) {
+    kron_batch_destroy(b);
+    return st;
+  }
+  if (res)
+    for (int i = 0; i < njobs; ++i) res[i] = b->res[i];
+  *out = b;
+  return KR_OK;
+}
+
+kr_status kron_batch_launch(kr_batch* b, kr_stream stream) {
+  if (!b) return KR_ERR_INVALID;
+  if (!b->exec) return KR_OK;   // nothing to recompute
+  return guarded(b->ctx, [&]() -> kr_status {
+    ck(b->ctx, cudaGraphLaunch(b->exec, (cudaStream_t)stream), "graph launch");
+    return KR_OK;
+  });
+}
+
+kr_status kron_batch_results(kr_batch* b, kr_result* res, int32_t njobs) {
+  if (!b || !res || njobs != (int32_t)b->res.size()) return KR_ERR_INVALID;
+  return guarded(b->ctx, [&]() -> kr_status {
+    const int nl = (int)b->live.size();
+    std::vector<Prod> hp(nl);
+    if (nl > 0) ck(b->ctx, cudaMemcpy(hp.data(), b->dprods, sizeof(Prod) * nl, cudaMemcpyDeviceToHost), "download");
+    for (int i = 0; i < njobs; ++i) res[i] = b->res[i];
+    for (int q = 0; q < nl; ++q) {
+      kr_result& R = res[b->idx[b->live[q]]];
+      if (R.status != KR_OK) continue;
+      const uint32_t stq = hp[q].status;
+      if (stq) R.status = status_to_kr(stq);
+      else if (hp[q].nout != b->nout[q]) R.status = KR_ERR_CAPACITY;   // counts moved: prepare again
+    }
+    return KR_OK;
+  });
+}
+
+void kron_batch_destroy(kr_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->block) cudaFree(b->block);
+  if (b->ctx) kr_ctx_destroy(b->ctx);
+  delete b;
 }
 
 kr_status kron_fetch_poly(kr_ctx* ctx, kr_poly_out* h, kr_stream stream) {

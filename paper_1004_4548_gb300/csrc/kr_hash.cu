@@ -27,7 +27,8 @@
 namespace kr {
 
 constexpr int HASH_THREADS = 256;
-constexpr int HGROUP_R = 4;
+constexpr int HGROUP_R = 4;   // f terms per warp step, polynomial tiles
+constexpr int PGROUP_R = 2;   // f terms per warp step, Poisson tiles (two keys each)
 
 template <typename T>
 __device__ __forceinline__ void gatomic_add(T* p, T v);
@@ -60,6 +61,48 @@ __device__ __forceinline__ bool hash_add(uint64_t* __restrict__ table, uint64_t 
     slot = (slot + 1) & mask;
   }
   return false;
+}
+
+// R independent insert-or-adds issued together so that their L2 round trips
+// overlap.  Each probe claims the slot with a CAS whatever its state: an
+// empty slot is taken in one round trip, a slot holding the same key is
+// recognised by the value the CAS returns, any other key moves the probe on.
+// The adds are fire-and-forget reductions.  Returns false if some key found
+// no slot within `limit` probes.
+template <int R, typename T>
+struct KeyBatch {
+  uint64_t key[R];
+  T val[R];
+};
+
+template <int R, typename T>
+__device__ __forceinline__ bool hash_add_batch(uint64_t* __restrict__ table, uint64_t mask, int limit,
+                                               KeyBatch<R, T> kb, unsigned valid) {
+  uint64_t slot[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) slot[r] = mix64(kb.key[r]) & mask;
+  unsigned pend = valid;
+  for (int p = 0; p < limit && pend; ++p) {
+    unsigned long long got[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      got[r] = 0ull;
+      if (pend & (1u << r))
+        got[r] = atomicCAS((unsigned long long*)(table + 2 * slot[r]), 0ull, kb.key[r] + 1ull);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (pend & (1u << r)) {
+        if (got[r] == 0ull || got[r] == kb.key[r] + 1ull) {
+          gatomic_add<T>((T*)(table + 2 * slot[r] + 1), kb.val[r]);
+          pend &= ~(1u << r);
+        } else {
+          slot[r] = (slot[r] + 1) & mask;
+        }
+      }
+    }
+  }
+  return pend == 0;
 }
 
 struct HashTile {
@@ -108,13 +151,17 @@ __device__ __forceinline__ bool poly_tile(const Prod& P, const HashTile& h) {
       fr[r] = F[i];
       cr[r] = CF[i];
     }
+    const unsigned valid = (1u << m) - 1u;
     for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
       const int64_t gj = G[j];
       const T cg = CG[j];
+      KeyBatch<HGROUP_R, T> kb;
 #pragma unroll
       for (int r = 0; r < HGROUP_R; ++r) {
-        if (r < m && ok) ok = hash_add<T>(P.table, mask, P.probe_limit, (uint64_t)(fr[r] + gj), cr[r] * cg);
+        kb.key[r] = (uint64_t)(fr[r] + gj);
+        kb.val[r] = cr[r] * cg;
       }
+      ok &= hash_add_batch<HGROUP_R, T>(P.table, mask, P.probe_limit, kb, valid);
     }
   }
   return ok;
@@ -134,15 +181,15 @@ __device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
   const uint64_t mask = (uint64_t)P.slots - 1;
   const int64_t T2Wp = P.T2 * P.Wp;
   bool ok = true;
-  const int64_t ngroups = (h.i1 - h.i0 + HGROUP_R - 1) / HGROUP_R;
+  const int64_t ngroups = (h.i1 - h.i0 + PGROUP_R - 1) / PGROUP_R;
   for (int64_t grp = warp; grp < ngroups; grp += NW) {
-    const int64_t ia = h.i0 + grp * HGROUP_R;
-    const int m = (int)min((int64_t)HGROUP_R, h.i1 - ia);
-    int64_t pr[HGROUP_R], tr[HGROUP_R];
-    double cr[HGROUP_R];
-    int kr_[HGROUP_R];
+    const int64_t ia = h.i0 + grp * PGROUP_R;
+    const int m = (int)min((int64_t)PGROUP_R, h.i1 - ia);
+    int64_t pr[PGROUP_R], tr[PGROUP_R];
+    double cr[PGROUP_R];
+    int kr_[PGROUP_R];
 #pragma unroll
-    for (int r = 0; r < HGROUP_R; ++r) {
+    for (int r = 0; r < PGROUP_R; ++r) {
       const int64_t i = ia + (r < m ? r : 0);
       pr[r] = PF[i];
       tr[r] = TF[i];
@@ -153,32 +200,33 @@ __device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
       const int64_t pg = PG[j], tg = TG[j];
       const int kg = KG[j];
       const double cg = CG[j];
+      // two f terms at a time: four keys (a sum and a difference each) in flight
+      {
+        const int r0 = 0;
+        KeyBatch<4, double> kb;
+        unsigned valid = 0;
 #pragma unroll
-      for (int r = 0; r < HGROUP_R; ++r) {
-        if (r >= m || !ok) continue;
-        const int64_t pc = pr[r] + pg;
-        const double hcoef = cr[r] * cg;         // (C_f / 2) * C_g
-        const int kd = kr_[r] ^ kg;              // cos if same kinds, sin otherwise
-        // sum term
-        {
+        for (int u = 0; u < 2; ++u) {
+          const int r = r0 + u;
+          const int64_t pc = pr[r] + pg;
+          const double hcoef = cr[r] * cg;         // (C_f / 2) * C_g
+          const int kd = kr_[r] ^ kg;              // cos if same kinds, sin otherwise
+          // sum term
           int64_t T = tr[r] + tg;
           double v = (kr_[r] & kg) ? -hcoef : hcoef;   // sin*sin: -cos(a+b)
           if (T < 0) { T = -T; if (kd) v = -v; }
-          if (!(T == 0 && kd)) {
-            const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
-            ok = hash_add<double>(P.table, mask, P.probe_limit, key, v);
-          }
-        }
-        // difference term
-        if (ok) {
-          int64_t T = tr[r] - tg;
-          double v = (!kr_[r] && kg) ? -hcoef : hcoef;  // cos*sin: -sin(a-b)
+          kb.key[2 * u] = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+          kb.val[2 * u] = v;
+          if (r < m && !(T == 0 && kd)) valid |= 1u << (2 * u);
+          // difference term
+          T = tr[r] - tg;
+          v = (!kr_[r] && kg) ? -hcoef : hcoef;          // cos*sin: -sin(a-b)
           if (T < 0) { T = -T; if (kd) v = -v; }
-          if (!(T == 0 && kd)) {
-            const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
-            ok = hash_add<double>(P.table, mask, P.probe_limit, key, v);
-          }
+          kb.key[2 * u + 1] = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+          kb.val[2 * u + 1] = v;
+          if (r < m && !(T == 0 && kd)) valid |= 1u << (2 * u + 1);
         }
+        ok &= hash_add_batch<4, double>(P.table, mask, P.probe_limit, kb, valid);
       }
     }
   }
@@ -298,7 +346,7 @@ cudaError_t launch_hll_estimate(Prod* dprods, const int32_t* dhash_prods, int nh
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(HASH_THREADS) k_hash_insert(Prod* __restrict__ prods,
+__global__ void __launch_bounds__(HASH_THREADS, 3) k_hash_insert(Prod* __restrict__ prods,
                                                               const int32_t* __restrict__ hash_prods,
                                                               const int64_t* __restrict__ task_begin,
                                                               int nhash) {

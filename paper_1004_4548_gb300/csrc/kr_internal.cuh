@@ -197,6 +197,12 @@ cudaError_t radix_sort_pairs(uint64_t* key, uint64_t* val, uint64_t* key_tmp, ui
 // bins 2 * (order_bins(krange) + 1) int64.  Result in key/val.
 constexpr int64_t ORDER_MAX_BINS = int64_t(1) << 24;
 int64_t order_bins(int64_t krange);
+// Bitmap-rank ordering for code ranges up to ORDER_BITMAP_MAX codes: result in
+// key2/val2; scratch of order_bitmap_bytes(krange).
+constexpr int64_t ORDER_BITMAP_MAX = int64_t(1) << 35;
+int64_t order_bitmap_bytes(int64_t krange);
+cudaError_t order_by_bitmap(const uint64_t* key, const uint64_t* val, uint64_t* key2, uint64_t* val2,
+                            int64_t n, int64_t krange, void* scratch, cudaStream_t s);
 cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
                           int64_t krange, int64_t* bins, cudaStream_t s);
 

@@ -9,6 +9,12 @@
 //   4. sort segments of whole bins, at most 2C terms each, in shared memory.
 // Steps 1-3 are one counting-sort pass on the high part of the code; step 4
 // orders within bins.  Two reads and two writes of the terms in total.
+//
+// When the code range is small enough for a bitmap of one bit per code
+// (order_bitmap_bytes), a cheaper route is taken: set the bit of every key,
+// prefix-popcount the bitmap, and write each term directly at its rank (the
+// number of keys below it).  One read and one write of the terms, no
+// contended atomics (the bit sets are fire-and-forget reductions).
 #include "kr_internal.cuh"
 
 namespace kr {
@@ -108,6 +114,103 @@ __global__ void __launch_bounds__(ORD_THREADS) k_seg_sort(const uint64_t* __rest
 }
 
 int64_t order_bins(int64_t krange) { return (krange + ORD_C - 1) / ORD_C; }
+
+// ---------------------------------------------------------------------------
+// bitmap rank ordering
+// layout: bits[W64] (uint64), wpre[W64] (uint32: ones in the superblock before
+// the word), spre[NSB + 1] (int64: ones before the superblock); a superblock
+// is BM_SB words
+// ---------------------------------------------------------------------------
+constexpr int BM_SB = 1024;   // words per superblock (65536 codes)
+
+static int64_t bm_words(int64_t krange) { return (krange + 63) / 64; }
+static int64_t bm_sblocks(int64_t krange) { return (bm_words(krange) + BM_SB - 1) / BM_SB; }
+
+int64_t order_bitmap_bytes(int64_t krange) {
+  const int64_t w = bm_sblocks(krange) * BM_SB;
+  return w * 8 + w * 4 + (bm_sblocks(krange) + 1) * 8 + 3 * 256;
+}
+
+__global__ void __launch_bounds__(256) k_bm_set(const uint64_t* __restrict__ key, int64_t n, int64_t krange,
+                                                unsigned long long* __restrict__ bits) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    if (k < (uint64_t)krange) atomicOr(&bits[k >> 6], 1ull << (k & 63));
+  }
+}
+
+// one CTA per superblock: exclusive popcount prefix of its words, and its total
+__global__ void __launch_bounds__(BM_SB) k_bm_prefix(const unsigned long long* __restrict__ bits,
+                                                     uint32_t* __restrict__ wpre, int64_t* __restrict__ stot) {
+  __shared__ uint32_t ws[BM_SB / 32];
+  const int64_t w = (int64_t)blockIdx.x * BM_SB + threadIdx.x;
+  const uint32_t c = (uint32_t)__popcll(bits[w]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    ws[lane] = v;
+  }
+  __syncthreads();
+  wpre[w] = (warp > 0 ? ws[warp - 1] : 0) + x - c;
+  if (threadIdx.x == BM_SB - 1) stot[blockIdx.x] = (int64_t)((warp > 0 ? ws[warp - 1] : 0) + x);
+}
+
+__global__ void __launch_bounds__(256) k_bm_scatter(const uint64_t* __restrict__ key,
+                                                    const uint64_t* __restrict__ val, int64_t n,
+                                                    int64_t krange,
+                                                    const unsigned long long* __restrict__ bits,
+                                                    const uint32_t* __restrict__ wpre,
+                                                    const int64_t* __restrict__ spre,
+                                                    uint64_t* __restrict__ okey,
+                                                    uint64_t* __restrict__ oval) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    if (k >= (uint64_t)krange) continue;
+    const int64_t w = (int64_t)(k >> 6);
+    const uint64_t below = bits[w] & ((1ull << (k & 63)) - 1ull);
+    const int64_t rank = spre[w / BM_SB] + wpre[w] + __popcll(below);
+    if (rank < n) {
+      okey[rank] = k;
+      oval[rank] = val[i];
+    }
+  }
+}
+
+// Sorts (key, val)[0, n) by key (distinct keys < krange) into key2/val2.
+// scratch: order_bitmap_bytes(krange) bytes.
+cudaError_t order_by_bitmap(const uint64_t* key, const uint64_t* val, uint64_t* key2, uint64_t* val2,
+                            int64_t n, int64_t krange, void* scratch, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nsb = bm_sblocks(krange);
+  const int64_t nw = nsb * BM_SB;
+  char* base = (char*)scratch;
+  unsigned long long* bits = (unsigned long long*)base;
+  uint32_t* wpre = (uint32_t*)(base + ((nw * 8 + 255) / 256) * 256);
+  int64_t* spre = (int64_t*)((char*)wpre + ((nw * 4 + 255) / 256) * 256);
+  cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)nw * 8, s);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (n + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_bm_set<<<(unsigned)grid, 256, 0, s>>>(key, n, krange, bits);
+  k_bm_prefix<<<(unsigned)nsb, BM_SB, 0, s>>>(bits, wpre, spre);
+  e = launch_scan_exclusive(spre, nsb, spre + nsb, s);
+  if (e != cudaSuccess) return e;
+  k_bm_scatter<<<(unsigned)grid, 256, 0, s>>>(key, val, n, krange, bits, wpre, spre, key2, val2);
+  return cudaGetLastError();
+}
 
 // Sorts (key, val)[0, n) by key, keys distinct and < krange.  Uses key2/val2
 // as the binned copy and writes the sorted terms back to key/val.  bins:

@@ -14,6 +14,13 @@ The memory prediction per product is the term-product count times 16 bytes
 times the observed ratio of output terms to term-products (updated after
 every batch, separately for polynomials and Poisson series), plus the dense
 array or hash table it needs.
+
+A batch is also capped in work (term-products): the oldest waiting request
+always starts the batch, and later requests join it only while the cap holds,
+so a small request never waits behind a very large one in the same batch
+and can overtake it on the other worker.  A worker that fails (an exception
+from the library, such as running out of memory) reports the failure on the
+requests of its batch instead of dropping them.
 """
 from __future__ import annotations
 
@@ -75,8 +82,9 @@ class Server:
     """Continuous batching over `workers` contexts on one GPU."""
 
     def __init__(self, device: int = 0, workers: int = 2, mem_budget: float = 64e9,
-                 max_batch: int = 256, wave_pairs: int = 0):
+                 max_batch: int = 256, wave_pairs: int = 0, work_cap: float = 2e8):
         self.device = device
+        self.work_cap = work_cap
         self.workers = [_Worker(device) for _ in range(workers)]
         self.mem_budget = mem_budget
         self.max_batch = max_batch
@@ -92,6 +100,7 @@ class Server:
 
     def _run_batch(self, w: _Worker, batch: list[Request], t0: float, bytes_: float):
         import torch
+        out = None
         try:
             with torch.cuda.stream(w.stream):
                 now = time.perf_counter() - t0
@@ -114,6 +123,13 @@ class Server:
                 for k, (n, p) in obs.items():
                     if p > 0:
                         self.ratio[k] = 0.7 * self.ratio[k] + 0.3 * max(n / p, 1e-4)
+        except Exception as e:   # the batch failed as a whole: report it on every request
+            done = time.perf_counter() - t0
+            for r in batch:
+                if r.done < 0:
+                    r.status = getattr(e, "status", -2)
+                    r.done = done
+                    r.result = None
         finally:
             with self.lock:
                 self.in_flight_bytes -= bytes_
@@ -140,17 +156,21 @@ class Server:
             if pending and free:
                 with self.lock:
                     room = self.mem_budget - self.in_flight_bytes
-                batch, used = [], 0.0
+                batch, used, work = [], 0.0, 0.0
                 for r in pending:
                     b = self.predict_bytes(r)
-                    if batch and (used + b > room or len(batch) >= self.max_batch):
-                        break
-                    if not batch and b > room and self.in_flight_bytes > 0:
-                        break   # wait for memory to come back
+                    if not batch:
+                        if b > room and self.in_flight_bytes > 0:
+                            break   # wait for memory to come back
+                    elif (used + b > room or work + r.pairs > self.work_cap
+                          or len(batch) >= self.max_batch):
+                        continue    # later, smaller requests may still fit
                     batch.append(r)
                     used += b
+                    work += r.pairs
                 if batch:
-                    pending = pending[len(batch):]
+                    taken = set(id(r) for r in batch)
+                    pending = [r for r in pending if id(r) not in taken]
                     w = free[0]
                     with self.lock:
                         w.busy = True
@@ -168,9 +188,10 @@ class Server:
             if w.thread is not None:
                 w.thread.join()
         wall = time.perf_counter() - t0
-        done = [r for r in reqs if r.done >= 0]
+        done = [r for r in reqs if r.done >= 0 and r.status == 0]
         lat = np.array([r.latency for r in done]) if done else np.zeros(1)
-        return ServeStats(completed=len(done), wall_s=wall,
+        failed = sum(1 for r in reqs if r.done >= 0 and r.status != 0)
+        return ServeStats(completed=len(done), wall_s=wall, extra={"failed": failed},
                           products_per_s=len(done) / wall if wall > 0 else 0.0,
                           p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                           mean_batch=float(np.mean(sizes)) if sizes else 0.0, batches=batches,

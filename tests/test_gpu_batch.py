@@ -113,3 +113,47 @@ def test_served_results_equal_alone(kron):
         else:
             e, c = _alone(kron, f, g)
             assert np.array_equal(to_np(r.result["exps"]), e) and np.array_equal(to_np(r.result["coef"]), c)
+
+
+def test_prepared_batch_graph_replay(kron):
+    """A batch captured into a CUDA graph: the replay reproduces the prepared
+    results, and replays again correctly after the coefficients change in place
+    (doubling every f coefficient doubles every product coefficient exactly)."""
+    import torch
+    mix = batch_mix(24, seed_base=8000, max_terms=500)
+
+    def dev(p):
+        if isinstance(p, PSeries):
+            return PSeries(*(torch.from_numpy(x.copy()).cuda() for x in (p.exps, p.trig, p.kind, p.coef)))
+        return Poly(torch.from_numpy(p.exps.copy()).cuda(), torch.from_numpy(p.coef.copy()).cuda())
+
+    D = [(dev(f), dev(g)) for f, g in mix]
+    ref = [{k: (v.clone() if hasattr(v, "clone") else v) for k, v in r.items()} for r in kron.kron_mul_batch(D)]
+    pb = kron.PreparedBatch(D)
+    first = pb.first_results()
+    for a, b in zip(first, ref):
+        assert a["status"] == 0 and a["nterms"] == b["nterms"]
+        assert torch.equal(a["exps"], b["exps"])
+    for it in range(2):
+        pb.launch()
+        torch.cuda.synchronize()
+        out = pb.results()
+        for i, (a, b) in enumerate(zip(out, ref)):
+            assert a["status"] == 0, f"replay {it} product {i}: status {a['status']}"
+            assert torch.equal(a["exps"], b["exps"])
+            if isinstance(mix[i][0], Poly):
+                assert torch.equal(a["coef"], b["coef"])
+            else:
+                assert torch.allclose(a["coef"], b["coef"], rtol=0, atol=1e-12 * float(b["coef"].abs().max()))
+    for f, g in D:
+        f.coef.mul_(2)
+    pb.launch()
+    torch.cuda.synchronize()
+    out = pb.results()
+    for i, (a, b) in enumerate(zip(out, ref)):
+        assert a["status"] == 0
+        if isinstance(mix[i][0], Poly):
+            assert torch.equal(a["coef"], 2 * b["coef"])
+        else:
+            assert torch.allclose(a["coef"], 2 * b["coef"], rtol=0, atol=2e-12 * float(b["coef"].abs().max()))
+    pb.close()
