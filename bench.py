@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--block-slots", type=int, default=0, help="dense output block size (0 = library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched / served measurements")
     ap.add_argument("--batch-products", type=int, default=4096, help="products in the uneven batch")
+    ap.add_argument("--case", default="", choices=["", "cfg3", "cfg4s"],
+                    help="profiling runs: time only this secondary case (cfg4s = cfg4 at 5000 terms)")
     return ap.parse_args()
 
 
@@ -186,6 +188,9 @@ def main():
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if args.case:
+        profile_case(args)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -216,7 +221,6 @@ def main():
         if st != 0:
             raise RuntimeError(f"poly_mul failed: {st} {L.kr_last_error(ctx.h).decode()}")
 
-    ctx.set_profiling(True)
     for _ in range(max(3, args.warmup)):
         step()
     assert int(H.nterms) == nout
@@ -236,13 +240,21 @@ def main():
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
-        accum_ms.extend(ms for name, ms in ctx.stages() if name == "dense_accum")
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
     launches = ctx.launch_count() - l0
+    # the dominant kernel's duration: the library's CUDA events around it, on
+    # the launch stream, in a separate pass (the events are not in the timed loop)
+    ctx.set_profiling(True)
+    for i in range(args.steps):
+        flush.zero_()
+        step()
+        accum_ms.extend(ms for name, ms in ctx.stages() if name == "dense_accum")
+    stages = ctx.stages()
+    ctx.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
     if world > 1:
@@ -250,7 +262,6 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     value = world * tp / (ms * 1e-3) / 1e6
-    stages = ctx.stages()
 
     # ---- roofline of the dominant kernel (dense accumulation)
     peak_smem = kron.kr_probe_smem_atomic_rate(local, False, 5)
@@ -308,6 +319,7 @@ def main():
 
     batched = None
     if not args.no_batch:
+        ctx.trim()
         batched = time_batched(kron, ctx, dev, args.batch_products)
 
     line = None
@@ -332,6 +344,24 @@ def main():
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def profile_case(args):
+    """One secondary case only, for profiler captures (small device footprint)."""
+    import torch
+    import paper_1004_4548_gb300 as kron
+    from workloads import workload_cfg3, workload_cfg4
+    dev = torch.device("cuda", 0)
+    ctx = kron.Context(0)
+    ctx.set_profiling(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    if args.case == "cfg3":
+        r = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert", args.steps)
+    else:
+        f, g = workload_cfg4(5000)
+        r = time_pseries(kron, ctx, f, g, dev, stream, flush, args.steps)
+    print(json.dumps({"case": args.case, **{k: v for k, v in r.items() if k != "stages_ms_last_step"}}))
 
 
 def time_batched(kron, ctx, dev, nprod):
@@ -423,6 +453,26 @@ def time_batched(kron, ctx, dev, nprod):
     graph["replay_products_per_s"] = graph["products"] / graph["replay_s"]
     graph["batch_call_products_per_s"] = graph["products"] / graph["batch_call_s"]
     res["cuda_graph"] = graph
+    # CUDA graphs where launches dominate: 512 small products (<= 200 terms per operand)
+    small = [(todev(f), todev(g)) for f, g in batch_mix(512, seed_base=9000, max_terms=200)]
+    pb = kron.PreparedBatch(small, device=dev.index or 0)
+    pb.launch()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(5):
+        pb.launch()
+    torch.cuda.synchronize()
+    rs = (time.perf_counter() - t) / 5
+    pb.close()
+    t = time.perf_counter()
+    for _ in range(5):
+        kron.kron_mul_batch(small, ctx=ctx)
+    torch.cuda.synchronize()
+    cs = (time.perf_counter() - t) / 5
+    res["cuda_graph_small_products"] = {"products": 512, "max_terms": 200, "replay_s": rs,
+                                        "batch_call_s": cs, "replay_products_per_s": 512 / rs,
+                                        "batch_call_products_per_s": 512 / cs}
+    ctx.trim()
     # serving: Poisson arrivals at 0.5 and 0.8 of the batched throughput
     serve = {}
     cap = nprod / bt
@@ -431,14 +481,17 @@ def time_batched(kron, ctx, dev, nprod):
         rate = frac * cap
         t_arr = arrival_times(nreq, rate, seed=99)
         reqs = [Request(f, g, float(a)) for (f, g), a in zip(D[:nreq], t_arr)]
-        st = Server(device=dev.index or 0, workers=2, max_batch=chunk, mem_budget=60e9).run(reqs, time_limit=60.0)
+        server = Server(device=dev.index or 0, workers=2, max_batch=chunk, mem_budget=60e9)
+        st = server.run(reqs, time_limit=60.0)
+        server.close()
         reqs1 = [Request(f, g, float(a)) for (f, g), a in zip(D[:nreq], t_arr)]
         st1 = serve_one_by_one(reqs1, device=dev.index or 0, time_limit=min(60.0, float(t_arr[-1]) * 1.5 + 5))
         serve[f"rate_{frac}"] = {
             "arrival_rate_per_s": rate, "requests": nreq,
             "continuous_batching": {"completed": st.completed, "products_per_s": st.products_per_s,
                                     "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_batch": st.mean_batch,
-                                    "batches": st.batches, "failed": st.extra.get("failed", 0)},
+                                    "batches": st.batches, "failed": st.extra.get("failed", 0),
+                                    "errors": st.extra.get("errors", [])},
             "one_by_one": {"completed": st1.completed, "products_per_s": st1.products_per_s,
                            "p50_ms": st1.p50_ms, "p99_ms": st1.p99_ms,
                            "note": "requests still queued at the time limit are not counted"}}

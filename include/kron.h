@@ -148,6 +148,10 @@ const char* kr_last_error(const kr_ctx* ctx);
 const char* kron_strerror(kr_status s);
 /* Bytes of device scratch currently held by the context. */
 int64_t kr_ctx_scratch_bytes(const kr_ctx* ctx);
+/* Releases the context's cached scratch (device arenas, pinned staging and
+ * the results of its last batch); the next call allocates what it needs.
+ * Synchronises the context's device. */
+kr_status kr_ctx_trim(kr_ctx* ctx);
 /* Stage timing.  When enabled, every multiplication records a CUDA event on
  * its stream after each pipeline stage (range_scan, zero_accumulators, encode,
  * sort, gather, dense_plan, dense_accum, hash_insert, compact, output_sort,

@@ -68,6 +68,7 @@ SIGNATURES = {
     "kron_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "kr_ctx_scratch_bytes": (_i64, [_vp]),
     "kr_ctx_set_profiling": (ctypes.c_int, [_vp, _i32]),
+    "kr_ctx_trim": (ctypes.c_int, [_vp]),
     "kr_ctx_stage_count": (_i32, [_vp]),
     "kr_ctx_stage": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(ctypes.c_char_p),
                                     ctypes.POINTER(ctypes.c_double)]),
@@ -202,6 +203,10 @@ class Context:
 
     def scratch_bytes(self) -> int:
         return int(self.L.kr_ctx_scratch_bytes(self.h))
+
+    def trim(self):
+        """Release the context's cached device and pinned scratch."""
+        _check(self.L, self.h, self.L.kr_ctx_trim(self.h), "kr_ctx_trim")
 
     def set_profiling(self, on: bool = True):
         _check(self.L, self.h, self.L.kr_ctx_set_profiling(self.h, int(on)), "kr_ctx_set_profiling")

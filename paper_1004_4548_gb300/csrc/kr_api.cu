@@ -792,6 +792,26 @@ int64_t kr_ctx_scratch_bytes(const kr_ctx* ctx) {
   return ctx ? (int64_t)(ctx->in_cap + ctx->work_cap + ctx->acc_cap) : 0;
 }
 
+kr_status kr_ctx_trim(kr_ctx* ctx) {
+  if (!ctx) return KR_ERR_INVALID;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->in_arena) cudaFree(ctx->in_arena);
+  if (ctx->work) cudaFree(ctx->work);
+  if (ctx->acc) cudaFree(ctx->acc);
+  for (void* b : ctx->batch_blocks) cudaFree(b);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  ctx->in_arena = ctx->work = ctx->acc = ctx->pinned = nullptr;
+  ctx->in_cap = ctx->work_cap = ctx->acc_cap = ctx->pinned_cap = 0;
+  ctx->batch_blocks.clear();
+  ctx->has_result = false;
+  const cudaError_t e = cudaGetLastError();
+  cudaSetDevice(prev);
+  return e == cudaSuccess ? KR_OK : KR_ERR_CUDA;
+}
+
 kr_status kr_ctx_set_profiling(kr_ctx* ctx, int32_t enable) {
   if (!ctx) return KR_ERR_INVALID;
   ctx->profile = enable != 0;

@@ -18,9 +18,14 @@ array or hash table it needs.
 A batch is also capped in work (term-products): the oldest waiting request
 always starts the batch, and later requests join it only while the cap holds,
 so a small request never waits behind a very large one in the same batch
-and can overtake it on the other worker.  A worker that fails (an exception
-from the library, such as running out of memory) reports the failure on the
-requests of its batch instead of dropping them.
+and can overtake it on the other worker.  A request above `giant` term
+products runs in a batch of its own and no other batch starts while it runs,
+so that the largest products, which set the tail latency, share the GPU with
+at most the batch already running.  A worker releases its
+context's cached scratch after a batch when it holds more than `trim_bytes`.
+A worker that fails (an exception from the library, such as running out of
+memory) reports the failure on the requests of its batch instead of
+dropping them.
 """
 from __future__ import annotations
 
@@ -82,9 +87,14 @@ class Server:
     """Continuous batching over `workers` contexts on one GPU."""
 
     def __init__(self, device: int = 0, workers: int = 2, mem_budget: float = 64e9,
-                 max_batch: int = 256, wave_pairs: int = 0, work_cap: float = 2e8):
+                 max_batch: int = 256, wave_pairs: int = 0, work_cap: float = 2e8,
+                 giant: float = 5e7, trim_bytes: float = 24e9):
         self.device = device
         self.work_cap = work_cap
+        self.giant = giant
+        self.trim_bytes = trim_bytes
+        self.exclusive = False
+        self.errors: list[str] = []
         self.workers = [_Worker(device) for _ in range(workers)]
         self.mem_budget = mem_budget
         self.max_batch = max_batch
@@ -92,6 +102,13 @@ class Server:
         self.ratio = {False: 0.3, True: 1.0}   # output terms per term-product, learned
         self.lock = threading.Lock()
         self.in_flight_bytes = 0.0
+
+    def close(self):
+        """Release the workers' contexts (their scratch and results)."""
+        for w in self.workers:
+            if w.thread is not None:
+                w.thread.join()
+            w.ctx.close()
 
     def predict_bytes(self, r: Request) -> float:
         out_terms = r.pairs * self.ratio[r.poisson]
@@ -125,14 +142,21 @@ class Server:
                         self.ratio[k] = 0.7 * self.ratio[k] + 0.3 * max(n / p, 1e-4)
         except Exception as e:   # the batch failed as a whole: report it on every request
             done = time.perf_counter() - t0
+            self.errors.append(f"{type(e).__name__}: {e}"[:200])
             for r in batch:
                 if r.done < 0:
                     r.status = getattr(e, "status", -2)
                     r.done = done
                     r.result = None
         finally:
+            try:
+                if w.ctx.scratch_bytes() > self.trim_bytes:
+                    w.ctx.trim()
+            except Exception:
+                pass
             with self.lock:
                 self.in_flight_bytes -= bytes_
+                self.exclusive = False if any(r.pairs > self.giant for r in batch) else self.exclusive
                 w.busy = False
 
     def run(self, requests: list[Request], time_limit: float = 120.0) -> ServeStats:
@@ -153,12 +177,22 @@ class Server:
             if now > time_limit:
                 break
             free = [w for w in self.workers if not w.busy]
+            if self.exclusive:
+                free = []
             if pending and free:
                 with self.lock:
                     room = self.mem_budget - self.in_flight_bytes
                 batch, used, work = [], 0.0, 0.0
-                for r in pending:
+                idle = all(not w.busy for w in self.workers)
+                if pending[0].pairs > self.giant:
+                    # the oldest request is very large: it starts on the free
+                    # worker at once and no new batch starts until it is done
+                    batch.append(pending[0])
+                    used += self.predict_bytes(pending[0])
+                for r in ([] if pending[0].pairs > self.giant else pending):
                     b = self.predict_bytes(r)
+                    if r.pairs > self.giant:
+                        continue
                     if not batch:
                         if b > room and self.in_flight_bytes > 0:
                             break   # wait for memory to come back
@@ -169,6 +203,8 @@ class Server:
                     used += b
                     work += r.pairs
                 if batch:
+                    if batch[0].pairs > self.giant:
+                        self.exclusive = True
                     taken = set(id(r) for r in batch)
                     pending = [r for r in pending if id(r) not in taken]
                     w = free[0]
@@ -191,7 +227,8 @@ class Server:
         done = [r for r in reqs if r.done >= 0 and r.status == 0]
         lat = np.array([r.latency for r in done]) if done else np.zeros(1)
         failed = sum(1 for r in reqs if r.done >= 0 and r.status != 0)
-        return ServeStats(completed=len(done), wall_s=wall, extra={"failed": failed},
+        return ServeStats(completed=len(done), wall_s=wall,
+                          extra={"failed": failed, "errors": sorted(set(self.errors))[:3]},
                           products_per_s=len(done) / wall if wall > 0 else 0.0,
                           p50_ms=float(np.percentile(lat, 50) * 1e3), p99_ms=float(np.percentile(lat, 99) * 1e3),
                           mean_batch=float(np.mean(sizes)) if sizes else 0.0, batches=batches,
@@ -218,6 +255,7 @@ def serve_one_by_one(requests: list[Request], device: int = 0, time_limit: float
         r.status = 0
         r.done = time.perf_counter() - t0
     wall = time.perf_counter() - t0
+    ctx.close()
     done = [r for r in reqs if r.done >= 0]
     lat = np.array([r.latency for r in done]) if done else np.zeros(1)
     return ServeStats(completed=len(done), wall_s=wall, products_per_s=len(done) / wall if wall > 0 else 0.0,
