@@ -117,6 +117,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch of k_dense_accum on this workload, from
+# one ncu capture (profiles/k_dense_accum_cfg2.md); valid only for the kernel
+# source it was taken on, identified by the leading hex digits of its SHA-256.
+DENSE_TRAFFIC = {"source_sha256": "964e275ba9055a27", "bytes": 2769920}
+
+
+def dense_traffic():
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_1004_4548_gb300", "csrc", "kr_dense.cu"), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    return DENSE_TRAFFIC["bytes"] if sha.startswith(DENSE_TRAFFIC["source_sha256"]) else None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -273,7 +289,7 @@ def main():
             "peak_source": "measured: kr_probe_smem_atomic_rate (conflict-free 64-bit shared-memory "
                            "atomic adds, all SMs, best of 5)",
             "kernel_ms": acc_ms, "algorithmic_units_per_launch": tp,
-            "traffic": None}
+            "traffic": dense_traffic()}
 
     # ---- end to end through the C ABI with pinned host buffers
     hfe = torch.from_numpy(f.exps).pin_memory(); hfc = torch.from_numpy(f.coef).pin_memory()
