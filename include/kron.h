@@ -204,7 +204,11 @@ kr_status kron_decode(kr_ctx* ctx, const int64_t* codes, int64_t n, int32_t nvar
 kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out* h,
                    const kr_opts* opts, kr_stream stream);
 
-/* h = f * g for Poisson series (Eq. 1, Eq. 6 with the factor 1/2); hash path.
+/* h = f * g for Poisson series (Eq. 1, Eq. 6 with the factor 1/2).  Dense
+ * path (Sec. 3.1): each pair adds into an array indexed by the key of the sum
+ * and of the difference term (up to 48 GiB); hash path (Sec. 3.2): both terms
+ * go into the open-addressing table.  AUTO picks the dense path when the key
+ * range is at most sixteen times the number of updates.
  * Polynomial exponents are coded in the product's box; trig multipliers in the
  * symmetric box |t_k| <= R_k = max|f_k| + max|g_k|, so that sums and
  * differences of codes are the codes of the sums and differences (the

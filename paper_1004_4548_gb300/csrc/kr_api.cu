@@ -273,11 +273,16 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   }
   }   // phase A
   std::vector<Plan>& plans = ctx->plans;
-  std::vector<int> live_ids, dense_ids, hash_ids;
+  // dense_ids: polynomial products on the dense path (output-block tasks);
+  // hash_ids: everything accumulated by tiles of term pairs (hash products and
+  // Poisson products on the dense path); hll_ids: products with a hash table
+  std::vector<int> live_ids, dense_ids, hash_ids, hll_ids;
   for (int p = 0; p < nprod; ++p) {
     if (plans[p].st != KR_OK) continue;
     live_ids.push_back(p);
-    (plans[p].p.path == PATH_DENSE ? dense_ids : hash_ids).push_back(p);
+    const bool block = plans[p].p.path == PATH_DENSE && plans[p].p.nt == 0;
+    (block ? dense_ids : hash_ids).push_back(p);
+    if (plans[p].p.path == PATH_HASH) hll_ids.push_back(p);
   }
   const int nlive = (int)live_ids.size();
   if (nlive == 0) return;
@@ -286,6 +291,8 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   std::vector<int32_t> h_dense_local, h_hash_local;
   for (int p : dense_ids) h_dense_local.push_back(local[p]);
   for (int p : hash_ids) h_hash_local.push_back(local[p]);
+  std::vector<int32_t> h_hll_local;
+  for (int p : hll_ids) h_hll_local.push_back(local[p]);
   // ---------------- phase B1 layout (work arena)
   int64_t dense_tasks_total = 0, nblocks_total = 0, scan_b1 = 0, max_ng_dense = 0, max_S = 0;
   for (int p : dense_ids) {
@@ -298,6 +305,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   struct B1 {
     Prod* lprods; OpRef* oplists; int32_t* dense_ids; int64_t* block_begin; int32_t* hash_ids;
     int64_t* task_begin; int64_t* scan; DenseTask* tasks; uint32_t* hll; size_t hll_bytes;
+    int32_t* hll_ids; int64_t* hll_task_begin;
   } A{};
   for (int pass = 0; pass < 2; ++pass) {
     Bump b(pass ? ctx->work : nullptr);
@@ -309,10 +317,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     A.task_begin = b.take<int64_t>((int64_t)hash_ids.size() + 1);
     A.scan = b.take<int64_t>(scan_b1 + 1);
     A.tasks = b.take<DenseTask>(dense_tasks_total);
-    A.hll = b.take<uint32_t>((int64_t)hash_ids.size() * HLL_M);
-    A.hll_bytes = sizeof(uint32_t) * hash_ids.size() * HLL_M;
-    for (int q = 0; q < (int)hash_ids.size(); ++q)
-      if (pass) plans[hash_ids[q]].p.hll = A.hll + (int64_t)q * HLL_M;
+    A.hll_ids = b.take<int32_t>((int64_t)hll_ids.size() + 1);
+    A.hll_task_begin = b.take<int64_t>((int64_t)hll_ids.size() + 1);
+    A.hll = b.take<uint32_t>((int64_t)hll_ids.size() * HLL_M);
+    A.hll_bytes = sizeof(uint32_t) * hll_ids.size() * HLL_M;
+    for (int q = 0; q < (int)hll_ids.size(); ++q)
+      if (pass) plans[hll_ids[q]].p.hll = A.hll + (int64_t)q * HLL_M;
     for (int p : live_ids) {
       Plan& pl = plans[p];
       for (int which = 0; which < 2; ++which) {
@@ -335,7 +345,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
           op.kind = b.take<uint8_t>(n);
         }
       }
-      if (pl.p.path == PATH_DENSE) {
+      if (pl.p.path == PATH_DENSE && pl.p.nt == 0) {
         pl.p.gidx = b.take<int32_t>(pl.p.gidx_n + 1);
         pl.p.g.code32 = b.take<int32_t>(pl.p.g.n);
       }
@@ -349,6 +359,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     plans[hash_ids[q]].p.task_begin = h_task_begin[q];
     h_task_begin[q + 1] = h_task_begin[q] + plans[hash_ids[q]].p.ntasks;
   }
+  std::vector<int64_t> h_hll_task_begin(hll_ids.size() + 1, 0);
+  for (size_t q = 0; q < hll_ids.size(); ++q)
+    h_hll_task_begin[q + 1] = h_hll_task_begin[q] + plans[hll_ids[q]].p.ntasks;
   std::vector<OpRef> all, bm, bt;
   for (int q = 0; q < nlive; ++q) {
     const Prod& P = plans[live_ids[q]].p;
@@ -379,6 +392,8 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   up(A.block_begin, h_block_begin.data(), 8 * h_block_begin.size());
   up(A.hash_ids, h_hash_local.data(), 4 * h_hash_local.size());
   up(A.task_begin, h_task_begin.data(), 8 * h_task_begin.size());
+  up(A.hll_ids, h_hll_local.data(), 4 * h_hll_local.size());
+  up(A.hll_task_begin, h_hll_task_begin.data(), 8 * h_hll_task_begin.size());
   const OpRef* d_all = A.oplists;
   const OpRef* d_bm = d_all + all.size();
   const OpRef* d_bt = d_bm + bm.size();
@@ -431,14 +446,14 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     ck(ctx, launch_build_gindex(A.lprods, A.dense_ids, (int)dense_ids.size(), max_ng_dense, s), "g index");
     ctx->launches += 1;
   }
-  if (!hash_ids.empty()) {
+  if (!hll_ids.empty()) {
     bool need_hll = false;
-    for (int p : hash_ids) need_hll |= ins[p].opts.table_slots <= 0;
+    for (int p : hll_ids) need_hll |= ins[p].opts.table_slots <= 0;
     if (ctx->replay) need_hll = false;   // table sizes are fixed by the prepared run
     if (need_hll) {
-      ck(ctx, launch_hll(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(), ctx->num_sms * 8, s),
+      ck(ctx, launch_hll(A.lprods, A.hll_ids, A.hll_task_begin, (int)hll_ids.size(), ctx->num_sms * 8, s),
          "hll");
-      ck(ctx, launch_hll_estimate(A.lprods, A.hash_ids, (int)hash_ids.size(), s), "hll estimate");
+      ck(ctx, launch_hll_estimate(A.lprods, A.hll_ids, (int)hll_ids.size(), s), "hll estimate");
       ctx->launches += 2;
       mark(ctx, s, "hll");
     }
@@ -457,7 +472,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   std::vector<int> regrows(nprod, 0);
   for (;;) {
     int64_t out_total = 0, nchunks_total = 0, bins_total = 0, scan_b2 = 0, max_hash_out = 0;
-    for (int p : hash_ids) {
+    for (int p : hll_ids) {
       Plan& pl = plans[p];
       finish_hash_sizes(ins[p].opts, &pl);
       max_hash_out = std::max(max_hash_out, pl.out_cap);
@@ -984,7 +999,6 @@ kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g, kr_
   };
   if (bad(f) || bad(g)) return KR_ERR_INVALID;
   if (h->capacity > 0 && !h->coef) return KR_ERR_INVALID;
-  if (opts && opts->path == KR_PATH_DENSE) return KR_ERR_INVALID;
   return guarded(ctx, [&]() -> kr_status {
     cudaStream_t s = (cudaStream_t)stream;
     ctx->has_result = false;
@@ -1153,7 +1167,7 @@ kr_status kron_mul_batch(kr_ctx* ctx, const kr_job* jobs, int32_t njobs, kr_resu
         in.fe = J.f.exps; in.fc = J.f.coef; in.nf = J.f.nterms;
         in.ge = J.g.exps; in.gc = J.g.coef; in.ng = J.g.nterms;
       } else if (J.kind == 1) {
-        if (!pseries_job_ok(&J.pf, &J.pg) || J.opts.path == KR_PATH_DENSE) { R.status = KR_ERR_INVALID; continue; }
+        if (!pseries_job_ok(&J.pf, &J.pg)) { R.status = KR_ERR_INVALID; continue; }
         if (J.pf.nterms == 0 || J.pg.nterms == 0) { R.status = KR_OK; continue; }
         in.poisson = true;
         in.f64 = true;
@@ -1249,8 +1263,7 @@ kr_status kron_batch_prepare(int32_t device, const kr_job* jobs, int32_t njobs, 
         in.np = J.f.nvars;
         in.fe = J.f.exps; in.fc = J.f.coef; in.nf = J.f.nterms;
         in.ge = J.g.exps; in.gc = J.g.coef; in.ng = J.g.nterms;
-      } else if (J.kind == 1 && pseries_job_ok(&J.pf, &J.pg) && J.pf.nterms > 0 && J.pg.nterms > 0 &&
-                 J.opts.path != KR_PATH_DENSE) {
+      } else if (J.kind == 1 && pseries_job_ok(&J.pf, &J.pg) && J.pf.nterms > 0 && J.pg.nterms > 0) {
         for (const void* p : {(const void*)J.pf.exps, (const void*)J.pf.trig, (const void*)J.pf.kind,
                               (const void*)J.pf.coef, (const void*)J.pg.exps, (const void*)J.pg.trig,
                               (const void*)J.pg.kind, (const void*)J.pg.coef})

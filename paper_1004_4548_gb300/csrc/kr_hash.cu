@@ -233,6 +233,50 @@ __device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
   return ok;
 }
 
+// Poisson series on the dense path (Sec. 3.1): both terms of a pair add into
+// the array indexed by their key, with fire-and-forget float64 reductions.
+__device__ __forceinline__ void pseries_dense_tile(const Prod& P, const HashTile& h) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = HASH_THREADS / 32;
+  const int64_t* __restrict__ PF = P.f.code;
+  const int64_t* __restrict__ PG = P.g.code;
+  const int64_t* __restrict__ TF = P.f.tcode;
+  const int64_t* __restrict__ TG = P.g.tcode;
+  const uint8_t* __restrict__ KF = P.f.kind;
+  const uint8_t* __restrict__ KG = P.g.kind;
+  const double* __restrict__ CF = (const double*)P.f.coef;   // already halved
+  const double* __restrict__ CG = (const double*)P.g.coef;
+  double* __restrict__ out = (double*)P.dense;
+  const int64_t T2Wp = P.T2 * P.Wp;
+  const uint64_t K = (uint64_t)P.krange;
+  for (int64_t i = h.i0 + warp; i < h.i1; i += NW) {
+    const int64_t pf = PF[i], tf = TF[i];
+    const int kf = KF[i];
+    const double cf = CF[i];
+    for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
+      const int64_t pc = pf + PG[j];
+      const int64_t tg = TG[j];
+      const int kg = KG[j];
+      const double hcoef = cf * CG[j];
+      const int kd = kf ^ kg;
+      int64_t T = tf + tg;
+      double v = (kf & kg) ? -hcoef : hcoef;
+      if (T < 0) { T = -T; if (kd) v = -v; }
+      if (!(T == 0 && kd)) {
+        const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+        if (key < K) atomicAdd(&out[key], v);
+      }
+      T = tf - tg;
+      v = (!kf && kg) ? -hcoef : hcoef;
+      if (T < 0) { T = -T; if (kd) v = -v; }
+      if (!(T == 0 && kd)) {
+        const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+        if (key < K) atomicAdd(&out[key], v);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // HyperLogLog pass: same tiles and keys as the inserts, no table traffic.
 // ---------------------------------------------------------------------------
@@ -356,7 +400,10 @@ __global__ void __launch_bounds__(HASH_THREADS, 3) k_hash_insert(Prod* __restric
     Prod& P = prods[h.pid];
     if (*(volatile uint32_t*)&P.status) continue;   // failed product: skip its remaining tiles
     bool ok;
-    if (P.nt > 0) ok = pseries_tile(P, h);
+    if (P.nt > 0) {
+      if (P.path == PATH_DENSE) { pseries_dense_tile(P, h); ok = true; }
+      else ok = pseries_tile(P, h);
+    }
     else if (P.f64) ok = poly_tile<double>(P, h);
     else ok = poly_tile<int64_t>(P, h);
     if (!ok) atomicOr(&P.status, ST_TABLE_FULL);

@@ -107,7 +107,17 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
   P.coef32 = (!job.f64 && P.nt == 0 && rf[3 * MAXV] == 1 && rg[3 * MAXV] == 1) ? 1 : 0;
   // ---- path (Sec. 3.2: the density of the product decides)
   if (job.poisson) {
-    P.path = PATH_HASH;
+    // the lookup array of Sec. 3.1 receives both the sum and the difference
+    const bool fits = (double)P.krange * 8.0 <= (double)DENSE_POISSON_MAX_BYTES;
+    if (o.path == KR_PATH_DENSE) {
+      if (!fits) { pl.st = KR_ERR_INVALID; return; }
+      P.path = PATH_DENSE;
+    } else if (o.path == KR_PATH_HASH) {
+      P.path = PATH_HASH;
+    } else {
+      const bool dense_enough = (double)P.krange <= DENSE_POISSON_KAPPA * 2.0 * pairs + 65536.0;
+      P.path = (fits && dense_enough) ? PATH_DENSE : PATH_HASH;
+    }
   } else if (o.path == KR_PATH_DENSE) {
     if ((double)P.krange * 8.0 > (double)DENSE_MAX_BYTES) { pl.st = KR_ERR_INVALID; return; }
     P.path = PATH_DENSE;
@@ -133,7 +143,17 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     pl.op_bytes[which] = op.n * (8 * 7 + 1) + 8 * 256;
   }
   // ---- accumulators
-  if (P.path == PATH_DENSE) {
+  if (P.path == PATH_DENSE && P.nt > 0) {
+    // Poisson series on the dense path: tiles of term pairs add into the array
+    P.tile_i = HASH_TILE_I;
+    P.tile_j = HASH_TILE_J;
+    P.tiles_j = ceil_div(ng, HASH_TILE_J);
+    P.ntasks = ceil_div(nf, HASH_TILE_I) * P.tiles_j;
+    pl.accum_bytes = P.krange * 8;
+    P.chunk = COMPACT_CHUNK;
+    P.nchunks = ceil_div(P.krange, P.chunk);
+    pl.out_cap = (int64_t)std::min((double)P.krange, 2.0 * pairs);
+  } else if (P.path == PATH_DENSE) {
     int64_t S = o.block_slots > 0 ? o.block_slots : DEFAULT_S;
     if (S < 256) S = 256;
     if (S > MAX_S) S = MAX_S;

@@ -17,6 +17,10 @@ namespace kr {
 // O(W), Sec. 3.2).
 constexpr int64_t DENSE_MAX_BYTES = int64_t(16) << 30;
 constexpr double DENSE_KAPPA = 4.0;
+// Poisson series on the dense path: the array may reach 48 GiB, and the code
+// range may be sixteen times the number of updates (two per term pair)
+constexpr int64_t DENSE_POISSON_MAX_BYTES = int64_t(48) << 30;
+constexpr double DENSE_POISSON_KAPPA = 16.0;
 constexpr int64_t BITMAP_MAX_BITS = 1600000;   // on-chip bitmap sort (<= 200 KB)
 constexpr int64_t BITONIC_MAX_N = 16384;       // shared-memory bitonic sort (128 KB)
 constexpr int64_t DEFAULT_S = 8192;            // dense block: 64 KB of shared memory

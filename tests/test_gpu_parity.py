@@ -86,15 +86,19 @@ def test_cfg4_reduced_full_compare(kron):
     """cfg4's distributions at 1600 terms per operand, every output term compared."""
     f, g = workload_cfg4(1600)
     r = oracle.poisson_mul(f, g, nthreads=NT, keep_zero=True)
-    out = run_pseries(kron, f, g)
-    assert_pseries_close(out, r, REL, "cfg4 n=1600")
+    for path in (kron.KR_PATH_DENSE, kron.KR_PATH_HASH):
+        out = run_pseries(kron, f, g, path=path)
+        assert_pseries_close(out, r, REL, f"cfg4 n=1600 path={path}")
 
 
 def test_cfg4_full_size_sampled_shard(kron):
     """Full cfg4 (20000 x 20000 terms) on the GPU; one 1/4096 slice of the output
     keys (FNV-1a shard) recomputed exactly by the oracle."""
     f, g = workload_cfg4()
-    out = run_pseries(kron, f, g)
+    out = run_pseries(kron, f, g)                                   # dense path (AUTO)
+    outh = run_pseries(kron, f, g, path=kron.KR_PATH_HASH)
+    assert np.array_equal(out[0], outh[0]) and np.array_equal(out[1], outh[1])
+    assert np.array_equal(out[2], outh[2])
     ge, gt, gk, gc = out
     keys = np.concatenate([gk.astype(np.int32)[None, :], gt, ge], axis=0).T
     mod, sid = 4096, 17
@@ -160,9 +164,10 @@ def test_random_pseries(kron, case):
     f = random_pseries(np_, nt, nf, pr, tr, 3000 + case)
     g = random_pseries(np_, nt, ng, pr, tr, 4000 + case)
     r = oracle.poisson_mul(f, g, nthreads=NT, keep_zero=True)
-    for device_inputs in (True, False):
-        out = run_pseries(kron, f, g, device_inputs)
-        assert_pseries_close(out, r, REL, f"pseries case {case} dev={device_inputs}")
+    for path in (kron.KR_PATH_AUTO, kron.KR_PATH_DENSE, kron.KR_PATH_HASH):
+        for device_inputs in (True, False):
+            out = run_pseries(kron, f, g, device_inputs, path=path)
+            assert_pseries_close(out, r, REL, f"pseries case {case} path={path} dev={device_inputs}")
 
 
 def test_werner_special_cases_on_gpu(kron):
