@@ -200,7 +200,7 @@ def main():
     import ctypes
     import paper_1004_4548_gb300 as kron
     from paper_1004_4548_gb300 import binding as B
-    from workloads import workload_cfg2, workload_cfg3, workload_cfg4, PSeries
+    from workloads import workload_cfg2, workload_cfg3, workload_cfg4, PSeries, fateman
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -331,6 +331,13 @@ def main():
                                        max(3, args.steps // 2))
         f4, g4 = workload_cfg4()
         paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3)
+        paths["poisson_cfg4_hash"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3,
+                                                  path=kron.KR_PATH_HASH)
+        fa, ga = fateman()
+        paths["fateman_full"] = time_poly(kron, ctx, fa, ga, dev, stream, flush, "dense_accum", 5)
+        paths["fateman_full"]["context"] = ("Fateman's benchmark, (1+x+y+z+t)^30 times itself plus one, "
+                                            "true coefficients modulo 2^64; the paper's Table 5: 4.29 s "
+                                            "on one Core2Quad core with double coefficients")
         ctx.set_profiling(False)
 
     batched = None
@@ -539,18 +546,19 @@ def time_poly(kron, ctx, f, g, dev, stream, flush, kernel, steps):
             "kernel_rate": tp / (kms * 1e-3) / 1e6, "stages_ms_last_step": dict(ctx.stages())}
 
 
-def time_pseries(kron, ctx, f, g, dev, stream, flush, steps):
+def time_pseries(kron, ctx, f, g, dev, stream, flush, steps, path=0):
     import torch
     from workloads import PSeries
     F = PSeries(*(torch.from_numpy(x).to(dev) for x in (f.exps, f.trig, f.kind, f.coef)))
     G = PSeries(*(torch.from_numpy(x).to(dev) for x in (g.exps, g.trig, g.kind, g.coef)))
-    out = kron.poisson_mul(F, G, ctx=ctx)
+    out = kron.poisson_mul(F, G, ctx=ctx, path=path)
+    kernel = "hash_insert"
     times, kt = [], []
     for _ in range(steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        out = kron.poisson_mul(F, G, ctx=ctx, capacity=int(out[3].shape[0]))
+        out = kron.poisson_mul(F, G, ctx=ctx, capacity=int(out[3].shape[0]), path=path)
         b.record(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from gpu_compare import (assert_poly_close, assert_poly_equal, assert_pseries_close, to_np)
-from workloads import (PSeries, Poly, Rng, poisson_random, random_poly, random_pseries,
+from workloads import (PSeries, Poly, Rng, fateman, poisson_random, random_poly, random_pseries,
                        workload_cfg1, workload_cfg2, workload_cfg3, workload_cfg4)
 
 pytestmark = pytest.mark.gpu
@@ -107,6 +107,23 @@ def test_cfg4_full_size_sampled_shard(kron):
     r = oracle.poisson_mul(f, g, nthreads=NT, shard=(mod, sid), keep_zero=True)
     assert r.coef.shape[0] > 1000
     assert_pseries_close((ge[:, sel], gt[:, sel], gk[sel], gc[sel]), r, REL, "cfg4 shard")
+
+
+def test_fateman_full_size_mod_2_64(kron):
+    """Fateman's benchmark at full size (Sec. 5): (1+x+y+z+t)^30 times itself plus one,
+    46376 x 46376 terms, the true multinomial coefficients.  The sums exceed int64;
+    both sides reduce them modulo 2^64.  Every output term's exponents, the closed-form
+    count C(4 + 60, 4), and a 1/997 slice of the coefficients are checked against the
+    oracle (exact 128-bit sums, reduced)."""
+    f, g = fateman()
+    ex, cf = run_poly(kron, f, g)
+    assert ex.shape[1] == math.comb(64, 4) == 635376
+    assert (ex.sum(axis=0) <= 60).all() and (ex >= 0).all()
+    mod, sid = 997, 5
+    sel = oracle.shard_of_keys(np.ascontiguousarray(ex.T), mod) == sid
+    r = oracle.poly_mul(f, g, nthreads=NT, shard=(mod, sid))
+    assert r.overflow and r.coef.shape[0] > 300
+    assert_poly_equal(ex[:, sel], cf[sel], r, "fateman slice")
 
 
 # ---------------------------------------------------------------------------

@@ -14,7 +14,7 @@ import pytest
 import oracle
 from pins import (M61, as_dict, box_convolution, eval_mod_m31, eval_mod_p,
                   eval_pseries)
-from workloads import (PSeries, Poly, Rng, dense_total_degree, random_poly,
+from workloads import (PSeries, Poly, Rng, dense_total_degree, fateman, random_poly,
                        random_pseries, total_degree_tuples, workload_cfg1,
                        workload_cfg2, workload_cfg3)
 
@@ -224,6 +224,26 @@ def test_oracle_cfg3_support_and_eval():
         pt = [int(x) for x in rng.ints(2, (1 << 31) - 2, 5)]
         assert eval_mod_m31(r.exps, r.coef, pt) == \
             eval_mod_m31(f.exps, f.coef, pt) * eval_mod_m31(g.exps, g.coef, pt) % ((1 << 31) - 1)
+
+
+def test_fateman_operands_and_small_product():
+    """Fateman's operands (Sec. 5) are (1+x+y+z+t)^n and that plus one: their
+    evaluations at a point are closed forms, and so is the product's."""
+    M = (1 << 31) - 1
+    f, g = fateman(30)
+    assert f.n == g.n == math.comb(34, 4) == 46376
+    assert int(f.coef.astype(np.uint64).sum(dtype=np.uint64)) == 5 ** 30 % (1 << 64)
+    f, g = fateman(6)
+    r = oracle.poly_mul(f, g)
+    assert r.coef.shape[0] == math.comb(4 + 12, 4) and not r.overflow
+    rng = Rng(3131)
+    for _ in range(3):
+        pt = [int(x) for x in rng.ints(2, M - 1, 4)]
+        s = (1 + sum(pt)) % M
+        fv = pow(s, 6, M)
+        assert eval_mod_m31(f.exps, f.coef, pt) == fv
+        assert eval_mod_m31(g.exps, g.coef, pt) == (fv + 1) % M
+        assert eval_mod_m31(r.exps, r.coef, pt) == fv * (fv + 1) % M
 
 
 def test_oracle_int64_wraps_and_flags_overflow():

@@ -237,6 +237,33 @@ def workload_cfg4(n: int = 20000):
             poisson_random(n, 3, 4, 4, 8, 4002))
 
 
+def fateman(power: int = 30, seed: int = 6001):
+    """Fateman's benchmark operands: f = (1 + x + y + z + t)^power, g = f + 1.
+
+    The coefficients are the multinomial coefficients of the expansion, reduced
+    modulo 2^64 into int64 (the library's integer arithmetic wraps modulo 2^64).
+    Terms in a seeded random order.
+    """
+    rows = total_degree_tuples(4, power)
+    # multinomial coefficient power! / (a! b! c! d! e!) with e = power - a - b - c - d
+    fact = [1]
+    for k in range(1, power + 1):
+        fact.append(fact[-1] * k)
+    coef = []
+    for a, b, c, d in rows.tolist():
+        e = power - a - b - c - d
+        m = fact[power] // (fact[a] * fact[b] * fact[c] * fact[d] * fact[e])
+        m %= 1 << 64
+        coef.append(m - (1 << 64) if m >= 1 << 63 else m)
+    coef = np.array(coef, dtype=np.int64)
+    gcoef = coef.copy()
+    zero = np.nonzero((rows == 0).all(axis=1))[0][0]
+    gcoef[zero] = np.int64((int(gcoef[zero]) + 1 + (1 << 63)) % (1 << 64) - (1 << 63))
+    rng = Rng(seed)
+    pf, pg = rng.perm(rows.shape[0]), rng.perm(rows.shape[0])
+    return Poly(_soa(rows[pf]), coef[pf]), Poly(_soa(rows[pg]), gcoef[pg])
+
+
 def _batch_operand(rng: Rng, v: int, poisson: bool):
     lo, hi = math.log(50.0), math.log(20000.0)
     n = int(round(math.exp(lo + (hi - lo) * float(rng.uniform(1)[0]))))
