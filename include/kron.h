@@ -34,7 +34,8 @@
  *   - Canonical output: terms sorted by ascending code (reverse lexicographic
  *     exponent order, variable 0 least significant; Poisson keys ordered by
  *     kind (cos < sin), then trig multipliers, then exponents), no zero
- *     coefficients.  int64 coefficients use wrapping arithmetic modulo 2^64.
+ *     coefficients; a truncated product is sorted by degree first (kr_opts).
+ *     int64 coefficients use wrapping arithmetic modulo 2^64.
  *   - Trig canonical form: a multiplier vector is canonical when its
  *     highest-index nonzero entry is positive.  Inputs must be canonical and a
  *     sine may not have the zero vector (KR_ERR_INVALID otherwise).  Results
@@ -131,6 +132,24 @@ typedef struct {
                             to the term-product bound); 0 = 4, <0 = none */
   int64_t table_slots;   /* hash path: initial table slots (power of two), 0 = sized
                             from the term-product bound and load_factor */
+  /* Truncated multiplication (Sec. 3: truncation by the exponents of one or
+   * more polynomial variables).  With truncate = 1 the product keeps only the
+   * terms whose degree in the variables of trunc_mask (the sum of their
+   * exponents; bit k = polynomial variable k, 0 = all of them) is at most
+   * trunc_degree, which may be negative.  Degree is additive, so these are
+   * exactly the terms of the full product of that degree, and a term pair of
+   * higher degree is never formed: the degree becomes the most significant
+   * digit of the code (the highest-index variable of the mask is replaced by
+   * the degree; the map stays one to one), the truncation becomes an upper
+   * bound on the output code, and the pairs below it are, for each term of
+   * f, a prefix of g's sorted codes.  Terms of an operand whose degree alone
+   * leaves no partner are dropped before the multiplication.  The output is
+   * sorted by that graded code: by degree first, then as usual (reverse
+   * lexicographic, variable 0 least significant) over the other variables.
+   * For Poisson series the degree is that of the polynomial part. */
+  int32_t truncate;
+  uint32_t trunc_mask;
+  int64_t trunc_degree;
 } kr_opts;
 
 /* ------------------------------------------------------------------------ */

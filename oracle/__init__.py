@@ -48,6 +48,11 @@ def _lib(plant: int = 0) -> ctypes.CDLL:
             L.orc_poisson_mul.restype = vp
             L.orc_poisson_mul.argtypes = [i32, i32, i64, vp, vp, vp, vp, i64, vp, vp, vp, vp,
                                           i32, i64, i64, i32]
+            u32 = ctypes.c_uint32
+            L.orc_poly_mul_trunc.restype = vp
+            L.orc_poly_mul_trunc.argtypes = L.orc_poly_mul.argtypes + [u32, i64]
+            L.orc_poisson_mul_trunc.restype = vp
+            L.orc_poisson_mul_trunc.argtypes = L.orc_poisson_mul.argtypes + [u32, i64]
             L.orc_result_nterms.restype = i64
             L.orc_result_nterms.argtypes = [vp]
             L.orc_result_overflow.restype = i32
@@ -83,9 +88,17 @@ class PSeriesResult:
     mass: np.ndarray          # float64 [n]
 
 
+def _trunc_mask(trunc, nv):
+    deg, mask = trunc
+    return (int(mask) if mask else (1 << nv) - 1), int(deg)
+
+
 def poly_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
-             keep_zero: bool = False, plant: int = 0) -> PolyResult:
-    """h = f * g by the definition.  f, g: objects with .exps [v, n] int32, .coef."""
+             keep_zero: bool = False, plant: int = 0, trunc=None) -> PolyResult:
+    """h = f * g by the definition.  f, g: objects with .exps [v, n] int32, .coef.
+
+    trunc = (N, mask): keep the pairs whose product term has degree <= N in the
+    variables of the bit mask (0 = all variables)."""
     L = _lib(plant)
     is_f64 = f.coef.dtype == np.float64
     ef = np.ascontiguousarray(f.exps, dtype=np.int32)
@@ -94,8 +107,12 @@ def poly_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
     cf = np.ascontiguousarray(f.coef, dtype=dt)
     cg = np.ascontiguousarray(g.coef, dtype=dt)
     nv = ef.shape[0]
-    r = L.orc_poly_mul(nv, cf.shape[0], _p(ef), _p(cf), cg.shape[0], _p(eg), _p(cg),
-                       int(is_f64), nthreads, shard[0], shard[1], int(keep_zero))
+    args = (nv, cf.shape[0], _p(ef), _p(cf), cg.shape[0], _p(eg), _p(cg),
+            int(is_f64), nthreads, shard[0], shard[1], int(keep_zero))
+    if trunc is None:
+        r = L.orc_poly_mul(*args)
+    else:
+        r = L.orc_poly_mul_trunc(*args, *_trunc_mask(trunc, nv))
     if not r:
         raise ValueError("oracle rejected the arguments")
     try:
@@ -110,16 +127,22 @@ def poly_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
 
 
 def poisson_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
-                keep_zero: bool = False, plant: int = 0) -> PSeriesResult:
-    """h = f * g for Poisson series, by the product-to-sum identities."""
+                keep_zero: bool = False, plant: int = 0, trunc=None) -> PSeriesResult:
+    """h = f * g for Poisson series, by the product-to-sum identities.
+
+    trunc = (N, mask) truncates by the degree of the polynomial part."""
     L = _lib(plant)
     np_, nt = f.exps.shape[0], f.trig.shape[0]
     a = [np.ascontiguousarray(x) for x in (f.exps.astype(np.int32), f.trig.astype(np.int32),
                                            f.kind.astype(np.uint8), f.coef.astype(np.float64))]
     b = [np.ascontiguousarray(x) for x in (g.exps.astype(np.int32), g.trig.astype(np.int32),
                                            g.kind.astype(np.uint8), g.coef.astype(np.float64))]
-    r = L.orc_poisson_mul(np_, nt, a[3].shape[0], *[_p(x) for x in a], b[3].shape[0],
-                          *[_p(x) for x in b], nthreads, shard[0], shard[1], int(keep_zero))
+    args = (np_, nt, a[3].shape[0], *[_p(x) for x in a], b[3].shape[0],
+            *[_p(x) for x in b], nthreads, shard[0], shard[1], int(keep_zero))
+    if trunc is None:
+        r = L.orc_poisson_mul(*args)
+    else:
+        r = L.orc_poisson_mul_trunc(*args, *_trunc_mask(trunc, np_))
     if not r:
         raise ValueError("oracle rejected the arguments")
     try:

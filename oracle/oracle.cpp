@@ -33,6 +33,12 @@
 // summation (Neumaier 1974); the sum of |contribution| per key is returned too,
 // since the parity tolerance is relative to it.
 //
+// Truncation (Sec. 3 names truncation by the exponents of one or more
+// polynomial variables): with a degree bound N over a set of polynomial
+// variables, a pair of terms contributes only when the degree of its product
+// term in those variables (the sum of their exponents) is at most N.  The
+// oracle forms every pair and skips the ones above the bound.
+//
 // Parallelism: the f terms are split into contiguous slices, one map per
 // thread, maps merged at the end.  An optional shard filter keeps only the
 // output keys whose FNV-1a hash is congruent to shard_id modulo shard_mod, so
@@ -144,6 +150,25 @@ void run_threads(int nthreads, int64_t nf, F body) {
   for (auto& x : th) x.join();
 }
 
+// Degree truncation: on = 0 keeps every term.
+struct Trunc {
+  int on = 0;
+  uint32_t mask = 0;   // bit k: polynomial variable k counts
+  int64_t N = 0;
+};
+
+// Degree of the polynomial part poly[0..np) in the truncation variables.
+bool above_bound(const Trunc& T, const int32_t* poly, int np) {
+  if (!T.on) return false;
+  int64_t d = 0;
+  for (int k = 0; k < np; ++k)
+    if ((T.mask >> k) & 1u) d += poly[k];
+#if ORC_PLANT == 7
+  return d >= T.N;   // planted: the bound itself excluded
+#endif
+  return d > T.N;
+}
+
 #ifndef ORC_PLANT
 #define ORC_PLANT 0   // 0 = the oracle; k > 0 plants mistake k (mutation tests only)
 #endif
@@ -154,7 +179,7 @@ void run_threads(int nthreads, int64_t nf, F body) {
 template <class Acc, class Coef>
 void poly_slice(int nv, const int32_t* ef, const Coef* cf, int64_t nf, int64_t i0, int64_t i1,
                 const int32_t* eg, const Coef* cg, int64_t ng, int64_t smod, int64_t sid,
-                TermMap<Acc>& map) {
+                const Trunc& T, TermMap<Acc>& map) {
   Key key;
   std::memset(&key, 0, sizeof key);
   int64_t jend = ng;
@@ -167,6 +192,7 @@ void poly_slice(int nv, const int32_t* ef, const Coef* cf, int64_t nf, int64_t i
 #if ORC_PLANT == 6
       key.c[0] = ef[i] + ef[i];   // planted: uses f's first exponent twice
 #endif
+      if (above_bound(T, key.c, nv)) continue;
       if (!in_shard(key, nv, smod, sid)) continue;
       auto it = map.find(key);
       if (it == map.end()) it = map.emplace(key, Acc()).first;
@@ -181,7 +207,7 @@ void poly_slice(int nv, const int32_t* ef, const Coef* cf, int64_t nf, int64_t i
 
 Result* poly_mul(int nv, int64_t nf, const int32_t* ef, const void* cfv, int64_t ng,
                  const int32_t* eg, const void* cgv, int is_f64, int nthreads, int64_t smod,
-                 int64_t sid, int keep_zero) {
+                 int64_t sid, int keep_zero, const Trunc& T) {
   KeyLess L = poly_order(nv);
   Result* R = new Result;
   R->np = nv; R->nt = 0; R->poisson = false; R->is_f64 = is_f64 != 0;
@@ -190,7 +216,7 @@ Result* poly_mul(int nv, int64_t nf, const int32_t* ef, const void* cfv, int64_t
     std::vector<TermMap<AccI>> maps(nthreads, TermMap<AccI>(L));
     auto cf = (const int64_t*)cfv; auto cg = (const int64_t*)cgv;
     run_threads(nthreads, nf, [&](int t, int64_t a, int64_t b) {
-      poly_slice<AccI, int64_t>(nv, ef, cf, nf, a, b, eg, cg, ng, smod, sid, maps[t]);
+      poly_slice<AccI, int64_t>(nv, ef, cf, nf, a, b, eg, cg, ng, smod, sid, T, maps[t]);
     });
     for (int t = 1; t < nthreads; ++t)
       for (auto& kv : maps[t]) maps[0][kv.first].s += kv.second.s;
@@ -206,7 +232,7 @@ Result* poly_mul(int nv, int64_t nf, const int32_t* ef, const void* cfv, int64_t
     std::vector<TermMap<AccF>> maps(nthreads, TermMap<AccF>(L));
     auto cf = (const double*)cfv; auto cg = (const double*)cgv;
     run_threads(nthreads, nf, [&](int t, int64_t a, int64_t b) {
-      poly_slice<AccF, double>(nv, ef, cf, nf, a, b, eg, cg, ng, smod, sid, maps[t]);
+      poly_slice<AccF, double>(nv, ef, cf, nf, a, b, eg, cg, ng, smod, sid, T, maps[t]);
     });
     for (int t = 1; t < nthreads; ++t)
       for (auto& kv : maps[t]) maps[0][kv.first].merge(kv.second);
@@ -259,11 +285,16 @@ void emit(TermMap<AccF>& map, Key& key, int np, int nt, double coef, int64_t smo
 }
 
 void poisson_slice(int np, int nt, const PSIn& F, const PSIn& G, int64_t i0, int64_t i1,
-                   int64_t smod, int64_t sid, TermMap<AccF>& map) {
+                   int64_t smod, int64_t sid, const Trunc& T, TermMap<AccF>& map) {
   Key key;
   std::memset(&key, 0, sizeof key);
   for (int64_t i = i0; i < i1; ++i) {
     for (int64_t j = 0; j < G.n; ++j) {
+      if (T.on) {   // both terms of the pair share the polynomial part
+        int32_t poly[MAXK];
+        for (int k = 0; k < np; ++k) poly[k] = F.e[(int64_t)k * F.n + i] + G.e[(int64_t)k * G.n + j];
+        if (above_bound(T, poly, np)) continue;
+      }
       double h = (F.c[i] * G.c[j]) * 0.5;
 #if ORC_PLANT == 1
       h = F.c[i] * G.c[j];   // planted: the product-to-sum halves dropped
@@ -301,14 +332,14 @@ void poisson_slice(int np, int nt, const PSIn& F, const PSIn& G, int64_t i0, int
 }
 
 Result* poisson_mul(int np, int nt, const PSIn& F, const PSIn& G, int nthreads, int64_t smod,
-                    int64_t sid, int keep_zero) {
+                    int64_t sid, int keep_zero, const Trunc& T) {
   KeyLess L = poisson_order(np, nt);
   Result* R = new Result;
   R->np = np; R->nt = nt; R->poisson = true; R->is_f64 = true;
   if (nthreads < 1) nthreads = 1;
   std::vector<TermMap<AccF>> maps(nthreads, TermMap<AccF>(L));
   run_threads(nthreads, F.n, [&](int t, int64_t a, int64_t b) {
-    poisson_slice(np, nt, F, G, a, b, smod, sid, maps[t]);
+    poisson_slice(np, nt, F, G, a, b, smod, sid, T, maps[t]);
   });
   for (int t = 1; t < nthreads; ++t)
     for (auto& kv : maps[t]) maps[0][kv.first].merge(kv.second);
@@ -333,7 +364,19 @@ void* orc_poly_mul(int nv, int64_t nf, const int32_t* ef, const void* cf, int64_
                    const int32_t* eg, const void* cg, int is_f64, int nthreads,
                    int64_t shard_mod, int64_t shard_id, int keep_zero) {
   if (nv < 1 || nv > MAXK || nf < 0 || ng < 0) return nullptr;
-  return poly_mul(nv, nf, ef, cf, ng, eg, cg, is_f64, nthreads, shard_mod, shard_id, keep_zero);
+  return poly_mul(nv, nf, ef, cf, ng, eg, cg, is_f64, nthreads, shard_mod, shard_id, keep_zero, Trunc());
+}
+
+// As orc_poly_mul, keeping only the pairs whose product term has degree at
+// most max_degree in the variables of mask (bit k = variable k).
+void* orc_poly_mul_trunc(int nv, int64_t nf, const int32_t* ef, const void* cf, int64_t ng,
+                         const int32_t* eg, const void* cg, int is_f64, int nthreads,
+                         int64_t shard_mod, int64_t shard_id, int keep_zero, uint32_t mask,
+                         int64_t max_degree) {
+  if (nv < 1 || nv > MAXK || nf < 0 || ng < 0) return nullptr;
+  Trunc T;
+  T.on = 1; T.mask = mask; T.N = max_degree;
+  return poly_mul(nv, nf, ef, cf, ng, eg, cg, is_f64, nthreads, shard_mod, shard_id, keep_zero, T);
 }
 
 // Product of two Poisson series with np polynomial variables and nt trig
@@ -344,7 +387,20 @@ void* orc_poisson_mul(int np, int nt, int64_t nf, const int32_t* ef, const int32
                       int64_t shard_mod, int64_t shard_id, int keep_zero) {
   if (np < 0 || nt < 1 || 1 + np + nt > MAXK || nf < 0 || ng < 0) return nullptr;
   PSIn F{nf, ef, tf, kf, cf}, G{ng, eg, tg, kg, cg};
-  return poisson_mul(np, nt, F, G, nthreads, shard_mod, shard_id, keep_zero);
+  return poisson_mul(np, nt, F, G, nthreads, shard_mod, shard_id, keep_zero, Trunc());
+}
+
+// As orc_poisson_mul with the polynomial part truncated as in orc_poly_mul_trunc.
+void* orc_poisson_mul_trunc(int np, int nt, int64_t nf, const int32_t* ef, const int32_t* tf,
+                            const uint8_t* kf, const double* cf, int64_t ng, const int32_t* eg,
+                            const int32_t* tg, const uint8_t* kg, const double* cg, int nthreads,
+                            int64_t shard_mod, int64_t shard_id, int keep_zero, uint32_t mask,
+                            int64_t max_degree) {
+  if (np < 1 || nt < 1 || 1 + np + nt > MAXK || nf < 0 || ng < 0) return nullptr;
+  PSIn F{nf, ef, tf, kf, cf}, G{ng, eg, tg, kg, cg};
+  Trunc T;
+  T.on = 1; T.mask = mask; T.N = max_degree;
+  return poisson_mul(np, nt, F, G, nthreads, shard_mod, shard_id, keep_zero, T);
 }
 
 int64_t orc_result_nterms(const void* r) { return (int64_t)((const Result*)r)->keys.size(); }

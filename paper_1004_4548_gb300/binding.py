@@ -47,7 +47,8 @@ class kr_pseries_out(ctypes.Structure):
 class kr_opts(ctypes.Structure):
     _fields_ = [("path", _i32), ("block_slots", _i32), ("load_factor", ctypes.c_double),
                 ("probe_limit", _i32), ("unsorted", _i32), ("max_regrow", _i32),
-                ("table_slots", _i64)]
+                ("table_slots", _i64), ("truncate", _i32), ("trunc_mask", ctypes.c_uint32),
+                ("trunc_degree", _i64)]
 
 
 class kr_job(ctypes.Structure):
@@ -175,8 +176,12 @@ def _stream_ptr(stream):
 
 
 def _opts(path=0, block_slots=0, load_factor=0.0, probe_limit=0, unsorted=0, max_regrow=0,
-          table_slots=0):
-    return kr_opts(path, block_slots, load_factor, probe_limit, unsorted, max_regrow, table_slots)
+          table_slots=0, trunc_degree=None, trunc_mask=0):
+    """kr_opts from keywords; trunc_degree (an int) asks for the truncated product
+    of degree <= trunc_degree in the variables of trunc_mask (0 = all)."""
+    t = trunc_degree is not None
+    return kr_opts(path, block_slots, load_factor, probe_limit, unsorted, max_regrow, table_slots,
+                   1 if t else 0, int(trunc_mask) if t else 0, int(trunc_degree) if t else 0)
 
 
 class Context:

@@ -248,6 +248,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       P.np = jobs[p].np;
       P.nt = jobs[p].nt;
       P.f64 = jobs[p].f64;
+      if (jobs[p].opts.truncate && P.np > 0) {
+        // the range scan also measures the degree range of the mask
+        uint32_t m = jobs[p].opts.trunc_mask ? jobs[p].opts.trunc_mask : 0xffffffffu;
+        if (P.np < 32) m &= (1u << P.np) - 1u;
+        P.gmask = m;
+      }
       hprods[p] = P;
       hops[2 * p] = OpRef{p, 0};
       hops[2 * p + 1] = OpRef{p, 1};
@@ -279,6 +285,11 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   std::vector<int> live_ids, dense_ids, hash_ids, hll_ids;
   for (int p = 0; p < nprod; ++p) {
     if (plans[p].st != KR_OK) continue;
+    if (plans[p].empty) {   // truncated to nothing: a zero product
+      res[p].n = 0;
+      res[p].prod = plans[p].p;
+      continue;
+    }
     live_ids.push_back(p);
     const bool block = plans[p].p.path == PATH_DENSE && plans[p].p.nt == 0;
     (block ? dense_ids : hash_ids).push_back(p);
@@ -466,6 +477,8 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Plan& pl = plans[live_ids[q]];
       pl.p.status = hl[q].status;
       pl.p.hll_est = hl[q].hll_est;
+      pl.p.f.nkeep = hl[q].f.nkeep;
+      pl.p.g.nkeep = hl[q].g.nkeep;
     }
   }
   // ---------------- phase B2, repeated for products whose table filled up
@@ -679,6 +692,10 @@ kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
   for (int k = 0; k < P.np; ++k) {
     h->omin[k] = P.omin[k];
     h->omax[k] = P.omin[k] + P.w[k] - 1;
+  }
+  if (P.graded) {   // a truncated product: the range of the variable itself
+    h->omin[P.gvar] = P.gvar_min;
+    h->omax[P.gvar] = P.gvar_max;
   }
   if (n > h->capacity) return KR_ERR_CAPACITY;
   if (n == 0) return KR_OK;

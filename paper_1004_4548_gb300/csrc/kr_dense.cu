@@ -41,10 +41,12 @@ __global__ void __launch_bounds__(256) k_dense_plan(const Prod* __restrict__ pro
   const Prod& P = prods[pid];
   if (P.status) return;
   const int64_t b = gw - block_begin[lo];
-  const int64_t B = b * P.S, E = B + P.S;
+  // a truncated product's code range ends inside its last block
+  const int64_t B = b * P.S, E = min(B + P.S, P.krange);
   const int64_t* F = P.f.code;
   const int64_t* G = P.g.code;
-  const int64_t nf = P.f.n, ng = P.g.n;
+  const int64_t nf = P.f.nkeep, ng = P.g.nkeep;   // dropped terms sort last
+  if (nf <= 0 || ng <= 0) return;
   const int64_t i_lo = lower_bound_i64(F, nf, B - G[ng - 1]);
   const int64_t i_hi = lower_bound_i64(F, nf, E - G[0]);
   const int32_t* gx = P.gidx;
@@ -181,6 +183,8 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
   constexpr unsigned FULL = 0xffffffffu;
   const int64_t S = P.S;
   const int64_t B = tk.block * S;
+  // pairs land in [B, B + lim): the block, clipped to the code range
+  const int64_t lim = min(S, P.krange - B);
   const int64_t* __restrict__ F = P.f.code;
   const int64_t* __restrict__ G = P.g.code;
   const int32_t* __restrict__ G32 = P.g.code32;
@@ -193,7 +197,7 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
     if (i < tk.i1) {
       const int64_t fi = F[i] - B;
       const int64_t l = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, -fi);
-      const int64_t h = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, S - fi);
+      const int64_t h = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, lim - fi);
       ct.f32[threadIdx.x] = (int32_t)fi;
       ct.lo[threadIdx.x] = (int32_t)l;
       cnt = (int32_t)(h - l);

@@ -10,6 +10,8 @@
 // |t_k| <= R_k; sums and differences of such codes are the codes of the sums
 // and differences of the vectors, and the sign of a code is the sign of the
 // highest-index nonzero entry, which is what the canonical form looks at.
+#include <climits>
+
 #include "kr_internal.cuh"
 
 namespace kr {
@@ -66,6 +68,32 @@ __global__ void __launch_bounds__(512) k_range_scan(const Prod* __restrict__ pro
     else { out[2 * MAXV + (k - P.np)] = hi; }
   }
   if (threadIdx.x == 0) out[3 * MAXV] = fits_all;
+  if (P.gmask) {
+    // least and largest degree in the truncation variables (int64 sums)
+    __shared__ long long dlo_s, dhi_s;
+    if (threadIdx.x == 0) { dlo_s = LLONG_MAX; dhi_s = LLONG_MIN; }
+    __syncthreads();
+    long long dlo = LLONG_MAX, dhi = LLONG_MIN;
+    for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x) {
+      long long d = 0;
+      for (int k = 0; k < P.np; ++k)
+        if ((P.gmask >> k) & 1u) d += O.e[(int64_t)k * O.n + i];
+      dlo = min(dlo, d);
+      dhi = max(dhi, d);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dlo = min(dlo, __shfl_xor_sync(0xffffffffu, dlo, o));
+      dhi = max(dhi, __shfl_xor_sync(0xffffffffu, dhi, o));
+    }
+    if (lane == 0) { atomicMin(&dlo_s, dlo); atomicMax(&dhi_s, dhi); }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const bool over = dlo_s < INT32_MIN || dhi_s > INT32_MAX;
+      out[3 * MAXV + 1] = over ? 0 : (int32_t)dlo_s;
+      out[3 * MAXV + 2] = over ? 0 : (int32_t)dhi_s;
+      out[3 * MAXV + 3] = over ? 1 : 0;
+    }
+  }
 }
 
 cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int32_t* dranges,
@@ -84,15 +112,27 @@ struct TermCode {
   int64_t tcode;
   int kind;
   uint32_t bad;   // status bits
+  bool drop;      // truncated product: the term's degree leaves it no partner
 };
 
 __device__ __forceinline__ TermCode encode_term(const Prod& P, const Operand& O, int64_t i) {
   TermCode tc;
-  tc.pcode = 0; tc.tcode = 0; tc.kind = 0; tc.bad = 0;
+  tc.pcode = 0; tc.tcode = 0; tc.kind = 0; tc.bad = 0; tc.drop = false;
+  int64_t deg = 0;
   for (int k = 0; k < P.np; ++k) {
     int32_t e = O.e[(int64_t)k * O.n + i];
+    if (P.graded) {
+      if ((P.gmask >> k) & 1u) deg += e;
+      if (k == P.gvar) continue;   // its digit is the degree
+    }
     if (e < O.emin[k] || e > O.emax[k]) tc.bad |= ST_RANGE;
     tc.pcode += P.c[k] * (int64_t)(e - O.emin[k]);
+  }
+  if (P.graded) {
+    const int r = P.gvar;
+    if (deg < O.emin[r]) tc.bad |= ST_RANGE;
+    if (deg > O.emax[r]) tc.drop = true;   // above the operand's degree limit
+    else tc.pcode += P.c[r] * (deg - O.emin[r]);
   }
   if (P.nt > 0) {
     for (int k = 0; k < P.nt; ++k) {
@@ -124,7 +164,7 @@ __global__ void __launch_bounds__(256) k_encode(Prod* __restrict__ prods, const 
        i += (int64_t)gridDim.x * blockDim.x) {
     TermCode tc = encode_term(P, O, i);
     bad |= tc.bad;
-    uint64_t key = term_key(P, tc);
+    uint64_t key = tc.drop ? (uint64_t)(O.sent + i) : term_key(P, tc);
     if (tc.bad) key = 0;   // keeps later kernels in bounds; the status fails the product
     if (O.sort_method == SORT_BITONIC) {
       O.skey[i] = (key << O.idx_bits) | (uint64_t)i;
@@ -167,7 +207,9 @@ __global__ void __launch_bounds__(256) k_gather(Prod* __restrict__ prods, const 
       src = (int64_t)((const uint64_t*)O.sidx2)[q];
       if (q > 0) prev = O.skey2[q - 1];
     }
-    if (q > 0 && prev == key) bad |= ST_DUP;
+    const bool dropped = key >= (uint64_t)O.sent;   // truncated away (sorted last)
+    if (q > 0 && prev == key && !dropped) bad |= ST_DUP;
+    if (dropped && (q == 0 || prev < (uint64_t)O.sent)) O.nkeep = q;
     if (src < 0 || src >= O.n) { bad |= ST_DUP; src = 0; }
     if (P.nt == 0) {
       O.code[q] = (int64_t)key;
@@ -176,6 +218,7 @@ __global__ void __launch_bounds__(256) k_gather(Prod* __restrict__ prods, const 
       else ((int64_t*)O.coef)[q] = ((const int64_t*)O.c)[src];
     } else {
       TermCode tc = encode_term(P, O, src);
+      if (dropped) { tc.pcode = TRUNC_PSENT; tc.tcode = 0; tc.kind = 0; }
       O.code[q] = tc.pcode;
       O.tcode[q] = tc.tcode;
       O.kind[q] = (uint8_t)tc.kind;
@@ -206,14 +249,7 @@ __global__ void __launch_bounds__(256) k_decode_poly(const Prod* __restrict__ pr
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t code = (int64_t)okey[q];
     if (codes) codes[q] = code;
-    if (exps) {
-      int64_t rem = code;
-      for (int k = 0; k < P.np; ++k) {
-        const int64_t d = (k + 1 < P.np) ? rem % P.w[k] : rem;
-        rem = (k + 1 < P.np) ? rem / P.w[k] : 0;
-        exps[(int64_t)k * ld + q] = (int32_t)(d + P.omin[k]);
-      }
-    }
+    if (exps) decode_poly_part(P, code, exps, ld, q);
   }
 }
 
@@ -243,15 +279,9 @@ __global__ void __launch_bounds__(256) k_decode_pseries(const Prod* __restrict__
     const int64_t kd = key / per_kind;
     const int64_t rem = key - kd * per_kind;
     const int64_t T = rem / P.Wp;
-    int64_t pc = rem - T * P.Wp;
+    const int64_t pc = rem - T * P.Wp;
     if (kind) kind[q] = (uint8_t)kd;
-    if (exps) {
-      for (int k = 0; k < P.np; ++k) {
-        const int64_t d = (k + 1 < P.np) ? pc % P.w[k] : pc;
-        pc = (k + 1 < P.np) ? pc / P.w[k] : 0;
-        exps[(int64_t)k * ld + q] = (int32_t)(d + P.omin[k]);
-      }
-    }
+    if (exps) decode_poly_part(P, pc, exps, ld, q);
     if (trig) {
       int64_t u = T + half;
       for (int k = 0; k < P.nt; ++k) {
@@ -295,24 +325,15 @@ __global__ void __launch_bounds__(256) k_decode_batch(const Prod* __restrict__ p
     const int64_t key = (int64_t)okey[q];
     ((uint64_t*)R.coef)[t] = oval[q];
     if (P.nt == 0) {
-      int64_t rem = key;
-      for (int k = 0; k < P.np; ++k) {
-        const int64_t d = (k + 1 < P.np) ? rem % P.w[k] : rem;
-        rem = (k + 1 < P.np) ? rem / P.w[k] : 0;
-        R.exps[(int64_t)k * R.n + t] = (int32_t)(d + P.omin[k]);
-      }
+      decode_poly_part(P, key, R.exps, R.n, t);
     } else {
       const int64_t per_kind = P.T2 * P.Wp;
       const int64_t kd = key / per_kind;
       const int64_t r2 = key - kd * per_kind;
       const int64_t T = r2 / P.Wp;
-      int64_t pc = r2 - T * P.Wp;
+      const int64_t pc = r2 - T * P.Wp;
       R.kind[t] = (uint8_t)kd;
-      for (int k = 0; k < P.np; ++k) {
-        const int64_t d = (k + 1 < P.np) ? pc % P.w[k] : pc;
-        pc = (k + 1 < P.np) ? pc / P.w[k] : 0;
-        R.exps[(int64_t)k * R.n + t] = (int32_t)(d + P.omin[k]);
-      }
+      if (P.np > 0) decode_poly_part(P, pc, R.exps, R.n, t);
       int64_t u = T + (P.T2 - 1);
       for (int k = 0; k < P.nt; ++k) {
         const int32_t wk = P.w[P.np + k];

@@ -122,10 +122,11 @@ __device__ __forceinline__ HashTile find_tile(const Prod* prods, const int32_t* 
   const Prod& P = prods[h.pid];
   const int64_t local = t - task_begin[lo];
   const int64_t ti = local / P.tiles_j, tj = local - ti * P.tiles_j;
+  // terms dropped by truncation sort after the kept ones: tiles stop there
   h.i0 = ti * P.tile_i;
-  h.i1 = min(P.f.n, h.i0 + P.tile_i);
+  h.i1 = min(P.f.nkeep, h.i0 + P.tile_i);
   h.j0 = tj * P.tile_j;
-  h.j1 = min(P.g.n, h.j0 + P.tile_j);
+  h.j1 = min(P.g.nkeep, h.j0 + P.tile_j);
   return h;
 }
 
@@ -152,16 +153,23 @@ __device__ __forceinline__ bool poly_tile(const Prod& P, const HashTile& h) {
       cr[r] = CF[i];
     }
     const unsigned valid = (1u << m) - 1u;
-    for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
+    // truncated product: codes at or above krange are beyond the degree
+    // bound.  F is ascending, so the group's first term has the longest
+    // prefix of g below the bound; the others are masked per pair.
+    int64_t jend = h.j1;
+    if (P.graded) jend = min(jend, lower_bound_i64(G, P.g.nkeep, P.krange - fr[0]));
+    for (int64_t j = h.j0 + lane; j < jend; j += 32) {
       const int64_t gj = G[j];
       const T cg = CG[j];
       KeyBatch<HGROUP_R, T> kb;
+      unsigned v = valid;
 #pragma unroll
       for (int r = 0; r < HGROUP_R; ++r) {
         kb.key[r] = (uint64_t)(fr[r] + gj);
         kb.val[r] = cr[r] * cg;
+        if (P.graded && fr[r] + gj >= P.krange) v &= ~(1u << r);
       }
-      ok &= hash_add_batch<HGROUP_R, T>(P.table, mask, P.probe_limit, kb, valid);
+      ok &= hash_add_batch<HGROUP_R, T>(P.table, mask, P.probe_limit, kb, v);
     }
   }
   return ok;
@@ -209,6 +217,8 @@ __device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
         for (int u = 0; u < 2; ++u) {
           const int r = r0 + u;
           const int64_t pc = pr[r] + pg;
+          // truncation: the polynomial part's degree digit is the top one
+          const bool keep = r < m && !(P.graded && pc >= P.Wp);
           const double hcoef = cr[r] * cg;         // (C_f / 2) * C_g
           const int kd = kr_[r] ^ kg;              // cos if same kinds, sin otherwise
           // sum term
@@ -217,14 +227,14 @@ __device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
           if (T < 0) { T = -T; if (kd) v = -v; }
           kb.key[2 * u] = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
           kb.val[2 * u] = v;
-          if (r < m && !(T == 0 && kd)) valid |= 1u << (2 * u);
+          if (keep && !(T == 0 && kd)) valid |= 1u << (2 * u);
           // difference term
           T = tr[r] - tg;
           v = (!kr_[r] && kg) ? -hcoef : hcoef;          // cos*sin: -sin(a-b)
           if (T < 0) { T = -T; if (kd) v = -v; }
           kb.key[2 * u + 1] = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
           kb.val[2 * u + 1] = v;
-          if (r < m && !(T == 0 && kd)) valid |= 1u << (2 * u + 1);
+          if (keep && !(T == 0 && kd)) valid |= 1u << (2 * u + 1);
         }
         ok &= hash_add_batch<4, double>(P.table, mask, P.probe_limit, kb, valid);
       }
@@ -255,6 +265,7 @@ __device__ __forceinline__ void pseries_dense_tile(const Prod& P, const HashTile
     const double cf = CF[i];
     for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
       const int64_t pc = pf + PG[j];
+      if (P.graded && pc >= P.Wp) continue;   // above the degree bound
       const int64_t tg = TG[j];
       const int kg = KG[j];
       const double hcoef = cf * CG[j];
@@ -301,12 +312,16 @@ __device__ __forceinline__ void hll_tile(const Prod& P, const HashTile& h, uint3
   for (int64_t i = h.i0 + warp; i < h.i1; i += NW) {
     const int64_t fi = F[i];
     if (P.nt == 0) {
-      for (int64_t j = h.j0 + lane; j < h.j1; j += 32) hll_add(reg, (uint64_t)(fi + G[j]));
+      for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
+        const int64_t key = fi + G[j];
+        if (!(P.graded && key >= P.krange)) hll_add(reg, (uint64_t)key);
+      }
     } else {
       const int64_t ti = TF[i];
       const int ki = KF[i];
       for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
         const int64_t pc = fi + G[j];
+        if (P.graded && pc >= P.Wp) continue;
         const int kd = ki ^ KG[j];
         int64_t T = ti + TG[j];
         if (T < 0) T = -T;

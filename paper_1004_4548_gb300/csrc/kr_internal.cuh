@@ -11,8 +11,14 @@ namespace kr {
 constexpr int MAXV = KR_MAXV;
 // per-operand range record written by k_range_scan: [0, MAXV) exponent minima,
 // [MAXV, 2 MAXV) maxima, [2 MAXV, 3 MAXV) max |t|, [3 MAXV] 1 when every
-// coefficient is an int64 within the int32 range
+// coefficient is an int64 within the int32 range; for a truncated product
+// [3 MAXV + 1], [3 MAXV + 2] the least and largest degree of a term in the
+// truncation variables and [3 MAXV + 3] 1 when a degree leaves the int32 range
 constexpr int RANGE_STRIDE = 3 * MAXV + 4;
+// code of the polynomial part of a Poisson term dropped by truncation: any
+// sum of two such codes stays at or above every code range that truncation
+// allows (those are at most 2^61)
+constexpr int64_t TRUNC_PSENT = int64_t(1) << 61;
 constexpr int PATH_DENSE = 1;
 constexpr int PATH_HASH = 2;
 
@@ -51,6 +57,11 @@ struct Operand {
   int32_t sort_method;
   int32_t idx_bits;     // bits of the index packed under the key (bitmap/bitonic)
   int64_t key_range;    // input keys lie in [0, key_range)
+  // truncated products: a term that cannot reach the kept degrees gets the
+  // key sent + (its index), so it sorts after every kept term; the gather
+  // records how many terms are kept (the sorted prefix [0, nkeep))
+  int64_t sent;
+  int64_t nkeep;
 };
 
 // One product, planned on the host, read by every kernel.
@@ -63,6 +74,15 @@ struct Prod {
   int64_t c[MAXV];      // coding vector; poly part [0, np), trig part [np, np + nt)
   int32_t w[MAXV];      // output widths
   int32_t omin[MAXV];   // output box minimum (poly), -R_k (trig)
+  // truncated product (graded coding): the degree in the variables of gmask
+  // replaces variable gvar and is the most significant polynomial digit; the
+  // digits are the other variables in ascending order, then the degree.
+  // w[gvar], omin[gvar] describe the degree digit; gvar_min / gvar_max are
+  // the output range of variable gvar itself.
+  int32_t graded;
+  int32_t gvar;
+  uint32_t gmask;
+  int32_t gvar_min, gvar_max;
   int64_t Wp;           // polynomial code range (product of poly widths)
   int64_t T2;           // canonical |trig code| values: (Wt - 1) / 2 + 1
   int64_t krange;       // output key range: Wp, or 2 * T2 * Wp for Poisson
@@ -130,6 +150,32 @@ __device__ __forceinline__ int64_t g_lower_bound(const int64_t* G, int64_t ng, c
     if (G[mid] < x) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// Exponents of the polynomial part of an output code (the inverse of the
+// mixed-radix coding): variable k of the term goes to exps[k * ld + q].  A
+// graded code holds the other variables first and the degree last; the
+// exponent of gvar is the degree minus the other exponents of the mask.
+__device__ __forceinline__ void decode_poly_part(const Prod& P, int64_t pc, int32_t* __restrict__ exps,
+                                                 int64_t ld, int64_t q) {
+  if (!P.graded) {
+    for (int k = 0; k < P.np; ++k) {
+      const int64_t d = (k + 1 < P.np) ? pc % P.w[k] : pc;
+      pc = (k + 1 < P.np) ? pc / P.w[k] : 0;
+      exps[(int64_t)k * ld + q] = (int32_t)(d + P.omin[k]);
+    }
+    return;
+  }
+  int64_t deg_rest = 0;
+  for (int k = 0; k < P.np; ++k) {
+    if (k == P.gvar) continue;
+    const int64_t d = pc % P.w[k];
+    pc /= P.w[k];
+    const int64_t e = d + P.omin[k];
+    if ((P.gmask >> k) & 1u) deg_rest += e;
+    exps[(int64_t)k * ld + q] = (int32_t)e;
+  }
+  exps[(int64_t)P.gvar * ld + q] = (int32_t)(pc + P.omin[P.gvar] - deg_rest);
 }
 
 // 64-bit mixing function (the finaliser of MurmurHash3, Appleby) for table slots

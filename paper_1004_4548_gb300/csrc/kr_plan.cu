@@ -1,4 +1,5 @@
 // Host-side planning of one product: coding box, path, scratch sizes.
+#include <algorithm>
 #include <cmath>
 
 #include "kr_plan.h"
@@ -74,10 +75,55 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     if (w[k] > INT32_MAX) { pl.st = KR_ERR_OVERFLOW; return; }
     P.w[k] = (int32_t)w[k];
   }
+  // ---- truncation by degree (Sec. 3): graded coding.  The degree in the
+  // mask's variables replaces the mask's highest-index variable r and becomes
+  // the most significant digit, so "degree <= N" is "code < Wp" with Wp the
+  // clipped code range.  Each operand keeps the terms whose degree leaves a
+  // partner: deg_f <= N - min deg_g (and the same for g).
+  P.graded = 0;
+  if (o.truncate) {
+    uint32_t m = o.trunc_mask ? o.trunc_mask : 0xffffffffu;
+    if (P.np < 32) m &= (1u << P.np) - 1u;
+    if (P.np == 0 || m == 0) { pl.st = KR_ERR_INVALID; return; }
+    if (rf[3 * MAXV + 3] || rg[3 * MAXV + 3]) { pl.st = KR_ERR_OVERFLOW; return; }
+    int r = 0;
+    for (int k = 0; k < P.np; ++k)
+      if ((m >> k) & 1u) r = k;
+    const int64_t dminf = rf[3 * MAXV + 1], dmaxf = rf[3 * MAXV + 2];
+    const int64_t dming = rg[3 * MAXV + 1], dmaxg = rg[3 * MAXV + 2];
+    const int64_t N = o.trunc_degree;
+    const int64_t dlo = dminf + dming;
+    const int64_t dhi = std::min(N, dmaxf + dmaxg);
+    P.graded = 1;
+    P.gvar = r;
+    P.gmask = m;
+    P.gvar_min = P.omin[r];
+    P.gvar_max = (int32_t)((int64_t)P.omin[r] + P.w[r] - 1);
+    if (dhi < dlo) { pl.empty = true; return; }   // every term pair exceeds N
+    if (dhi - dlo + 1 > INT32_MAX || dlo < INT32_MIN) { pl.st = KR_ERR_OVERFLOW; return; }
+    w[r] = dhi - dlo + 1;
+    P.w[r] = (int32_t)w[r];
+    P.omin[r] = (int32_t)dlo;
+    P.f.emin[r] = (int32_t)dminf;
+    P.f.emax[r] = (int32_t)std::min(dmaxf, N - dming);
+    P.g.emin[r] = (int32_t)dming;
+    P.g.emax[r] = (int32_t)std::min(dmaxg, N - dminf);
+  }
   int64_t Wp = 1;
   if (P.np > 0) {
-    pl.st = coding_vector(w, P.np, c, &Wp);
+    // digits in coding order: variable 0 first; a graded code moves the
+    // degree digit (variable r's slot) to the top
+    int64_t wd[MAXV], cd[MAXV];
+    int ord[MAXV], nd = 0;
+    for (int k = 0; k < P.np; ++k)
+      if (!(P.graded && k == P.gvar)) ord[nd++] = k;
+    if (P.graded) ord[nd++] = P.gvar;
+    for (int q = 0; q < nd; ++q) wd[q] = w[ord[q]];
+    pl.st = coding_vector(wd, nd, cd, &Wp);
     if (pl.st != KR_OK) return;
+    for (int q = 0; q < nd; ++q) c[ord[q]] = cd[q];
+    // room for the keys of dropped terms above the code range, and for sums
+    if (P.graded && Wp > (int64_t(1) << 61)) { pl.st = KR_ERR_OVERFLOW; return; }
   }
   for (int k = 0; k < P.np; ++k) P.c[k] = c[k];
   P.Wp = Wp;
@@ -99,7 +145,8 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     for (int k = 0; k < P.nt; ++k) P.c[P.np + k] = ct[k];
     P.T2 = (Wt - 1) / 2 + 1;
     const unsigned __int128 kr = (unsigned __int128)2 * (unsigned __int128)P.T2 * (unsigned __int128)Wp;
-    if (kr > (unsigned __int128)INT64_MAX) { pl.st = KR_ERR_OVERFLOW; return; }
+    const unsigned __int128 lim = P.graded ? ((unsigned __int128)1 << 62) : (unsigned __int128)INT64_MAX;
+    if (kr > lim) { pl.st = KR_ERR_OVERFLOW; return; }
     P.krange = (int64_t)kr;
   }
   const int64_t nf = P.f.n, ng = P.g.n;
@@ -132,13 +179,17 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
   for (int which = 0; which < 2; ++which) {
     Operand& op = which ? P.g : P.f;
     int64_t kr;
-    if (P.nt == 0) {
+    if (P.graded) {
+      kr = P.krange + op.n;   // dropped terms get keys krange + index
+    } else if (P.nt == 0) {
       int64_t span = 0;
       for (int k = 0; k < P.np; ++k) span += P.c[k] * (int64_t)(op.emax[k] - op.emin[k]);
       kr = span + 1;
     } else {
       kr = P.krange;
     }
+    op.sent = P.graded ? P.krange : kr;
+    op.nkeep = op.n;
     plan_sort(op, kr, which ? &pl.passes_g : &pl.passes_f, &pl.radix_sort_n);
     pl.op_bytes[which] = op.n * (8 * 7 + 1) + 8 * 256;
   }

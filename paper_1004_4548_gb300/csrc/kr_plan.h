@@ -52,6 +52,7 @@ struct Plan {
   int64_t bound_slots = 0;   // hash: table size for the term-product bound at the load factor
   int64_t slots_override = 0;  // hash: table size forced by a regrowth
   bool outcap_full = false;    // hash: output room for a full table (after an overflow)
+  bool empty = false;          // truncation leaves no term: the product is zero
   int passes_f = 0, passes_g = 0;
 };
 

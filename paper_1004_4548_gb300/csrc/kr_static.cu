@@ -90,6 +90,8 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
   P.g.code = (int64_t*)gcode;
   P.g.coef = (void*)gcoef;
   P.g.n = ng;
+  P.f.nkeep = nf;
+  P.g.nkeep = ng;
   P.np = 1;
   P.nt = 0;
   P.f64 = type == KR_F64 ? 1 : 0;

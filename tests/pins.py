@@ -8,6 +8,11 @@ product by a different road than the oracle's ordered map.
   (Schwartz-Zippel: distinct polynomials agree at a random point with
   probability <= degree / p).
 * ``eval_pseries``: evaluation of a Poisson series at real x and angles y.
+* ``eval_truncated_mod_m31`` / ``eval_truncated_pseries``: the value of the
+  part of f*g of degree <= N, reached from f and g alone: the degree of a
+  product term is the sum of its factors' degrees, so that part is the sum of
+  the products of f's and g's degree-homogeneous parts whose degrees add up
+  to at most N.
 """
 from __future__ import annotations
 
@@ -79,3 +84,36 @@ def eval_pseries(s, x: np.ndarray, y: np.ndarray):
     trig = np.where(s.kind == 0, np.cos(phase), np.sin(phase))
     terms = s.coef * mono * trig
     return float(terms.sum()), float(np.abs(s.coef * mono).sum())
+
+
+def degrees(exps: np.ndarray, mask: int) -> np.ndarray:
+    """Degree of every term in the variables of the bit mask (0 = all)."""
+    v = exps.shape[0]
+    m = mask if mask else (1 << v) - 1
+    rows = [k for k in range(v) if (m >> k) & 1]
+    return exps[rows].astype(np.int64).sum(axis=0)
+
+
+def eval_truncated_mod_m31(f, g, point, mask: int, N: int) -> int:
+    """Value modulo 2^31 - 1 of the degree <= N part of f*g at `point`."""
+    df, dg = degrees(f.exps, mask), degrees(g.exps, mask)
+    F = {int(d): eval_mod_m31(f.exps[:, df == d], f.coef[df == d], point) for d in np.unique(df)}
+    G = {int(d): eval_mod_m31(g.exps[:, dg == d], g.coef[dg == d], point) for d in np.unique(dg)}
+    return sum(a * b for d1, a in F.items() for d2, b in G.items() if d1 + d2 <= N) % M31
+
+
+def eval_truncated_pseries(f, g, x: np.ndarray, y: np.ndarray, mask: int, N: int):
+    """(value, magnitude) of the part of f*g whose polynomial degree is <= N."""
+    df, dg = degrees(f.exps, mask), degrees(g.exps, mask)
+    val, mag = 0.0, 0.0
+    for d1 in np.unique(df):
+        sf = type(f)(f.exps[:, df == d1], f.trig[:, df == d1], f.kind[df == d1], f.coef[df == d1])
+        a, am = eval_pseries(sf, x, y)
+        for d2 in np.unique(dg):
+            if d1 + d2 > N:
+                continue
+            sg = type(g)(g.exps[:, dg == d2], g.trig[:, dg == d2], g.kind[dg == d2], g.coef[dg == d2])
+            b, bm = eval_pseries(sg, x, y)
+            val += a * b
+            mag += am * bm
+    return val, mag

@@ -12,8 +12,8 @@ import numpy as np
 import pytest
 
 import oracle
-from pins import (M61, as_dict, box_convolution, eval_mod_m31, eval_mod_p,
-                  eval_pseries)
+from pins import (M61, as_dict, box_convolution, degrees, eval_mod_m31, eval_mod_p,
+                  eval_pseries, eval_truncated_mod_m31, eval_truncated_pseries)
 from workloads import (PSeries, Poly, Rng, dense_total_degree, fateman, random_poly,
                        random_pseries, total_degree_tuples, workload_cfg1,
                        workload_cfg2, workload_cfg3)
@@ -289,6 +289,59 @@ def test_oracle_pseries_shards_and_mass():
     assert n == full.coef.shape[0]
 
 
+def pin_truncation(plant=0):
+    """Degree-truncated products (Sec. 3): the full product's convolution restricted
+    to degree <= N, the graded evaluation, and the count of a dense truncated square."""
+    errs = []
+    cases = [(3, 70, [-2, 0, -3], [3, 4, 2], 0b111, 2), (3, 70, [-2, 0, -3], [3, 4, 2], 0b010, 5),
+             (3, 70, [-2, 0, -3], [3, 4, 2], 0b101, -1), (2, 40, 0, 6, 0, 7), (4, 50, -2, 3, 0b1001, 0)]
+    for s, (v, n, lo, hi, mask, N) in enumerate(cases):
+        f = random_poly(v, n, lo, hi, 1300 + s)
+        g = random_poly(v, n + 5, lo, hi, 1400 + s)
+        r = oracle.poly_mul(f, g, plant=plant, trunc=(N, mask))
+        m = mask if mask else (1 << v) - 1
+        want = {k: int(c) for k, c in box_convolution(f, g).items()
+                if sum(k[j] for j in range(v) if (m >> j) & 1) <= N}
+        if as_dict(r.exps, r.coef) != want:
+            errs.append(f"truncated convolution mismatch v={v} mask={mask:b} N={N}")
+    for s, (mask, N) in enumerate([(0, 5), (0b0110, 3), (0b1000, -2)]):
+        f = random_poly(4, 400, -3, 4, 1500 + s)
+        g = random_poly(4, 350, -3, 4, 1600 + s)
+        r = oracle.poly_mul(f, g, plant=plant, trunc=(N, mask))
+        if (degrees(r.exps, mask) > N).any():
+            errs.append("truncated product holds a term above the bound")
+        rng = Rng(1700 + s)
+        for _ in range(2):
+            pt = [int(x) for x in rng.ints(2, (1 << 31) - 2, 4)]
+            if eval_mod_m31(r.exps, r.coef, pt) != eval_truncated_mod_m31(f, g, pt, mask, N):
+                errs.append(f"graded evaluation mismatch mask={mask:b} N={N}")
+                break
+    f = dense_total_degree(3, 6, 1, 9, 1801)
+    g = dense_total_degree(3, 6, 1, 9, 1802)
+    r = oracle.poly_mul(f, g, plant=plant, trunc=(8, 0))
+    if r.coef.shape[0] != math.comb(3 + 8, 3):
+        errs.append(f"dense truncated square: {r.coef.shape[0]} terms, want {math.comb(11, 3)}")
+    rng = Rng(1900)
+    for s, (mask, N) in enumerate([(0, 1), (0b10, 0)]):
+        f = random_pseries(2, 2, 120, 3, 3, 1910 + s)
+        g = random_pseries(2, 2, 130, 3, 3, 1920 + s)
+        h = oracle.poisson_mul(f, g, plant=plant, trunc=(N, mask))
+        H = PSeries(h.exps, h.trig, h.kind, h.coef)
+        for _ in range(3):
+            x = 0.5 + rng.uniform(2)
+            y = 2 * math.pi * rng.uniform(2)
+            want, mag = eval_truncated_pseries(f, g, x, y, mask, N)
+            got, _ = eval_pseries(H, x, y)
+            if abs(got - want) > 1e-12 * mag:
+                errs.append(f"truncated Poisson evaluation mismatch mask={mask:b} N={N}")
+                break
+    return errs
+
+
+def test_oracle_truncation():
+    assert pin_truncation() == []
+
+
 # ---------------------------------------------------------------------------
 # planted mistakes: each must be caught by some pin
 # ---------------------------------------------------------------------------
@@ -300,11 +353,12 @@ PLANTS = {
     4: "canonical sign from the lowest-index multiplier",
     5: "last term of g skipped",
     6: "first exponent of f used twice",
+    7: "degree bound applied as < N instead of <= N",
 }
 
 
 @pytest.mark.parametrize("plant", sorted(PLANTS))
 def test_planted_mistake_is_caught(plant):
     caught = (pin_werner(plant) + pin_canonical(plant) + pin_random_angles(plant)
-              + pin_bruteforce(plant) + pin_mod_p(plant))
+              + pin_bruteforce(plant) + pin_mod_p(plant) + pin_truncation(plant))
     assert caught, f"planted mistake {plant} ({PLANTS[plant]}) escaped every pin"
