@@ -154,21 +154,37 @@ __device__ __forceinline__ void smem_add<double>(double* p, double v) {
 // prefix of the window lengths (excl[ACC_THREADS] = total) and the coefficient.
 struct ChunkTable {
   int32_t f32[ACC_THREADS];
-  int32_t lo[ACC_THREADS];
+  int32_t lo[ACC_THREADS];            // first j of the tile's window (tile owners)
+  int16_t run[ACC_THREADS];           // tile length (0: not a tile owner)
   int32_t excl[ACC_THREADS + 1];
   int32_t warp_sum[ACC_THREADS / 32];
-  unsigned long long coef[ACC_THREADS];
 };
 
+// f terms are taken in tiles of up to TILE_R consecutive terms whose codes
+// share one aligned window of S / 8 codes; a lane multiplies one g term by
+// every term of a tile, so the window search, the g loads and the walk
+// bookkeeping are paid once per TILE_R term-products.  The tile's g-window is
+// the union of its terms' windows, at most S / 8 codes wider than one.
+#ifndef KR_TILE_R
+#define KR_TILE_R 8
+#endif
+constexpr int TILE_R = KR_TILE_R;
+
 // Accumulate the pairs of one task into the shared slice acc[0, S).
-// The task's f terms are taken ACC_THREADS at a time.  Each thread finds the
-// exact j-window of one f term in the sorted g codes; a block-wide prefix sum
-// flattens the windows into one range of pair indices, which is cut into
-// equal contiguous shares, one per warp, so that every warp reaches the
-// task's barrier with the same amount of work done.  A warp walks its share
-// 32 pairs at a time: consecutive lanes take consecutive g terms, and the
-// slice offset a = (F_i - B) + G_j lies in [0, S) by construction (32-bit
-// arithmetic is exact there; a guard keeps it in bounds regardless).
+//
+// The task's f terms are taken ACC_THREADS at a time.  The thread of the first
+// term of a tile (see TILE_R) finds the tile's exact g-window: the g terms
+// whose product with some term of the tile can land in the block.  A
+// block-wide prefix sum flattens the windows into one range of (tile, g term)
+// slots, cut into equal contiguous shares, one per warp, so that every warp
+// reaches the chunk's barrier with about the same work done.  A warp walks its
+// share 32 consecutive slots at a time, one per lane; each lane follows the
+// window its slot falls in, loads one g term and adds its products with the
+// tile's f terms to the slice with shared-memory atomics (consecutive lanes of
+// a window hold consecutive g terms, so one atomic instruction touches nearby
+// words).  The slice offset a = (F_i - B) + G_j lies in [0, S) for the pairs
+// this block owns; others are skipped (32-bit arithmetic is exact there, since
+// the dense path keeps codes below 2^31).
 template <typename T, bool C32>
 __device__ __forceinline__ T mul(T a, T b) {
   if constexpr (C32) return (T)((int64_t)(int32_t)a * (int64_t)(int32_t)b);
@@ -185,6 +201,7 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
   const int64_t B = tk.block * S;
   // pairs land in [B, B + lim): the block, clipped to the code range
   const int64_t lim = min(S, P.krange - B);
+  const int sh = 28 - __clz((int)S);   // tiles stay within aligned windows of about S / 8 codes
   const int64_t* __restrict__ F = P.f.code;
   const int64_t* __restrict__ G = P.g.code;
   const int32_t* __restrict__ G32 = P.g.code32;
@@ -193,20 +210,26 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
   const int64_t ng = P.g.n;
   for (int64_t ib = tk.i0; ib < tk.i1; ib += ACC_THREADS) {
     const int64_t i = ib + threadIdx.x;
-    int32_t cnt = 0;
+    int32_t cnt = 0, l32 = 0, r = 0;
     if (i < tk.i1) {
-      const int64_t fi = F[i] - B;
-      const int64_t l = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, -fi);
-      const int64_t h = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, lim - fi);
-      ct.f32[threadIdx.x] = (int32_t)fi;
-      ct.lo[threadIdx.x] = (int32_t)l;
-      cnt = (int32_t)(h - l);
-      ct.coef[threadIdx.x] = to_bits<T>(CF[i]);
-    } else {
-      ct.f32[threadIdx.x] = 0;
-      ct.lo[threadIdx.x] = 0;
-      ct.coef[threadIdx.x] = 0ull;
+      const int64_t fc = F[i];
+      // the offset of the next term too, so that the walk reads two per load
+      ct.f32[threadIdx.x] = (int32_t)(fc - B);
+      const bool owner = threadIdx.x == 0 || (fc >> sh) != (F[i - 1] >> sh) ||
+                         ((i - tk.i0) & (TILE_R - 1)) == 0;
+      if (owner) {
+        r = 1;
+        while (r < TILE_R && threadIdx.x + r < ACC_THREADS && i + r < tk.i1 &&
+               (F[i + r] >> sh) == (fc >> sh) && ((i + r - tk.i0) & (TILE_R - 1)) != 0)
+          ++r;
+        const int64_t l = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, B - F[i + r - 1]);
+        const int64_t h = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, B + lim - fc);
+        l32 = (int32_t)l;
+        cnt = (int32_t)(h - l);
+      }
     }
+    ct.lo[threadIdx.x] = l32;
+    ct.run[threadIdx.x] = (int16_t)r;
     // block-wide exclusive scan of the window lengths
     int32_t x = cnt;
 #pragma unroll
@@ -231,39 +254,37 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
     if (threadIdx.x == ACC_THREADS - 1) ct.excl[ACC_THREADS] = wbase + x;
     __syncthreads();
     const int32_t total = ct.excl[ACC_THREADS];
-    // this warp's share [pb, pe) of the flattened pairs
+    // this warp's share [pb, pe) of the flattened slots
     const int32_t pb = (int32_t)(((int64_t)total * warp) / NW);
     const int32_t pe = (int32_t)(((int64_t)total * (warp + 1)) / NW);
     if (pb < pe) {
-      // k = last f term whose window starts at or before pb
-      int lo_k = 0, hi_k = ACC_THREADS;
-      while (hi_k - lo_k > 1) {
-        const int mid = (lo_k + hi_k) >> 1;
-        if (ct.excl[mid] <= pb) lo_k = mid; else hi_k = mid;
-      }
-      // walk this warp's windows one by one; the lanes stride the j-range
-      for (int k = lo_k; k < ACC_THREADS; ++k) {
-        const int32_t e0 = ct.excl[k];
-        if (e0 >= pe) break;
-        const int32_t e1 = ct.excl[k + 1];
-        const int32_t s0 = max(pb, e0), s1 = min(pe, e1);
-        if (s0 >= s1) continue;
-        const int64_t jb = (int64_t)ct.lo[k] + (s0 - e0);
-        const int64_t je = (int64_t)ct.lo[k] + (s1 - e0);
-        const int32_t fk = ct.f32[k];
-        const T ck = from_bits<T>(ct.coef[k]);
-        int64_t j = jb + lane;
-        for (; j + 32 < je; j += 64) {
-          const int32_t a0 = fk + (G32 ? G32[j] : (int32_t)G[j]);
-          const int32_t a1 = fk + (G32 ? G32[j + 32] : (int32_t)G[j + 32]);
-          const T v0 = mul<T, C32>(ck, CG[j]);
-          const T v1 = mul<T, C32>(ck, CG[j + 32]);
-          if ((uint32_t)a0 < (uint32_t)S) smem_add<T>(&acc[a0], v0);
-          if ((uint32_t)a1 < (uint32_t)S) smem_add<T>(&acc[a1], v1);
+      // k = the window of this lane's first slot (the last k with
+      // excl[k] <= p); p < excl[ACC_THREADS] keeps k + 1 <= ACC_THREADS below
+      int32_t p = pb + lane;
+      int k = 0, hi_k = ACC_THREADS;
+      {
+        const int32_t ps = min(p, pe - 1);
+        while (hi_k - k > 1) {
+          const int mid = (k + hi_k) >> 1;
+          if (ct.excl[mid] <= ps) k = mid; else hi_k = mid;
         }
-        if (j < je) {
-          const int32_t a0 = fk + (G32 ? G32[j] : (int32_t)G[j]);
-          if ((uint32_t)a0 < (uint32_t)S) smem_add<T>(&acc[a0], mul<T, C32>(ck, CG[j]));
+      }
+      int32_t e0 = ct.excl[k], e1 = ct.excl[k + 1];
+      for (; p < pe; p += 32) {
+        while (p >= e1) {   // empty windows (non-owners) are skipped here too
+          ++k;
+          e0 = e1;
+          e1 = ct.excl[k + 1];
+        }
+        const int64_t j = (int64_t)ct.lo[k] + (p - e0);
+        const int32_t gc = G32 ? G32[j] : (int32_t)G[j];
+        const T cg = CG[j];
+        const int rk = ct.run[k];
+        const T* __restrict__ cf = CF + (ib + k);
+#pragma unroll 4
+        for (int a = 0; a < rk; ++a) {
+          const int32_t off = ct.f32[k + a] + gc;
+          if ((uint32_t)off < (uint32_t)S) smem_add<T>(&acc[off], mul<T, C32>(cf[a], cg));
         }
       }
     }
