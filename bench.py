@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--block-slots", type=int, default=0, help="dense output block size (0 = library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched / served measurements")
     ap.add_argument("--batch-products", type=int, default=4096, help="products in the uneven batch")
-    ap.add_argument("--case", default="", choices=["", "cfg3", "cfg4s"],
+    ap.add_argument("--case", default="", choices=["", "cfg3", "cfg4s", "cfg4"],
                     help="profiling runs: time only this secondary case (cfg4s = cfg4 at 5000 terms)")
     return ap.parse_args()
 
@@ -381,6 +381,8 @@ def profile_case(args):
     stream = torch.cuda.current_stream()
     if args.case == "cfg3":
         r = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert", args.steps)
+    elif args.case == "cfg4":
+        r = time_pseries(kron, ctx, *workload_cfg4(), dev, stream, flush, args.steps)
     else:
         f, g = workload_cfg4(5000)
         r = time_pseries(kron, ctx, f, g, dev, stream, flush, args.steps)

@@ -150,6 +150,17 @@ typedef struct {
   int32_t truncate;
   uint32_t trunc_mask;
   int64_t trunc_degree;
+  /* Output key window: only the terms of the product whose key (the code of a
+   * polynomial term, ((kind * T2) + |t|) * Wp + p for a Poisson term; the
+   * graded code for a truncated product) lies in [code_lo, code_hi) are
+   * computed; code_hi = 0 means no upper limit.  The dense path then holds an
+   * array of code_hi - code_lo slots only, so a product too large for one
+   * device splits into windows that run one after another or on several
+   * devices, each window's terms sorted; concatenated in window order they
+   * are the whole product (Sec. 4's disjoint output ranges, across calls).
+   * kron_split_hist helps choose windows of equal work. */
+  int64_t code_lo;
+  int64_t code_hi;
 } kr_opts;
 
 /* ------------------------------------------------------------------------ */
@@ -290,6 +301,19 @@ kr_status kron_batch_launch(kr_batch* b, kr_stream stream);
  * batch again for it. */
 kr_status kron_batch_results(kr_batch* b, kr_result* res, int32_t njobs);
 void kron_batch_destroy(kr_batch* b);
+
+/* Work histogram of one product for splitting it into output key windows:
+ * nsamples term pairs drawn uniformly (from a counter-based hash of seed) are
+ * expanded into their output keys (one per pair for polynomials, the sum and
+ * difference terms for Poisson series, both with the job's truncation), and
+ * hist[b] counts the keys k with floor(k * nbins / krange) = b, where krange
+ * (written to *krange_out) is the product's key range: the keys of the whole
+ * product lie in [0, krange).  hist: host int64 [nbins], caller-owned.  The
+ * job's code window is ignored.  Equal-work windows are the quantiles of the
+ * histogram.  Deterministic for fixed inputs and seed.  Synchronises the
+ * stream.  KR_ERR_INVALID for an empty product or nbins < 1. */
+kr_status kron_split_hist(kr_ctx* ctx, const kr_job* job, int32_t nbins, int64_t nsamples, uint64_t seed,
+                          int64_t* hist, int64_t* krange_out, kr_stream stream);
 
 /* Copy the product kept by the last poly_mul / poisson_mul of this context
  * (after KR_ERR_CAPACITY) into h.  KR_ERR_INVALID if there is none. */

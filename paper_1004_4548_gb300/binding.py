@@ -48,7 +48,7 @@ class kr_opts(ctypes.Structure):
     _fields_ = [("path", _i32), ("block_slots", _i32), ("load_factor", ctypes.c_double),
                 ("probe_limit", _i32), ("unsorted", _i32), ("max_regrow", _i32),
                 ("table_slots", _i64), ("truncate", _i32), ("trunc_mask", ctypes.c_uint32),
-                ("trunc_degree", _i64)]
+                ("trunc_degree", _i64), ("code_lo", _i64), ("code_hi", _i64)]
 
 
 class kr_job(ctypes.Structure):
@@ -86,6 +86,8 @@ SIGNATURES = {
                                    ctypes.POINTER(kr_pseries_out), ctypes.POINTER(kr_opts), _vp]),
     "kron_fetch_poly": (ctypes.c_int, [_vp, ctypes.POINTER(kr_poly_out), _vp]),
     "kron_mul_batch": (ctypes.c_int, [_vp, ctypes.POINTER(kr_job), _i32, ctypes.POINTER(kr_result), _i64, _vp]),
+    "kron_split_hist": (ctypes.c_int, [_vp, ctypes.POINTER(kr_job), _i32, _i64, ctypes.c_uint64,
+                                       ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp]),
     "kron_batch_prepare": (ctypes.c_int, [_i32, ctypes.POINTER(kr_job), _i32, ctypes.POINTER(_vp),
                                           ctypes.POINTER(kr_result), _vp]),
     "kron_batch_launch": (ctypes.c_int, [_vp, _vp]),
@@ -176,12 +178,14 @@ def _stream_ptr(stream):
 
 
 def _opts(path=0, block_slots=0, load_factor=0.0, probe_limit=0, unsorted=0, max_regrow=0,
-          table_slots=0, trunc_degree=None, trunc_mask=0):
+          table_slots=0, trunc_degree=None, trunc_mask=0, code_lo=0, code_hi=0):
     """kr_opts from keywords; trunc_degree (an int) asks for the truncated product
-    of degree <= trunc_degree in the variables of trunc_mask (0 = all)."""
+    of degree <= trunc_degree in the variables of trunc_mask (0 = all);
+    [code_lo, code_hi) restricts the product to a window of output keys."""
     t = trunc_degree is not None
     return kr_opts(path, block_slots, load_factor, probe_limit, unsorted, max_regrow, table_slots,
-                   1 if t else 0, int(trunc_mask) if t else 0, int(trunc_degree) if t else 0)
+                   1 if t else 0, int(trunc_mask) if t else 0, int(trunc_degree) if t else 0,
+                   int(code_lo), int(code_hi))
 
 
 class Context:
@@ -416,6 +420,24 @@ def _view(ptr, shape, typestr, device):
         dt = {"<i4": torch.int32, "<i8": torch.int64, "<f8": torch.float64, "|u1": torch.uint8}[typestr]
         return torch.empty(shape, dtype=dt, device=f"cuda:{device}")
     return torch.as_tensor(_DevArray(ptr, shape, typestr), device=f"cuda:{device}")
+
+
+def kron_split_hist(f, g, nbins: int = 65536, nsamples: int = 1 << 22, seed: int = 1,
+                    ctx: Context | None = None, stream=None, **opts):
+    """Work histogram of f * g over nbins equal slices of its key range.
+
+    Returns (hist int64 [nbins], krange): hist[b] counts sampled output keys k
+    with k * nbins // krange == b.
+    """
+    ctx = ctx or context()
+    jobs, keep = _make_jobs([(f, g)], [opts])
+    hist = np.zeros(nbins, np.int64)
+    kr = _i64(0)
+    st = ctx.L.kron_split_hist(ctx.h, jobs, int(nbins), int(nsamples), int(seed) & ((1 << 64) - 1),
+                               hist.ctypes.data_as(ctypes.POINTER(_i64)), ctypes.byref(kr),
+                               _stream_ptr(stream))
+    _check(ctx.L, ctx.h, st, "kron_split_hist")
+    return hist, int(kr.value)
 
 
 def kron_mul_batch(pairs, ctx: Context | None = None, stream=None, wave_pairs: int = 0, opts=None):

@@ -33,6 +33,12 @@ struct kr_ctx {
   // replay (prepared batches): run the device work of the saved plans again,
   // without host planning or synchronisation, so that it can be captured
   bool replay = false;
+  // split histogram (kron_split_hist): the pipeline stops after phase B1 and
+  // samples the keys of product 0 into split_hist (host) instead
+  int32_t split_nbins = 0;
+  int64_t split_nsamples = 0;
+  uint64_t split_seed = 0;
+  int64_t* split_hist = nullptr;
   void* pinned = nullptr;
   size_t pinned_cap = 0;
   // product kept after the last multiplication (for kron_fetch_*)
@@ -316,7 +322,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   struct B1 {
     Prod* lprods; OpRef* oplists; int32_t* dense_ids; int64_t* block_begin; int32_t* hash_ids;
     int64_t* task_begin; int64_t* scan; DenseTask* tasks; uint32_t* hll; size_t hll_bytes;
-    int32_t* hll_ids; int64_t* hll_task_begin;
+    int32_t* hll_ids; int64_t* hll_task_begin; unsigned long long* split;
   } A{};
   for (int pass = 0; pass < 2; ++pass) {
     Bump b(pass ? ctx->work : nullptr);
@@ -332,6 +338,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     A.hll_task_begin = b.take<int64_t>((int64_t)hll_ids.size() + 1);
     A.hll = b.take<uint32_t>((int64_t)hll_ids.size() * HLL_M);
     A.hll_bytes = sizeof(uint32_t) * hll_ids.size() * HLL_M;
+    A.split = ctx->split_hist ? b.take<unsigned long long>(ctx->split_nbins) : nullptr;
     for (int q = 0; q < (int)hll_ids.size(); ++q)
       if (pass) plans[hll_ids[q]].p.hll = A.hll + (int64_t)q * HLL_M;
     for (int p : live_ids) {
@@ -481,6 +488,20 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       pl.p.g.nkeep = hl[q].g.nkeep;
     }
   }
+  if (ctx->split_hist) {
+    // kron_split_hist: sample the output keys of the (one) product and stop
+    const size_t hb_bytes = sizeof(unsigned long long) * (size_t)ctx->split_nbins;
+    ck(ctx, cudaMemsetAsync(A.split, 0, hb_bytes, s), "memset histogram");
+    ck(ctx, launch_split_sample(A.lprods, 0, ctx->split_nbins, ctx->split_nsamples, ctx->split_seed,
+                                A.split, s), "split sample");
+    ctx->launches += 1;
+    ck(ctx, cudaMemcpyAsync(ctx->split_hist, A.split, hb_bytes, cudaMemcpyDeviceToHost, s), "download");
+    ck(ctx, cudaStreamSynchronize(s), "sync histogram");
+    const int p = live_ids[0];
+    res[p].st = status_to_kr(plans[p].p.status);
+    res[p].prod = plans[p].p;
+    return;
+  }
   // ---------------- phase B2, repeated for products whose table filled up
   std::vector<int> regrows(nprod, 0);
   for (;;) {
@@ -489,9 +510,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Plan& pl = plans[p];
       finish_hash_sizes(ins[p].opts, &pl);
       max_hash_out = std::max(max_hash_out, pl.out_cap);
-      const int64_t nb = order_bins(pl.p.krange);
-      if (pl.p.krange <= ORDER_BITMAP_MAX)
-        bins_total = std::max(bins_total, (order_bitmap_bytes(pl.p.krange) + 7) / 8);
+      const int64_t nb = order_bins(pl.p.kspan);
+      if (pl.p.kspan <= ORDER_BITMAP_MAX)
+        bins_total = std::max(bins_total, (order_bitmap_bytes(pl.p.kspan) + 7) / 8);
       else if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, 2 * (nb + 1));
       else scan_b2 = std::max(scan_b2, radix_scan_entries(pl.out_cap));
     }
@@ -527,7 +548,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Z.counters = b.take<int64_t>(4);
       for (int p : live_ids) {
         Plan& pl = plans[p];
-        if (pl.p.path == PATH_DENSE) pl.p.dense = (void*)b.take<uint64_t>(pl.p.krange);
+        if (pl.p.path == PATH_DENSE) pl.p.dense = (void*)b.take<uint64_t>(pl.p.kspan);
         else pl.p.table = b.take<uint64_t>(2 * pl.p.slots);
       }
       Z.zero_bytes = b.off - zero_start;
@@ -625,16 +646,17 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       uint64_t* v = Z.oval + r.prod.out_start;
       uint64_t* k2 = Z.okey2;
       uint64_t* v2 = Z.oval2;
-      if (r.prod.krange <= ORDER_BITMAP_MAX) {
-        ck(ctx, order_by_bitmap(k, v, k2, v2, r.n, r.prod.krange, Z.bins, s), "output order");
+      // compacted keys are relative to the key window: they lie in [0, kspan)
+      if (r.prod.kspan <= ORDER_BITMAP_MAX) {
+        ck(ctx, order_by_bitmap(k, v, k2, v2, r.n, r.prod.kspan, Z.bins, s), "output order");
         ck(ctx, cudaMemcpyAsync(k, k2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
         ck(ctx, cudaMemcpyAsync(v, v2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
         ctx->launches += 4;
-      } else if (order_bins(r.prod.krange) <= ORDER_MAX_BINS) {
-        ck(ctx, order_by_bins(k, v, k2, v2, r.n, r.prod.krange, Z.bins, s), "output order");
+      } else if (order_bins(r.prod.kspan) <= ORDER_MAX_BINS) {
+        ck(ctx, order_by_bins(k, v, k2, v2, r.n, r.prod.kspan, Z.bins, s), "output order");
         ctx->launches += 4;
       } else {
-        const int bits = bits_for((uint64_t)r.prod.krange);
+        const int bits = bits_for((uint64_t)r.prod.kspan);
         bool in_tmp = false;
         ck(ctx, radix_sort_pairs(k, v, k2, v2, r.n, bits, Z.scan, s, &in_tmp), "output sort");
         ctx->launches += 3 * ((bits + 7) / 8);
@@ -702,23 +724,27 @@ kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
   const bool exps_dev = is_device_ptr(h->exps);
   const bool codes_dev = is_device_ptr(h->codes);
   int32_t* exps_tmp = nullptr;
+  int64_t* codes_tmp = nullptr;
   int64_t ld = h->capacity;
-  if (h->exps && !exps_dev) {
-    // decode into the input arena, then one copy per variable row
-    ensure(ctx, &ctx->in_arena, &ctx->in_cap, (size_t)n * P.np * 4 + 256, s);
-    exps_tmp = (int32_t*)ctx->in_arena;
-    ld = n;
+  if ((h->exps && !exps_dev) || (h->codes && !codes_dev)) {
+    // decode into the input arena, then copies (one per variable row)
+    ensure(ctx, &ctx->in_arena, &ctx->in_cap, (size_t)n * (P.np * 4 + 8) + 1024, s);
+    Bump b(ctx->in_arena);
+    exps_tmp = b.take<int32_t>((int64_t)n * P.np);
+    codes_tmp = b.take<int64_t>(n);
+    if (!(h->exps && !exps_dev)) exps_tmp = nullptr;
+    else ld = n;
   }
   int32_t* ex = h->exps ? (exps_dev ? h->exps : exps_tmp) : nullptr;
-  ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, n, ex, ld, codes_dev ? h->codes : nullptr, s),
-     "decode");
+  int64_t* cd = h->codes ? (codes_dev ? h->codes : codes_tmp) : nullptr;
+  ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, n, ex, ld, cd, s), "decode");
   ctx->launches += 1;
   mark(ctx, s, "decode");
   if (exps_tmp) {
     for (int k = 0; k < P.np; ++k)
       copy_out(ctx, h->exps + (int64_t)k * h->capacity, exps_tmp + (int64_t)k * n, (size_t)n * 4, s);
   }
-  if (h->codes && !codes_dev) copy_out(ctx, h->codes, ctx->res_key, (size_t)n * 8, s);
+  if (h->codes && !codes_dev) copy_out(ctx, h->codes, codes_tmp, (size_t)n * 8, s);
   copy_out(ctx, h->coef, ctx->res_val, (size_t)n * 8, s);
   mark(ctx, s, "copy_out");
   ck(ctx, cudaStreamSynchronize(s), "sync output");
@@ -745,7 +771,8 @@ kr_status emit_pseries(kr_ctx* ctx, kr_pseries_out* h, cudaStream_t s) {
     int32_t* ex = b.take<int32_t>((int64_t)n * P.np);
     int32_t* tr = b.take<int32_t>((int64_t)n * P.nt);
     uint8_t* kd = b.take<uint8_t>(n);
-    ck(ctx, launch_decode_pseries(ctx->res_dprod, 0, ctx->res_key, n, ex, tr, kd, n, nullptr, s), "decode");
+    int64_t* cd = b.take<int64_t>(n);
+    ck(ctx, launch_decode_pseries(ctx->res_dprod, 0, ctx->res_key, n, ex, tr, kd, n, cd, s), "decode");
     ctx->launches += 1;
     if (h->exps)
       for (int k = 0; k < P.np; ++k)
@@ -754,7 +781,7 @@ kr_status emit_pseries(kr_ctx* ctx, kr_pseries_out* h, cudaStream_t s) {
       for (int k = 0; k < P.nt; ++k)
         copy_out(ctx, h->trig + (int64_t)k * h->capacity, tr + (int64_t)k * n, (size_t)n * 4, s);
     copy_out(ctx, h->kind, kd, (size_t)n, s);
-    copy_out(ctx, h->codes, ctx->res_key, (size_t)n * 8, s);
+    copy_out(ctx, h->codes, cd, (size_t)n * 8, s);
   }
   mark(ctx, s, "decode");
   copy_out(ctx, h->coef, ctx->res_val, (size_t)n * 8, s);
@@ -1415,6 +1442,56 @@ void kron_batch_destroy(kr_batch* b) {
   if (b->block) cudaFree(b->block);
   if (b->ctx) kr_ctx_destroy(b->ctx);
   delete b;
+}
+
+kr_status kron_split_hist(kr_ctx* ctx, const kr_job* job, int32_t nbins, int64_t nsamples, uint64_t seed,
+                          int64_t* hist, int64_t* krange_out, kr_stream stream) {
+  if (!ctx || !job || !hist || nbins < 1 || nsamples < 0) return KR_ERR_INVALID;
+  const kr_job& J = *job;
+  JobIn in;
+  if (J.kind == 0) {
+    if (!poly_job_ok(&J.f, &J.g) || J.f.nterms == 0 || J.g.nterms == 0) return KR_ERR_INVALID;
+    in.poisson = false;
+    in.f64 = J.f.type == KR_F64;
+    in.np = J.f.nvars;
+    in.fe = J.f.exps; in.fc = J.f.coef; in.nf = J.f.nterms;
+    in.ge = J.g.exps; in.gc = J.g.coef; in.ng = J.g.nterms;
+  } else if (J.kind == 1) {
+    if (!pseries_job_ok(&J.pf, &J.pg) || J.pf.nterms == 0 || J.pg.nterms == 0) return KR_ERR_INVALID;
+    in.poisson = true;
+    in.f64 = true;
+    in.np = J.pf.npoly;
+    in.nt = J.pf.ntrig;
+    in.fe = J.pf.exps; in.ft = J.pf.trig; in.fk = J.pf.kind; in.fc = J.pf.coef; in.nf = J.pf.nterms;
+    in.ge = J.pg.exps; in.gt = J.pg.trig; in.gk = J.pg.kind; in.gc = J.pg.coef; in.ng = J.pg.nterms;
+  } else {
+    return KR_ERR_INVALID;
+  }
+  in.opts = J.opts;
+  in.opts.code_lo = 0;
+  in.opts.code_hi = 0;
+  return guarded(ctx, [&]() -> kr_status {
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->has_result = false;
+    ctx->stage_ms.clear();
+    ctx->stage_name.clear();
+    ctx->nev = 0;
+    for (int32_t b = 0; b < nbins; ++b) hist[b] = 0;
+    ctx->split_nbins = nbins;
+    ctx->split_nsamples = nsamples;
+    ctx->split_seed = seed;
+    ctx->split_hist = hist;
+    std::vector<ProdResult> res;
+    try {
+      run_pipeline(ctx, {in}, s, res);
+    } catch (...) {
+      ctx->split_hist = nullptr;
+      throw;
+    }
+    ctx->split_hist = nullptr;
+    if (krange_out) *krange_out = res[0].prod.krange;
+    return res[0].st;
+  });
 }
 
 kr_status kron_fetch_poly(kr_ctx* ctx, kr_poly_out* h, kr_stream stream) {

@@ -4,51 +4,19 @@
 // of every product's accumulator: count the nonzero slots, exclusive scan,
 // then write each chunk's terms in slot order at its offset.  The dense
 // array's slot order is code order, so the dense output comes out sorted.
+#include <algorithm>
+
 #include "kr_internal.cuh"
 
 namespace kr {
 
 constexpr int CP_THREADS = 256;
+constexpr int CP_WARPS = CP_THREADS / 32;
+constexpr unsigned CP_FULL = 0xffffffffu;
 
-template <int NT>
-__device__ __forceinline__ int block_excl_scan_int(int v, int* total) {
-  __shared__ int ws[NT / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) ws[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int s = lane < NT / 32 ? ws[lane] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < NT / 32) ws[lane] = s;
-  }
-  __syncthreads();
-  const int base = warp > 0 ? ws[warp - 1] : 0;
-  *total = ws[NT / 32 - 1];
-  __syncthreads();
-  return base + x - v;
-}
-
-__device__ __forceinline__ bool slot_live(const Prod& P, int64_t s, uint64_t* key, uint64_t* val) {
-  if (P.path == PATH_DENSE) {
-    const uint64_t v = ((const uint64_t*)P.dense)[s];
-    *key = (uint64_t)s;
-    *val = v;
-    // int64 zero or float64 +-0.0
-    return (v << 1) != 0 || (!P.f64 && v != 0);
-  }
-  const uint64_t k = __ldcg(P.table + 2 * s);
-  const uint64_t v = __ldcg(P.table + 2 * s + 1);
-  *key = k - 1;
-  *val = v;
-  return k != 0 && ((v << 1) != 0 || (!P.f64 && v != 0));
+// A coefficient word is live unless it is int64 zero or float64 +-0.0.
+__device__ __forceinline__ int live_word(uint64_t v, bool f64) {
+  return (f64 ? (v << 1) != 0 : v != 0) ? 1 : 0;
 }
 
 __device__ __forceinline__ int find_prod_of_chunk(const int64_t* chunk_begin, int nprod, int64_t c) {
@@ -61,32 +29,141 @@ __device__ __forceinline__ int find_prod_of_chunk(const int64_t* chunk_begin, in
 }
 
 __device__ __forceinline__ int64_t accum_slots(const Prod& P) {
-  return P.path == PATH_DENSE ? P.krange : P.slots;
+  return P.path == PATH_DENSE ? P.kspan : P.slots;
+}
+
+// The chunk [s0, s1) of a product's accumulator (8192 dense slots of 8 bytes
+// or 4096 hash slots of 16 bytes) is split into CP_WARPS contiguous parts, one
+// per warp.  A warp holds its part in registers as CP_ROWS rows of 512 bytes,
+// one 16-byte load per lane and row (a dense row: 64 slots, two per lane; a
+// hash row: 32 (key + 1, value) slots, one per lane), so the accumulator is
+// read from memory once per pass and every load is coalesced.
+constexpr int CP_ROWS = 16;
+
+struct Part {
+  int64_t a, b;   // slots [a, b)
+  ulonglong2 v[CP_ROWS];
+};
+
+template <bool STREAM>
+__device__ __forceinline__ ulonglong2 ld_pair(const uint64_t* p) {
+  if constexpr (STREAM) return __ldcs((const ulonglong2*)p); else return *(const ulonglong2*)p;
+}
+
+// Loads the warp's part and returns its number of live slots (in every lane).
+template <bool STREAM>
+__device__ __forceinline__ int load_part(const Prod& P, int64_t s0, int64_t s1, int warp, Part& pt) {
+  const int lane = threadIdx.x & 31;
+  const bool dense = P.path == PATH_DENSE;
+  const int64_t per = P.chunk / CP_WARPS;   // CP_ROWS rows of 64 (dense) or 32 (hash) slots
+  pt.a = min(s1, s0 + per * warp);
+  pt.b = min(s1, pt.a + per);
+  const bool f64 = P.f64;
+  int n = 0;
+  if (dense) {
+    const uint64_t* a = (const uint64_t*)P.dense;
+#pragma unroll
+    for (int t = 0; t < CP_ROWS; ++t) {
+      const int64_t s = pt.a + 64 * t + 2 * lane;
+      ulonglong2 v = make_ulonglong2(0, 0);
+      if (s + 1 < pt.b) v = ld_pair<STREAM>(a + s);
+      else if (s < pt.b) v.x = a[s];
+      pt.v[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < CP_ROWS; ++t) n += live_word(pt.v[t].x, f64) + live_word(pt.v[t].y, f64);
+  } else {
+#pragma unroll
+    for (int t = 0; t < CP_ROWS; ++t) {
+      const int64_t s = pt.a + 32 * t + lane;
+      pt.v[t] = s < pt.b ? ld_pair<STREAM>(P.table + 2 * s) : make_ulonglong2(0, 0);
+    }
+#pragma unroll
+    for (int t = 0; t < CP_ROWS; ++t) n += (pt.v[t].x != 0) & live_word(pt.v[t].y, f64);
+  }
+  return __reduce_add_sync(CP_FULL, (unsigned)n);
+}
+
+// Live slots of the warp's part, streamed (for the counting pass: a few
+// registers, many warps in flight, each row read once and evicted first).
+__device__ __forceinline__ int count_part(const Prod& P, int64_t s0, int64_t s1, int warp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t per = P.chunk / CP_WARPS;
+  const int64_t a0 = min(s1, s0 + per * warp), b0 = min(s1, a0 + per);
+  const bool f64 = P.f64;
+  int n = 0;
+  if (P.path == PATH_DENSE) {
+    const uint64_t* a = (const uint64_t*)P.dense;
+#pragma unroll 4
+    for (int64_t s = a0 + 2 * lane; s < b0; s += 64) {
+      if (s + 1 < b0) {
+        const ulonglong2 v = ld_pair<true>(a + s);
+        n += live_word(v.x, f64) + live_word(v.y, f64);
+      } else {
+        n += live_word(__ldcs(a + s), f64);
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int64_t s = a0 + lane; s < b0; s += 32) {
+      const ulonglong2 kv = ld_pair<true>(P.table + 2 * s);
+      n += (kv.x != 0) & live_word(kv.y, f64);
+    }
+  }
+  return __reduce_add_sync(CP_FULL, (unsigned)n);
+}
+
+// Writes the live slots of the warp's part in slot order from output position
+// `run` (slots outside the part were loaded as zeros, which are not live).
+// Keys are written relative to the product's key window (dense: the slot).
+__device__ __forceinline__ void write_part(const Prod& P, const Part& pt, int64_t run, int64_t cap,
+                                           uint64_t* __restrict__ okey, uint64_t* __restrict__ oval) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const bool f64 = P.f64;
+  if (P.path == PATH_DENSE) {
+#pragma unroll
+    for (int t = 0; t < CP_ROWS; ++t) {
+      const int64_t s = pt.a + 64 * t + 2 * lane;
+      const int f0 = live_word(pt.v[t].x, f64), f1 = live_word(pt.v[t].y, f64);
+      const unsigned b0 = __ballot_sync(CP_FULL, f0), b1 = __ballot_sync(CP_FULL, f1);
+      const int64_t pos = run + __popc(b0 & lt) + __popc(b1 & lt);
+      if (f0 && pos < cap) { okey[pos] = (uint64_t)s; oval[pos] = pt.v[t].x; }
+      if (f1 && pos + f0 < cap) { okey[pos + f0] = (uint64_t)(s + 1); oval[pos + f0] = pt.v[t].y; }
+      run += __popc(b0) + __popc(b1);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < CP_ROWS; ++t) {
+      const int f = (pt.v[t].x != 0) & live_word(pt.v[t].y, f64);
+      const unsigned b = __ballot_sync(CP_FULL, f);
+      const int64_t pos = run + __popc(b & lt);
+      if (f && pos < cap) { okey[pos] = pt.v[t].x - 1 - (uint64_t)P.klo; oval[pos] = pt.v[t].y; }
+      run += __popc(b);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(CP_THREADS) k_compact_count(const Prod* __restrict__ prods, int nprod,
                                                               const int64_t* __restrict__ chunk_begin,
                                                               int64_t* __restrict__ counts) {
   const int64_t nchunks = chunk_begin[nprod];
-  __shared__ int red[CP_THREADS / 32];
+  __shared__ int red[CP_WARPS];
+  const int warp = threadIdx.x >> 5;
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int p = find_prod_of_chunk(chunk_begin, nprod, c);
     const Prod& P = prods[p];
     int n = 0;
-    if (P.status == 0) {
+    if (P.status == 0) {   // uniform across the CTA
       const int64_t s0 = (c - chunk_begin[p]) * P.chunk;
       const int64_t s1 = min(accum_slots(P), s0 + P.chunk);
-      for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        uint64_t k, v;
-        n += slot_live(P, s, &k, &v) ? 1 : 0;
-      }
+      n = count_part(P, s0, s1, warp);
     }
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n;
+    if ((threadIdx.x & 31) == 0) red[warp] = n;
     __syncthreads();
     if (threadIdx.x == 0) {
       int t = 0;
-      for (int w = 0; w < CP_THREADS / 32; ++w) t += red[w];
+      for (int w = 0; w < CP_WARPS; ++w) t += red[w];
       counts[c] = t;
     }
     __syncthreads();
@@ -100,25 +177,22 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(const Prod* __re
                                                                 uint64_t* __restrict__ okey,
                                                                 uint64_t* __restrict__ oval) {
   const int64_t nchunks = chunk_begin[nprod];
+  __shared__ int wsum[CP_WARPS];
+  const int warp = threadIdx.x >> 5;
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int p = find_prod_of_chunk(chunk_begin, nprod, c);
     const Prod& P = prods[p];
     if (P.status != 0) continue;   // uniform across the CTA
     const int64_t s0 = (c - chunk_begin[p]) * P.chunk;
     const int64_t s1 = min(accum_slots(P), s0 + P.chunk);
+    Part pt;
+    const int n = load_part<true>(P, s0, s1, warp, pt);
+    if ((threadIdx.x & 31) == 0) wsum[warp] = n;
+    __syncthreads();
     int64_t run = offs[c];
-    for (int64_t sb = s0; sb < s1; sb += blockDim.x) {
-      const int64_t s = sb + threadIdx.x;
-      uint64_t k = 0, v = 0;
-      const bool live = s < s1 && slot_live(P, s, &k, &v);
-      int tot;
-      const int pos = block_excl_scan_int<CP_THREADS>(live ? 1 : 0, &tot);
-      if (live && run + pos < cap) {
-        okey[run + pos] = k;
-        oval[run + pos] = v;
-      }
-      run += tot;
-    }
+    for (int w = 0; w < warp; ++w) run += wsum[w];
+    write_part(P, pt, run, cap, okey, oval);
+    __syncthreads();   // wsum is rewritten for the next chunk
   }
 }
 
@@ -142,11 +216,22 @@ __global__ void k_finish_counts(Prod* __restrict__ prods, int nprod,
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
                            int64_t* dcounts, uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s) {
   if (nchunks > 0) {
-    const int grid = (int)(nchunks < 152 * 8 ? nchunks : 152 * 8);
-    k_compact_count<<<grid, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts);
+    // persistent grids: every CTA that fits on the GPU at once
+    int dev = 0, sms = 152, pc = 0, ps = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_compact_count, CP_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_compact_scatter, CP_THREADS, 0) != cudaSuccess) {
+      cudaGetLastError();
+      pc = ps = 2;
+    }
+    const int64_t gc = std::min<int64_t>(nchunks, (int64_t)sms * std::max(pc, 1));
+    const int64_t gs = std::min<int64_t>(nchunks, (int64_t)sms * std::max(ps, 1));
+    k_compact_count<<<(unsigned)gc, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts);
     cudaError_t e = launch_scan_exclusive(dcounts, nchunks, dcounts + nchunks, s);
     if (e != cudaSuccess) return e;
-    k_compact_scatter<<<grid, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts, cap, okey, oval);
+    k_compact_scatter<<<(unsigned)gs, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts, cap, okey,
+                                                         oval);
   } else {
     cudaMemsetAsync(dcounts, 0, sizeof(int64_t), s);
   }

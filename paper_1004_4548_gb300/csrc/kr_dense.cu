@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(256) k_dense_plan(const Prod* __restrict__ pro
   const Prod& P = prods[pid];
   if (P.status) return;
   const int64_t b = gw - block_begin[lo];
-  // a truncated product's code range ends inside its last block
-  const int64_t B = b * P.S, E = min(B + P.S, P.krange);
+  // blocks tile the key window [klo, klo + kspan); its end may fall inside the last block
+  const int64_t B = P.klo + b * P.S, E = min(B + P.S, P.klo + P.kspan);
   const int64_t* F = P.f.code;
   const int64_t* G = P.g.code;
   const int64_t nf = P.f.nkeep, ng = P.g.nkeep;   // dropped terms sort last
@@ -198,9 +198,9 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
   constexpr int NW = ACC_THREADS / 32;
   constexpr unsigned FULL = 0xffffffffu;
   const int64_t S = P.S;
-  const int64_t B = tk.block * S;
-  // pairs land in [B, B + lim): the block, clipped to the code range
-  const int64_t lim = min(S, P.krange - B);
+  const int64_t B = P.klo + tk.block * S;
+  // pairs land in [B, B + lim): the block, clipped to the key window
+  const int64_t lim = min(S, P.klo + P.kspan - B);
   const int sh = 28 - __clz((int)S);   // tiles stay within aligned windows of about S / 8 codes
   const int64_t* __restrict__ F = P.f.code;
   const int64_t* __restrict__ G = P.g.code;
@@ -295,8 +295,8 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
 template <typename T>
 __device__ __forceinline__ void dense_flush(const Prod& P, const DenseTask& tk, T* acc) {
   const int64_t S = P.S;
-  const int64_t B = tk.block * S;
-  const int64_t lim = min(S, P.krange - B);
+  const int64_t B = tk.block * S;   // relative to the window
+  const int64_t lim = min(S, P.kspan - B);
   T* out = (T*)P.dense + B;
   for (int64_t s = threadIdx.x; s < lim; s += blockDim.x) {
     const T v = acc[s];

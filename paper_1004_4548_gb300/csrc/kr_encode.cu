@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) k_decode_poly(const Prod* __restrict__ pr
   const Prod& P = prods[prod];
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t code = (int64_t)okey[q];
+    const int64_t code = (int64_t)okey[q] + P.klo;   // keys are relative to the key window
     if (codes) codes[q] = code;
     if (exps) decode_poly_part(P, code, exps, ld, q);
   }
@@ -274,20 +274,18 @@ __global__ void __launch_bounds__(256) k_decode_pseries(const Prod* __restrict__
   const int64_t half = P.T2 - 1;   // sum_k c_k R_k
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t key = (int64_t)okey[q];
+    const int64_t key = (int64_t)okey[q] + P.klo;   // keys are relative to the key window
     if (codes) codes[q] = key;
-    const int64_t kd = key / per_kind;
-    const int64_t rem = key - kd * per_kind;
-    const int64_t T = rem / P.Wp;
-    const int64_t pc = rem - T * P.Wp;
+    const int64_t kd = key >= per_kind ? 1 : 0;   // keys lie below 2 * per_kind
+    int64_t pc;
+    const int64_t T = divmod_nn(key - kd * per_kind, P.Wp, &pc);
     if (kind) kind[q] = (uint8_t)kd;
     if (exps) decode_poly_part(P, pc, exps, ld, q);
     if (trig) {
       int64_t u = T + half;
       for (int k = 0; k < P.nt; ++k) {
-        const int32_t wk = P.w[P.np + k];
-        const int64_t d = (k + 1 < P.nt) ? u % wk : u;
-        u = (k + 1 < P.nt) ? u / wk : 0;
+        int64_t d = u;
+        if (k + 1 < P.nt) u = divmod_nn(u, P.w[P.np + k], &d);
         trig[(int64_t)k * ld + q] = (int32_t)(d + P.omin[P.np + k]);
       }
     }
@@ -322,23 +320,21 @@ __global__ void __launch_bounds__(256) k_decode_batch(const Prod* __restrict__ p
     const ResDesc& R = rd[lo];
     const int64_t t = q - ostart[lo];
     if (t >= R.n) continue;
-    const int64_t key = (int64_t)okey[q];
+    const int64_t key = (int64_t)okey[q] + P.klo;   // keys are relative to the key window
     ((uint64_t*)R.coef)[t] = oval[q];
     if (P.nt == 0) {
       decode_poly_part(P, key, R.exps, R.n, t);
     } else {
       const int64_t per_kind = P.T2 * P.Wp;
-      const int64_t kd = key / per_kind;
-      const int64_t r2 = key - kd * per_kind;
-      const int64_t T = r2 / P.Wp;
-      const int64_t pc = r2 - T * P.Wp;
+      const int64_t kd = key >= per_kind ? 1 : 0;   // keys lie below 2 * per_kind
+      int64_t pc;
+      const int64_t T = divmod_nn(key - kd * per_kind, P.Wp, &pc);
       R.kind[t] = (uint8_t)kd;
       if (P.np > 0) decode_poly_part(P, pc, R.exps, R.n, t);
       int64_t u = T + (P.T2 - 1);
       for (int k = 0; k < P.nt; ++k) {
-        const int32_t wk = P.w[P.np + k];
-        const int64_t d = (k + 1 < P.nt) ? u % wk : u;
-        u = (k + 1 < P.nt) ? u / wk : 0;
+        int64_t d = u;
+        if (k + 1 < P.nt) u = divmod_nn(u, P.w[P.np + k], &d);
         R.trig[(int64_t)k * R.n + t] = (int32_t)(d + P.omin[P.np + k]);
       }
     }
@@ -390,8 +386,8 @@ __global__ void k_decode_box(const int64_t* __restrict__ codes, int64_t n, int n
     int64_t rem = codes[i];
     if (rem < 0 || rem >= W) { bad = 1; rem = 0; }
     for (int k = 0; k < nvars; ++k) {
-      const int64_t d = (k + 1 < nvars) ? rem % b.w[k] : rem;
-      rem = (k + 1 < nvars) ? rem / b.w[k] : 0;
+      int64_t d = rem;
+      if (k + 1 < nvars) rem = divmod_nn(rem, b.w[k], &d);
       exps[(int64_t)k * n + i] = (int32_t)(d + b.emin[k]);
     }
   }

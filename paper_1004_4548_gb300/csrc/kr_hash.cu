@@ -105,6 +105,11 @@ __device__ __forceinline__ bool hash_add_batch(uint64_t* __restrict__ table, uin
   return pend == 0;
 }
 
+// Whether an output key lies in the product's key window.
+__device__ __forceinline__ bool in_window(const Prod& P, uint64_t key) {
+  return !P.clip || key - (uint64_t)P.klo < (uint64_t)P.kspan;
+}
+
 struct HashTile {
   int pid;
   int64_t i0, i1, j0, j1;
@@ -153,12 +158,20 @@ __device__ __forceinline__ bool poly_tile(const Prod& P, const HashTile& h) {
       cr[r] = CF[i];
     }
     const unsigned valid = (1u << m) - 1u;
-    // truncated product: codes at or above krange are beyond the degree
-    // bound.  F is ascending, so the group's first term has the longest
-    // prefix of g below the bound; the others are masked per pair.
-    int64_t jend = h.j1;
-    if (P.graded) jend = min(jend, lower_bound_i64(G, P.g.nkeep, P.krange - fr[0]));
-    for (int64_t j = h.j0 + lane; j < jend; j += 32) {
+    // a key window (or a truncation: codes at or above krange exceed the
+    // degree bound) keeps the keys in [klo, klo + kspan).  F is ascending, so
+    // the group's first term has the longest j-range below the window's end
+    // and its last term the earliest start; the rest is masked per pair.
+    int64_t jbeg = h.j0, jend = h.j1;
+    if (P.clip) {
+      int64_t flast = fr[0];
+#pragma unroll
+      for (int r = 1; r < HGROUP_R; ++r)
+        if (r < m) flast = fr[r];
+      jend = min(jend, lower_bound_i64(G, P.g.nkeep, P.klo + P.kspan - fr[0]));
+      jbeg = max(jbeg, lower_bound_i64(G, P.g.nkeep, P.klo - flast));
+    }
+    for (int64_t j = jbeg + lane; j < jend; j += 32) {
       const int64_t gj = G[j];
       const T cg = CG[j];
       KeyBatch<HGROUP_R, T> kb;
@@ -167,7 +180,7 @@ __device__ __forceinline__ bool poly_tile(const Prod& P, const HashTile& h) {
       for (int r = 0; r < HGROUP_R; ++r) {
         kb.key[r] = (uint64_t)(fr[r] + gj);
         kb.val[r] = cr[r] * cg;
-        if (P.graded && fr[r] + gj >= P.krange) v &= ~(1u << r);
+        if (P.clip && (uint64_t)(fr[r] + gj - P.klo) >= (uint64_t)P.kspan) v &= ~(1u << r);
       }
       ok &= hash_add_batch<HGROUP_R, T>(P.table, mask, P.probe_limit, kb, v);
     }
@@ -227,14 +240,14 @@ __device__ __forceinline__ bool pseries_tile(const Prod& P, const HashTile& h) {
           if (T < 0) { T = -T; if (kd) v = -v; }
           kb.key[2 * u] = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
           kb.val[2 * u] = v;
-          if (keep && !(T == 0 && kd)) valid |= 1u << (2 * u);
+          if (keep && !(T == 0 && kd) && in_window(P, kb.key[2 * u])) valid |= 1u << (2 * u);
           // difference term
           T = tr[r] - tg;
           v = (!kr_[r] && kg) ? -hcoef : hcoef;          // cos*sin: -sin(a-b)
           if (T < 0) { T = -T; if (kd) v = -v; }
           kb.key[2 * u + 1] = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
           kb.val[2 * u + 1] = v;
-          if (keep && !(T == 0 && kd)) valid |= 1u << (2 * u + 1);
+          if (keep && !(T == 0 && kd) && in_window(P, kb.key[2 * u + 1])) valid |= 1u << (2 * u + 1);
         }
         ok &= hash_add_batch<4, double>(P.table, mask, P.probe_limit, kb, valid);
       }
@@ -256,9 +269,9 @@ __device__ __forceinline__ void pseries_dense_tile(const Prod& P, const HashTile
   const uint8_t* __restrict__ KG = P.g.kind;
   const double* __restrict__ CF = (const double*)P.f.coef;   // already halved
   const double* __restrict__ CG = (const double*)P.g.coef;
-  double* __restrict__ out = (double*)P.dense;
+  double* __restrict__ out = (double*)P.dense;   // slot = key - klo
   const int64_t T2Wp = P.T2 * P.Wp;
-  const uint64_t K = (uint64_t)P.krange;
+  const uint64_t K = (uint64_t)P.kspan, K0 = (uint64_t)P.klo;
   for (int64_t i = h.i0 + warp; i < h.i1; i += NW) {
     const int64_t pf = PF[i], tf = TF[i];
     const int kf = KF[i];
@@ -274,14 +287,14 @@ __device__ __forceinline__ void pseries_dense_tile(const Prod& P, const HashTile
       double v = (kf & kg) ? -hcoef : hcoef;
       if (T < 0) { T = -T; if (kd) v = -v; }
       if (!(T == 0 && kd)) {
-        const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+        const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc) - K0;
         if (key < K) atomicAdd(&out[key], v);
       }
       T = tf - tg;
       v = (!kf && kg) ? -hcoef : hcoef;
       if (T < 0) { T = -T; if (kd) v = -v; }
       if (!(T == 0 && kd)) {
-        const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+        const uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc) - K0;
         if (key < K) atomicAdd(&out[key], v);
       }
     }
@@ -314,7 +327,7 @@ __device__ __forceinline__ void hll_tile(const Prod& P, const HashTile& h, uint3
     if (P.nt == 0) {
       for (int64_t j = h.j0 + lane; j < h.j1; j += 32) {
         const int64_t key = fi + G[j];
-        if (!(P.graded && key >= P.krange)) hll_add(reg, (uint64_t)key);
+        if (in_window(P, (uint64_t)key)) hll_add(reg, (uint64_t)key);
       }
     } else {
       const int64_t ti = TF[i];
@@ -325,10 +338,12 @@ __device__ __forceinline__ void hll_tile(const Prod& P, const HashTile& h, uint3
         const int kd = ki ^ KG[j];
         int64_t T = ti + TG[j];
         if (T < 0) T = -T;
-        if (!(T == 0 && kd)) hll_add(reg, (uint64_t)(kd * T2Wp + T * P.Wp + pc));
+        uint64_t key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+        if (!(T == 0 && kd) && in_window(P, key)) hll_add(reg, key);
         T = ti - TG[j];
         if (T < 0) T = -T;
-        if (!(T == 0 && kd)) hll_add(reg, (uint64_t)(kd * T2Wp + T * P.Wp + pc));
+        key = (uint64_t)(kd * T2Wp + T * P.Wp + pc);
+        if (!(T == 0 && kd) && in_window(P, key)) hll_add(reg, key);
       }
     }
   }
@@ -358,6 +373,57 @@ __global__ void __launch_bounds__(HASH_THREADS) k_hll(Prod* __restrict__ prods,
   if (cur >= 0)
     for (int r = threadIdx.x; r < HLL_M; r += blockDim.x)
       if (reg[r]) atomicMax(&prods[cur].hll[r], reg[r]);
+}
+
+// ---------------------------------------------------------------------------
+// Work histogram for splitting a product into key windows: uniformly drawn
+// term pairs, their output keys (as the tiles form them), counted per slice
+// of the key range.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split_count(unsigned long long* hist, int nbins, int64_t krange,
+                                            int64_t key) {
+  if (key < 0 || key >= krange) return;
+  int64_t b = (int64_t)(((unsigned __int128)key * (unsigned)nbins) / (unsigned __int128)krange);
+  if (b >= nbins) b = nbins - 1;
+  atomicAdd(&hist[b], 1ull);
+}
+
+__global__ void __launch_bounds__(256) k_split_sample(const Prod* __restrict__ prods, int prod, int nbins,
+                                                      int64_t nsamples, uint64_t seed,
+                                                      unsigned long long* __restrict__ hist) {
+  const Prod& P = prods[prod];
+  if (P.status) return;
+  const int64_t nf = P.f.nkeep, ng = P.g.nkeep;
+  if (nf <= 0 || ng <= 0) return;
+  const int64_t T2Wp = P.T2 * P.Wp;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nsamples;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (int64_t)(mix64(seed ^ (2ull * (uint64_t)u + 1ull)) % (uint64_t)nf);
+    const int64_t j = (int64_t)(mix64(seed ^ (2ull * (uint64_t)u + 2ull) ^ 0x9e3779b97f4a7c15ull) % (uint64_t)ng);
+    const int64_t pc = P.f.code[i] + P.g.code[j];
+    if (P.nt == 0) {
+      split_count(hist, nbins, P.krange, pc);   // truncated-away keys lie at or above krange
+      continue;
+    }
+    if (P.graded && pc >= P.Wp) continue;
+    const int kd = P.f.kind[i] ^ P.g.kind[j];
+    int64_t T = P.f.tcode[i] + P.g.tcode[j];
+    if (T < 0) T = -T;
+    if (!(T == 0 && kd)) split_count(hist, nbins, P.krange, kd * T2Wp + T * P.Wp + pc);
+    T = P.f.tcode[i] - P.g.tcode[j];
+    if (T < 0) T = -T;
+    if (!(T == 0 && kd)) split_count(hist, nbins, P.krange, kd * T2Wp + T * P.Wp + pc);
+  }
+}
+
+cudaError_t launch_split_sample(const Prod* dprods, int prod, int nbins, int64_t nsamples, uint64_t seed,
+                                unsigned long long* dhist, cudaStream_t s) {
+  if (nsamples > 0) {
+    int64_t grid = (nsamples + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_split_sample<<<(unsigned)grid, 256, 0, s>>>(dprods, prod, nbins, nsamples, seed, dhist);
+  }
+  return cudaGetLastError();
 }
 
 // One CTA per hash product: E = alpha_m m^2 / sum 2^-M_j, with linear counting

@@ -86,11 +86,19 @@ struct Prod {
   int64_t Wp;           // polynomial code range (product of poly widths)
   int64_t T2;           // canonical |trig code| values: (Wt - 1) / 2 + 1
   int64_t krange;       // output key range: Wp, or 2 * T2 * Wp for Poisson
+  // the window of output keys computed: [klo, klo + kspan) (the whole range
+  // unless a window was asked for).  Accumulator slots, compacted keys and
+  // ordering are relative to klo; the decode adds it back.  clip: some pairs
+  // produce keys outside the window (a window or a truncation), so the
+  // per-pair kernels test each key.
+  int64_t klo;
+  int64_t kspan;
+  int32_t clip;
   // dense path
   int64_t S;            // output codes per block
   int64_t nblocks;
   int64_t work_target;  // pairs per task
-  void* dense;          // [krange] accumulators
+  void* dense;          // [kspan] accumulators (slot = key - klo)
   int32_t* gidx;        // gidx[b] = first j with g.code[j] >= b << gshift, b in [0, gidx_n]
   int64_t gidx_n;       // buckets (the last entry gidx[gidx_n] = g.n)
   int32_t gshift;
@@ -152,6 +160,20 @@ __device__ __forceinline__ int64_t g_lower_bound(const int64_t* G, int64_t ng, c
   return lo;
 }
 
+// q = x / d and *r = x % d for x >= 0, d >= 1: 32-bit division when x fits
+// (a 64-bit division costs several times more), which after the first digits
+// of a code is almost always the case.
+__device__ __forceinline__ int64_t divmod_nn(int64_t x, int64_t d, int64_t* r) {
+  if ((uint64_t)x <= 0xffffffffull && d <= 0xffffffffll) {
+    const uint32_t q = (uint32_t)x / (uint32_t)d;
+    *r = (int64_t)((uint32_t)x - q * (uint32_t)d);
+    return q;
+  }
+  const int64_t q = x / d;
+  *r = x - q * d;
+  return q;
+}
+
 // Exponents of the polynomial part of an output code (the inverse of the
 // mixed-radix coding): variable k of the term goes to exps[k * ld + q].  A
 // graded code holds the other variables first and the degree last; the
@@ -160,8 +182,8 @@ __device__ __forceinline__ void decode_poly_part(const Prod& P, int64_t pc, int3
                                                  int64_t ld, int64_t q) {
   if (!P.graded) {
     for (int k = 0; k < P.np; ++k) {
-      const int64_t d = (k + 1 < P.np) ? pc % P.w[k] : pc;
-      pc = (k + 1 < P.np) ? pc / P.w[k] : 0;
+      int64_t d = pc;
+      if (k + 1 < P.np) pc = divmod_nn(pc, P.w[k], &d);
       exps[(int64_t)k * ld + q] = (int32_t)(d + P.omin[k]);
     }
     return;
@@ -169,8 +191,8 @@ __device__ __forceinline__ void decode_poly_part(const Prod& P, int64_t pc, int3
   int64_t deg_rest = 0;
   for (int k = 0; k < P.np; ++k) {
     if (k == P.gvar) continue;
-    const int64_t d = pc % P.w[k];
-    pc /= P.w[k];
+    int64_t d;
+    pc = divmod_nn(pc, P.w[k], &d);
     const int64_t e = d + P.omin[k];
     if ((P.gmask >> k) & 1u) deg_rest += e;
     exps[(int64_t)k * ld + q] = (int32_t)e;
@@ -221,6 +243,10 @@ constexpr int HLL_M = 1 << HLL_B;
 cudaError_t launch_hll(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin, int nhash,
                        int grid, cudaStream_t s);
 cudaError_t launch_hll_estimate(Prod* dprods, const int32_t* dhash_prods, int nhash, cudaStream_t s);
+// Histogram of the output keys of nsamples uniformly drawn term pairs of one
+// product over nbins equal slices of [0, krange) (hist zeroed by the caller).
+cudaError_t launch_split_sample(const Prod* dprods, int prod, int nbins, int64_t nsamples, uint64_t seed,
+                                unsigned long long* dhist, cudaStream_t s);
 cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
                                int nhash, int grid, cudaStream_t s);
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.

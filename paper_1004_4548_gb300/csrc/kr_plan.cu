@@ -149,13 +149,25 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     if (kr > lim) { pl.st = KR_ERR_OVERFLOW; return; }
     P.krange = (int64_t)kr;
   }
+  // ---- window of output keys (the whole range unless one was asked for)
+  P.klo = 0;
+  P.kspan = P.krange;
+  P.clip = P.graded;
+  if (o.code_lo > 0 || o.code_hi > 0) {
+    const int64_t lo = std::max<int64_t>(0, o.code_lo);
+    const int64_t hi = o.code_hi > 0 ? std::min(o.code_hi, P.krange) : P.krange;
+    if (lo >= hi) { pl.empty = true; return; }
+    P.klo = lo;
+    P.kspan = hi - lo;
+    P.clip = 1;
+  }
   const int64_t nf = P.f.n, ng = P.g.n;
   const double pairs = (double)nf * (double)ng;
   P.coef32 = (!job.f64 && P.nt == 0 && rf[3 * MAXV] == 1 && rg[3 * MAXV] == 1) ? 1 : 0;
   // ---- path (Sec. 3.2: the density of the product decides)
   if (job.poisson) {
     // the lookup array of Sec. 3.1 receives both the sum and the difference
-    const bool fits = (double)P.krange * 8.0 <= (double)DENSE_POISSON_MAX_BYTES;
+    const bool fits = (double)P.kspan * 8.0 <= (double)DENSE_POISSON_MAX_BYTES;
     if (o.path == KR_PATH_DENSE) {
       if (!fits) { pl.st = KR_ERR_INVALID; return; }
       P.path = PATH_DENSE;
@@ -166,12 +178,16 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
       P.path = (fits && dense_enough) ? PATH_DENSE : PATH_HASH;
     }
   } else if (o.path == KR_PATH_DENSE) {
-    if ((double)P.krange * 8.0 > (double)DENSE_MAX_BYTES) { pl.st = KR_ERR_INVALID; return; }
+    if ((double)P.kspan * 8.0 > (double)DENSE_MAX_BYTES || P.krange > INT32_MAX) {
+      pl.st = KR_ERR_INVALID;
+      return;
+    }
     P.path = PATH_DENSE;
   } else if (o.path == KR_PATH_HASH) {
     P.path = PATH_HASH;
   } else {
-    const bool fits = (double)P.krange * 8.0 <= (double)DENSE_MAX_BYTES;
+    // (the dense kernels use 32-bit offsets: codes below 2^31)
+    const bool fits = (double)P.kspan * 8.0 <= (double)DENSE_MAX_BYTES && P.krange <= INT32_MAX;
     const bool dense_enough = (double)P.krange <= DENSE_KAPPA * pairs + 65536.0;
     P.path = (fits && dense_enough) ? PATH_DENSE : PATH_HASH;
   }
@@ -200,19 +216,19 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     P.tile_j = HASH_TILE_J;
     P.tiles_j = ceil_div(ng, HASH_TILE_J);
     P.ntasks = ceil_div(nf, HASH_TILE_I) * P.tiles_j;
-    pl.accum_bytes = P.krange * 8;
+    pl.accum_bytes = P.kspan * 8;
     P.chunk = COMPACT_CHUNK;
-    P.nchunks = ceil_div(P.krange, P.chunk);
-    pl.out_cap = (int64_t)std::min((double)P.krange, 2.0 * pairs);
+    P.nchunks = ceil_div(P.kspan, P.chunk);
+    pl.out_cap = (int64_t)std::min((double)P.kspan, 2.0 * pairs);
   } else if (P.path == PATH_DENSE) {
     int64_t S = o.block_slots > 0 ? o.block_slots : DEFAULT_S;
     if (S < 256) S = 256;
     if (S > MAX_S) S = MAX_S;
     S = ceil_div(S, 32) * 32;
-    const int64_t kr32 = ceil_div(P.krange, 32) * 32;
+    const int64_t kr32 = ceil_div(P.kspan, 32) * 32;
     if (S > kr32) S = kr32;
     P.S = S;
-    P.nblocks = ceil_div(P.krange, S);
+    P.nblocks = ceil_div(P.kspan, S);
     // ~6 tasks per resident CTA so the dynamic task queue evens out the
     // uneven (diamond-shaped) work per output block
     const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, (227 * 1024) / (S * 8 + 11264)));
@@ -224,13 +240,13 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     while (((P.g.key_range >> sh) + 1) > 65535) ++sh;
     P.gshift = sh;
     P.gidx_n = (P.g.key_range >> sh) + 1;
-    pl.accum_bytes = P.krange * 8;
+    pl.accum_bytes = P.kspan * 8;
     P.chunk = COMPACT_CHUNK;
-    P.nchunks = ceil_div(P.krange, P.chunk);
-    pl.out_cap = std::min((double)P.krange, pairs) > 0 ? (int64_t)std::min((double)P.krange, pairs) : 0;
+    P.nchunks = ceil_div(P.kspan, P.chunk);
+    pl.out_cap = std::min((double)P.kspan, pairs) > 0 ? (int64_t)std::min((double)P.kspan, pairs) : 0;
   } else {
     const double m = job.poisson ? 2.0 : 1.0;
-    const double upper = std::min(m * pairs, (double)P.krange);
+    const double upper = std::min(m * pairs, (double)P.kspan);
     const double alpha = o.load_factor > 0.0 && o.load_factor <= 0.9 ? o.load_factor : DEFAULT_LOAD;
     pl.bound_slots = next_pow2(std::max<int64_t>(1024, (int64_t)std::ceil(upper / alpha)));
     P.probe_limit = o.probe_limit > 0 ? o.probe_limit : DEFAULT_PROBES;
@@ -238,7 +254,7 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     P.tile_j = HASH_TILE_J;
     P.tiles_j = ceil_div(ng, HASH_TILE_J);
     P.ntasks = ceil_div(nf, HASH_TILE_I) * P.tiles_j;
-    P.chunk = COMPACT_CHUNK;
+    P.chunk = COMPACT_CHUNK_HASH;
     // table size, chunks and output capacity follow in finish_hash_sizes
   }
 }
@@ -246,7 +262,7 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
 void finish_hash_sizes(const kr_opts& o, Plan* pl) {
   Prod& P = pl->p;
   const double m = P.nt > 0 ? 2.0 : 1.0;
-  const double upper = std::min(m * (double)P.f.n * (double)P.g.n, (double)P.krange);
+  const double upper = std::min(m * (double)P.f.n * (double)P.g.n, (double)P.kspan);
   const double alpha = o.load_factor > 0.0 && o.load_factor <= 0.9 ? o.load_factor : DEFAULT_LOAD;
   int64_t slots;
   if (pl->slots_override > 0) {

@@ -25,7 +25,10 @@ constexpr int64_t BITMAP_MAX_BITS = 1600000;   // on-chip bitmap sort (<= 200 KB
 constexpr int64_t BITONIC_MAX_N = 16384;       // shared-memory bitonic sort (128 KB)
 constexpr int64_t DEFAULT_S = 8192;            // dense block: 64 KB of shared memory
 constexpr int64_t MAX_S = 27648;               // 216 KB slice + the 10 KB window table
+// compaction chunks: 8192 dense slots (8 B) or 4096 hash slots (16 B), so that
+// each of the compaction CTA's 8 warps holds 16 rows of 512 bytes
 constexpr int64_t COMPACT_CHUNK = 8192;
+constexpr int64_t COMPACT_CHUNK_HASH = 4096;
 constexpr double DEFAULT_LOAD = 0.5;
 constexpr int DEFAULT_PROBES = 512;
 constexpr int HASH_TILE_I = 32;
@@ -52,7 +55,7 @@ struct Plan {
   int64_t bound_slots = 0;   // hash: table size for the term-product bound at the load factor
   int64_t slots_override = 0;  // hash: table size forced by a regrowth
   bool outcap_full = false;    // hash: output room for a full table (after an overflow)
-  bool empty = false;          // truncation leaves no term: the product is zero
+  bool empty = false;          // truncation or the key window leaves no term: the product is zero
   int passes_f = 0, passes_g = 0;
 };
 

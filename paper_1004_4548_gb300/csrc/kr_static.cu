@@ -97,6 +97,8 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
   P.f64 = type == KR_F64 ? 1 : 0;
   P.path = PATH_DENSE;
   P.krange = W;
+  P.klo = 0;
+  P.kspan = W;
   P.Wp = W;
   P.S = S;
   P.nblocks = nblocks;

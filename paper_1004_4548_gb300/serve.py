@@ -23,9 +23,10 @@ products runs in a batch of its own and no other batch starts while it runs,
 so that the largest products, which set the tail latency, share the GPU with
 at most the batch already running.  A worker releases its
 context's cached scratch after a batch when it holds more than `trim_bytes`.
-A worker that fails (an exception from the library, such as running out of
-memory) reports the failure on the requests of its batch instead of
-dropping them.
+A worker whose batch runs out of device memory releases its context's cached
+scratch, holds off new batches, waits until the other workers are idle and
+runs the batch once more; a batch that fails again (or fails otherwise)
+reports the failure on its requests instead of dropping them.
 """
 from __future__ import annotations
 
@@ -80,6 +81,7 @@ class _Worker:
         self.ctx = B.Context(device)
         self.stream = torch.cuda.Stream(device=device)
         self.busy = False
+        self.retrying = False
         self.thread = None
 
 
@@ -94,6 +96,8 @@ class Server:
         self.giant = giant
         self.trim_bytes = trim_bytes
         self.exclusive = False
+        self.hold = 0             # workers retrying alone after running out of memory
+        self.retry_lock = threading.Lock()
         self.errors: list[str] = []
         self.workers = [_Worker(device) for _ in range(workers)]
         self.mem_budget = mem_budget
@@ -115,6 +119,29 @@ class Server:
         # output (16 B) + ordering scratch (16 B) + table at load 0.5 (32 B) per term
         return 64.0 * out_terms + 1e6
 
+    def _mul(self, w: _Worker, batch: list[Request]):
+        return B.kron_mul_batch([(r.f, r.g) for r in batch], ctx=w.ctx, stream=w.stream,
+                                wave_pairs=self.wave_pairs)
+
+    def _retry_alone(self, w: _Worker, batch: list[Request]):
+        """After running out of memory: free cached scratch, wait for the other
+        workers to finish their batches (no new ones start), run once more."""
+        import torch
+        with self.lock:
+            self.hold += 1
+            w.retrying = True
+        try:
+            w.ctx.trim()
+            with self.retry_lock:   # one retry at a time; others waiting here have trimmed too
+                while any(x.busy and not x.retrying for x in self.workers if x is not w):
+                    time.sleep(0.0005)
+                torch.cuda.empty_cache()
+                return self._mul(w, batch)
+        finally:
+            with self.lock:
+                self.hold -= 1
+                w.retrying = False
+
     def _run_batch(self, w: _Worker, batch: list[Request], t0: float, bytes_: float):
         import torch
         out = None
@@ -123,8 +150,12 @@ class Server:
                 now = time.perf_counter() - t0
                 for r in batch:
                     r.start = now
-                out = B.kron_mul_batch([(r.f, r.g) for r in batch], ctx=w.ctx, stream=w.stream,
-                                       wave_pairs=self.wave_pairs)
+                try:
+                    out = self._mul(w, batch)
+                except B.KronError as e:
+                    if e.status != B.KR_ERR_OOM:
+                        raise
+                    out = self._retry_alone(w, batch)
                 # results are library-owned until the context's next batch: copy them out
                 for r, o in zip(batch, out):
                     r.status = o["status"]
@@ -177,7 +208,7 @@ class Server:
             if now > time_limit:
                 break
             free = [w for w in self.workers if not w.busy]
-            if self.exclusive:
+            if self.exclusive or self.hold:
                 free = []
             if pending and free:
                 with self.lock:
