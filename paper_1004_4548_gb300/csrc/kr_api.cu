@@ -212,6 +212,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   Prod* dprods = nullptr;
   OpRef* dops = nullptr;
   int32_t* dranges = nullptr;
+  char* drs = nullptr;
+  int64_t max_n = 1;
+  for (const JobIn& in : ins) max_n = std::max(max_n, std::max(in.nf, in.ng));
   for (int pass = 0; pass < 2; ++pass) {
     Bump b(pass ? ctx->in_arena : nullptr);
     for (int p = 0; p < nprod; ++p) {
@@ -239,6 +242,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     dprods = b.take<Prod>(nprod);
     dops = b.take<OpRef>(nops);
     dranges = b.take<int32_t>((int64_t)nops * RANGE_STRIDE);
+    drs = b.take<char>((int64_t)range_scan_scratch_bytes(nops, max_n));
     if (!pass) ensure(ctx, &ctx->in_arena, &ctx->in_cap, b.off + 1, s);
   }
   ensure_pinned(ctx, (sizeof(Prod) + 2 * sizeof(OpRef) + 2 * RANGE_STRIDE * 4) * (size_t)nprod + 65536, s);
@@ -267,8 +271,8 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     ck(ctx, cudaMemcpyAsync(dprods, hprods, sizeof(Prod) * nprod, cudaMemcpyHostToDevice, s), "upload");
     ck(ctx, cudaMemcpyAsync(dops, hops, sizeof(OpRef) * nops, cudaMemcpyHostToDevice, s), "upload");
     mark(ctx, s, "begin");
-    ck(ctx, launch_range_scan(dprods, dops, nops, dranges, s), "range scan");
-    ctx->launches += 1;
+    ck(ctx, launch_range_scan(dprods, dops, nops, max_n, drs, dranges, s), "range scan");
+    ctx->launches += 2;
     mark(ctx, s, "range_scan");
     ck(ctx, cudaMemcpyAsync(hranges, dranges, sizeof(int32_t) * nops * RANGE_STRIDE,
                             cudaMemcpyDeviceToHost, s), "download ranges");
@@ -427,7 +431,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       const Prod& P = plans[live_ids[r.prod]].p;
       mx = std::max(mx, ((r.which ? P.g : P.f).key_range + 1023) / 1024);
     }
-    ck(ctx, launch_sort_small(A.lprods, d_bm, (int)bm.size(), SORT_BITMAP, (size_t)mx * 33 * 4 + 64, s),
+    ck(ctx, launch_sort_small(A.lprods, d_bm, (int)bm.size(), SORT_BITMAP, (size_t)mx * 36 * 4 + 64, s),
        "bitmap sort");
     ctx->launches += 1;
   }

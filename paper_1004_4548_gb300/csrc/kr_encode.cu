@@ -17,64 +17,71 @@
 namespace kr {
 
 // ---------------------------------------------------------------------------
-// per-operand minima / maxima of the exponents, max |t| of the multipliers
-// ranges layout per operand: [0, MAXV) min, [MAXV, 2 MAXV) max, [2 MAXV, 3 MAXV) max|t|
+// per-operand minima / maxima of the exponents, max |t| of the multipliers,
+// whether every int64 coefficient fits in int32, and (truncated products) the
+// degree range.  ranges layout per operand: [0, MAXV) min, [MAXV, 2 MAXV) max,
+// [2 MAXV, 3 MAXV) max|t|, then the flags described with RANGE_STRIDE.
+// Two launches: RS_SPLIT CTAs per operand each reduce a slice of the terms to
+// a partial record, then one CTA per operand combines the partials.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_range_scan(const Prod* __restrict__ prods,
-                                                    const OpRef* __restrict__ ops,
-                                                    int32_t* __restrict__ ranges) {
-  const OpRef r = ops[blockIdx.x];
+constexpr int RS_THREADS = 256;
+constexpr int RS_SPLIT_MAX = 64;
+constexpr int64_t RS_TERMS_PER_CTA = 1024;
+
+struct RangePart {
+  int32_t lo[MAXV], hi[MAXV], tmax[MAXV];
+  int32_t fits;
+  int32_t pad;
+  long long dlo, dhi;
+};
+
+int range_scan_splits(int64_t max_n) {
+  int64_t k = (max_n + RS_TERMS_PER_CTA - 1) / RS_TERMS_PER_CTA;
+  return (int)(k < 1 ? 1 : (k > RS_SPLIT_MAX ? RS_SPLIT_MAX : k));
+}
+
+size_t range_scan_scratch_bytes(int nops, int64_t max_n) {
+  return sizeof(RangePart) * (size_t)nops * (size_t)range_scan_splits(max_n);
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_range_partial(const Prod* __restrict__ prods,
+                                                              const OpRef* __restrict__ ops,
+                                                              RangePart* __restrict__ parts) {
+  const OpRef r = ops[blockIdx.y];
   const Prod& P = prods[r.prod];
   const Operand& O = r.which ? P.g : P.f;
-  __shared__ int32_t smin[MAXV][16], smax[MAXV][16];
+  const int64_t i0 = O.n * blockIdx.x / gridDim.x, i1 = O.n * (blockIdx.x + 1) / gridDim.x;
+  __shared__ int32_t smin[MAXV][RS_THREADS / 32], smax[MAXV][RS_THREADS / 32];
+  __shared__ int sfits[RS_THREADS / 32];
+  __shared__ long long sdlo[RS_THREADS / 32], sdhi[RS_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nvar = P.np + P.nt;
   for (int k = 0; k < nvar; ++k) {
     const bool is_trig = k >= P.np;
     const int32_t* row = is_trig ? O.t + (int64_t)(k - P.np) * O.n : O.e + (int64_t)k * O.n;
     int32_t lo = INT32_MAX, hi = INT32_MIN;
-    for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       int32_t x = row[i];
       if (is_trig) x = x < 0 ? -x : x;
       lo = min(lo, x);
       hi = max(hi, x);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-      hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
     if (lane == 0) { smin[k][warp] = lo; smax[k][warp] = hi; }
   }
-  // do all coefficients (int64) fit in int32?
-  __shared__ int fits_all;
-  if (threadIdx.x == 0) fits_all = 1;
-  __syncthreads();
+  int fits = 1;
   if (!P.f64) {
-    int fits = 1;
     const int64_t* c = (const int64_t*)O.c;
-    for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x)
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
       if (c[i] < INT32_MIN || c[i] > INT32_MAX) fits = 0;
-    if (!__all_sync(0xffffffffu, fits) && lane == 0) fits_all = 0;
-  } else if (threadIdx.x == 0) {
-    fits_all = 0;
+  } else {
+    fits = 0;
   }
-  __syncthreads();
-  int32_t* out = ranges + (int64_t)blockIdx.x * RANGE_STRIDE;
-  if (threadIdx.x < nvar) {
-    const int k = threadIdx.x;
-    int32_t lo = INT32_MAX, hi = INT32_MIN;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { lo = min(lo, smin[k][w]); hi = max(hi, smax[k][w]); }
-    if (k < P.np) { out[k] = lo; out[MAXV + k] = hi; }
-    else { out[2 * MAXV + (k - P.np)] = hi; }
-  }
-  if (threadIdx.x == 0) out[3 * MAXV] = fits_all;
+  fits = __all_sync(0xffffffffu, fits);
+  long long dlo = LLONG_MAX, dhi = LLONG_MIN;
   if (P.gmask) {
-    // least and largest degree in the truncation variables (int64 sums)
-    __shared__ long long dlo_s, dhi_s;
-    if (threadIdx.x == 0) { dlo_s = LLONG_MAX; dhi_s = LLONG_MIN; }
-    __syncthreads();
-    long long dlo = LLONG_MAX, dhi = LLONG_MIN;
-    for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
       long long d = 0;
       for (int k = 0; k < P.np; ++k)
         if ((P.gmask >> k) & 1u) d += O.e[(int64_t)k * O.n + i];
@@ -85,20 +92,64 @@ __global__ void __launch_bounds__(512) k_range_scan(const Prod* __restrict__ pro
       dlo = min(dlo, __shfl_xor_sync(0xffffffffu, dlo, o));
       dhi = max(dhi, __shfl_xor_sync(0xffffffffu, dhi, o));
     }
-    if (lane == 0) { atomicMin(&dlo_s, dlo); atomicMax(&dhi_s, dhi); }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const bool over = dlo_s < INT32_MIN || dhi_s > INT32_MAX;
-      out[3 * MAXV + 1] = over ? 0 : (int32_t)dlo_s;
-      out[3 * MAXV + 2] = over ? 0 : (int32_t)dhi_s;
+  }
+  if (lane == 0) { sfits[warp] = fits; sdlo[warp] = dlo; sdhi[warp] = dhi; }
+  __syncthreads();
+  RangePart& out = parts[(int64_t)blockIdx.y * gridDim.x + blockIdx.x];
+  if (threadIdx.x < nvar) {
+    const int k = threadIdx.x;
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int w = 0; w < RS_THREADS / 32; ++w) { lo = min(lo, smin[k][w]); hi = max(hi, smax[k][w]); }
+    out.lo[k] = lo;
+    out.hi[k] = hi;
+  }
+  if (threadIdx.x == 0) {
+    int f = 1;
+    long long a = LLONG_MAX, b = LLONG_MIN;
+    for (int w = 0; w < RS_THREADS / 32; ++w) { f &= sfits[w]; a = min(a, sdlo[w]); b = max(b, sdhi[w]); }
+    out.fits = f;
+    out.dlo = a;
+    out.dhi = b;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_range_reduce(const Prod* __restrict__ prods,
+                                                     const OpRef* __restrict__ ops, int nsplit,
+                                                     const RangePart* __restrict__ parts,
+                                                     int32_t* __restrict__ ranges) {
+  const OpRef r = ops[blockIdx.x];
+  const Prod& P = prods[r.prod];
+  const RangePart* pp = parts + (int64_t)blockIdx.x * nsplit;
+  int32_t* out = ranges + (int64_t)blockIdx.x * RANGE_STRIDE;
+  const int k = threadIdx.x;
+  if (k < P.np + P.nt) {
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int s = 0; s < nsplit; ++s) { lo = min(lo, pp[s].lo[k]); hi = max(hi, pp[s].hi[k]); }
+    if (k < P.np) { out[k] = lo; out[MAXV + k] = hi; }
+    else { out[2 * MAXV + (k - P.np)] = hi; }
+  }
+  if (k == 0) {
+    int f = 1;
+    long long a = LLONG_MAX, b = LLONG_MIN;
+    for (int s = 0; s < nsplit; ++s) { f &= pp[s].fits; a = min(a, pp[s].dlo); b = max(b, pp[s].dhi); }
+    out[3 * MAXV] = f;
+    if (P.gmask) {
+      const bool over = a < INT32_MIN || b > INT32_MAX;
+      out[3 * MAXV + 1] = over ? 0 : (int32_t)a;
+      out[3 * MAXV + 2] = over ? 0 : (int32_t)b;
       out[3 * MAXV + 3] = over ? 1 : 0;
     }
   }
 }
 
-cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int32_t* dranges,
-                              cudaStream_t s) {
-  if (nops > 0) k_range_scan<<<nops, 512, 0, s>>>(dprods, dops, dranges);
+cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int64_t max_n, void* scratch,
+                              int32_t* dranges, cudaStream_t s) {
+  if (nops > 0) {
+    const int split = range_scan_splits(max_n);
+    RangePart* parts = (RangePart*)scratch;
+    k_range_partial<<<dim3(split, nops), RS_THREADS, 0, s>>>(dprods, dops, parts);
+    k_range_reduce<<<nops, 32, 0, s>>>(dprods, dops, split, parts, dranges);
+  }
   return cudaGetLastError();
 }
 

@@ -218,8 +218,11 @@ struct OpRef {      // (product, operand) pair addressed by a per-operand kernel
   int32_t which;    // 0 = f, 1 = g
 };
 
-cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int32_t* dranges,
-                              cudaStream_t s);
+// Range records of every operand (min / max exponents, max |t|, flags); the
+// scratch holds range_scan_scratch_bytes(nops, max_n) bytes.
+size_t range_scan_scratch_bytes(int nops, int64_t max_n);
+cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int64_t max_n, void* scratch,
+                              int32_t* dranges, cudaStream_t s);
 cudaError_t launch_encode(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s);
 cudaError_t launch_sort_small(Prod* dprods, const OpRef* dops, int nops, int method,
                               size_t smem, cudaStream_t s);

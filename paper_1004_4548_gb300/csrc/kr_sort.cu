@@ -68,7 +68,9 @@ cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, cudaSt
 }
 
 // ---------------------------------------------------------------------------
-// bitmap rank sort (one CTA per operand)
+// bitmap rank sort (one CTA per operand).  Shared memory: the bitmap (32-bit
+// words, padded to groups of 32 words) and, per 8 words, the number of set
+// bits before them, so the rank of a key costs at most 8 popcounts.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_bitmap_sort(Prod* __restrict__ prods,
                                                       const OpRef* __restrict__ ops) {
@@ -78,9 +80,11 @@ __global__ void __launch_bounds__(1024) k_bitmap_sort(Prod* __restrict__ prods,
   Operand& O = r.which ? P.g : P.f;
   const int64_t nwords = (O.key_range + 31) >> 5;
   const int64_t ngroups = (nwords + 31) >> 5;
+  const int64_t nw = ngroups * 32;       // padded bitmap words
+  const int64_t n8 = nw >> 3;            // 8-word blocks
   uint32_t* bits = sm;
-  uint32_t* gpre = sm + ngroups * 32;
-  for (int64_t w = threadIdx.x; w < ngroups * 32; w += blockDim.x) bits[w] = 0;
+  uint32_t* pre8 = sm + nw;
+  for (int64_t w = threadIdx.x; w < nw; w += blockDim.x) bits[w] = 0;
   __syncthreads();
   uint32_t dup = 0;
   for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x) {
@@ -90,29 +94,31 @@ __global__ void __launch_bounds__(1024) k_bitmap_sort(Prod* __restrict__ prods,
     if (old & bit) dup = 1;
   }
   __syncthreads();
-  // per-group popcounts, then an exclusive scan over the groups
-  const int64_t per = (ngroups + blockDim.x - 1) / blockDim.x;
-  const int64_t ga = min(ngroups, per * threadIdx.x), gb = min(ngroups, ga + per);
+  // set bits per 8-word block, each thread over a contiguous range of blocks,
+  // then an exclusive scan over the threads
+  const int64_t per = (n8 + blockDim.x - 1) / blockDim.x;
+  const int64_t ba = min(n8, per * threadIdx.x), bb = min(n8, ba + per);
   int64_t s = 0;
-  for (int64_t g = ga; g < gb; ++g) {
-    uint32_t c = 0;
-    for (int w = 0; w < 32; ++w) c += __popc(bits[g * 32 + w]);
-    gpre[g] = c;
+  for (int64_t b = ba; b < bb; ++b) {
+    const uint4 lo = *(const uint4*)&bits[8 * b];
+    const uint4 hi = *(const uint4*)&bits[8 * b + 4];
+    const uint32_t c = __popc(lo.x) + __popc(lo.y) + __popc(lo.z) + __popc(lo.w) +
+                       __popc(hi.x) + __popc(hi.y) + __popc(hi.z) + __popc(hi.w);
+    pre8[b] = c;
     s += c;
   }
   int64_t run = block_exclusive_scan<1024>(s, nullptr);
-  for (int64_t g = ga; g < gb; ++g) {
-    uint32_t c = gpre[g];
-    gpre[g] = (uint32_t)run;
+  for (int64_t b = ba; b < bb; ++b) {
+    const uint32_t c = pre8[b];
+    pre8[b] = (uint32_t)run;
     run += c;
   }
   __syncthreads();
   for (int64_t i = threadIdx.x; i < O.n; i += blockDim.x) {
     const uint64_t key = O.skey[i];
     const int64_t w = (int64_t)(key >> 5);
-    const int64_t g = w >> 5;
-    uint32_t rank = gpre[g];
-    for (int64_t x = g * 32; x < w; ++x) rank += __popc(bits[x]);
+    uint32_t rank = pre8[w >> 3];
+    for (int64_t x = w & ~(int64_t)7; x < w; ++x) rank += __popc(bits[x]);
     rank += __popc(bits[w] & ((1u << (key & 31)) - 1u));
     if (rank >= O.n) { dup = 1; continue; }
     O.skey2[rank] = key;
