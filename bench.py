@@ -118,9 +118,9 @@ class Clocks:
 
 
 # DRAM bytes (read + write) per launch of k_dense_accum on this workload, from
-# one ncu capture (profiles/k_dense_accum_cfg2.md); valid only for the kernel
-# source it was taken on, identified by the leading hex digits of its SHA-256.
-DENSE_TRAFFIC = {"source_sha256": "964e275ba9055a27", "bytes": 2769920}
+# one ncu capture of the kernel on it; valid only for the kernel source it was
+# taken on, identified by the leading hex digits of its SHA-256.
+DENSE_TRAFFIC = {"source_sha256": "943f6fe7fba0ede4", "bytes": 2740992}
 
 
 def dense_traffic():
