@@ -149,11 +149,48 @@ __device__ __forceinline__ void smem_add<double>(double* p, double v) {
   atomicAdd(p, v);
 }
 
+// The accumulator slice of a block in shared memory (8 bytes per code).
+// int64 sums are held as two 32-bit words per slot (low words in [0, S), high
+// words in [S, 2S)): a 64-bit add is a 32-bit add of the low word, whose
+// returned old value gives the carry, plus a 32-bit add of high word and carry
+// when that is nonzero.  The sums stay exact modulo 2^64 whatever the order of
+// the adds, since each carry is seen by exactly the add that makes it.
+// Shared-memory 32-bit atomics run several times faster than 64-bit ones on
+// this GPU (measured chip-wide, conflict-free: 8.8 T vs 1.6 T adds/s).
+// float64 sums use 64-bit atomic adds.
+template <typename T>
+struct Slice;
+
+template <>
+struct Slice<int64_t> {
+  uint32_t* lo;
+  uint32_t* hi;
+  __device__ __forceinline__ Slice(void* base, int64_t S) : lo((uint32_t*)base), hi((uint32_t*)base + S) {}
+  __device__ __forceinline__ void add(int32_t off, int64_t v) const {
+    const uint64_t u = (uint64_t)v;
+    const uint32_t l = (uint32_t)u;
+    const uint32_t old = atomicAdd(&lo[off], l);
+    const uint32_t h = (uint32_t)(u >> 32) + ((uint32_t)(old + l) < old ? 1u : 0u);
+    if (h) atomicAdd(&hi[off], h);
+  }
+  __device__ __forceinline__ int64_t get(int64_t s) const {
+    return (int64_t)(((uint64_t)hi[s] << 32) | (uint64_t)lo[s]);
+  }
+};
+
+template <>
+struct Slice<double> {
+  double* a;
+  __device__ __forceinline__ Slice(void* base, int64_t) : a((double*)base) {}
+  __device__ __forceinline__ void add(int32_t off, double v) const { atomicAdd(&a[off], v); }
+  __device__ __forceinline__ double get(int64_t s) const { return a[s]; }
+};
+
 // Per-chunk window table of a task, in shared memory: for the chunk's f terms,
 // the slice offset of F_i (32-bit), the first j of its window, the exclusive
 // prefix of the window lengths (excl[ACC_THREADS] = total) and the coefficient.
 struct ChunkTable {
-  int32_t f32[ACC_THREADS];
+  int2 fc[ACC_THREADS];               // (F_i - B, coefficient as int32 when it fits) of every f term
   int32_t lo[ACC_THREADS];            // first j of the tile's window (tile owners)
   int16_t run[ACC_THREADS];           // tile length (0: not a tile owner)
   int32_t excl[ACC_THREADS + 1];
@@ -192,7 +229,7 @@ __device__ __forceinline__ T mul(T a, T b) {
 }
 
 template <typename T, bool C32>
-__device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& tk, T* acc,
+__device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& tk, const Slice<T>& acc,
                                                 ChunkTable& ct) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NW = ACC_THREADS / 32;
@@ -214,7 +251,7 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
     if (i < tk.i1) {
       const int64_t fc = F[i];
       // the offset of the next term too, so that the walk reads two per load
-      ct.f32[threadIdx.x] = (int32_t)(fc - B);
+      ct.fc[threadIdx.x] = make_int2((int32_t)(fc - B), C32 ? (int32_t)(int64_t)CF[i] : 0);
       const bool owner = threadIdx.x == 0 || (fc >> sh) != (F[i - 1] >> sh) ||
                          ((i - tk.i0) & (TILE_R - 1)) == 0;
       if (owner) {
@@ -283,8 +320,12 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
         const T* __restrict__ cf = CF + (ib + k);
 #pragma unroll 4
         for (int a = 0; a < rk; ++a) {
-          const int32_t off = ct.f32[k + a] + gc;
-          if ((uint32_t)off < (uint32_t)S) smem_add<T>(&acc[off], mul<T, C32>(cf[a], cg));
+          const int2 e = ct.fc[k + a];
+          const int32_t off = e.x + gc;
+          if ((uint32_t)off < (uint32_t)S) {
+            if constexpr (C32) acc.add(off, (T)((int64_t)e.y * (int64_t)(int32_t)cg));
+            else acc.add(off, mul<T, C32>(cf[a], cg));
+          }
         }
       }
     }
@@ -293,13 +334,13 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
 }
 
 template <typename T>
-__device__ __forceinline__ void dense_flush(const Prod& P, const DenseTask& tk, T* acc) {
+__device__ __forceinline__ void dense_flush(const Prod& P, const DenseTask& tk, const Slice<T>& acc) {
   const int64_t S = P.S;
   const int64_t B = tk.block * S;   // relative to the window
   const int64_t lim = min(S, P.kspan - B);
   T* out = (T*)P.dense + B;
   for (int64_t s = threadIdx.x; s < lim; s += blockDim.x) {
-    const T v = acc[s];
+    const T v = acc.get(s);
     if (v != (T)0) {
       if (tk.single) out[s] = v;
       else smem_add<T>(&out[s], v);   // generic atomicAdd works on global memory too
@@ -326,16 +367,22 @@ __global__ void __launch_bounds__(ACC_THREADS, 3) k_dense_accum(const Prod* __re
     const Prod& P = prods[tk.prod];
     if (P.status) continue;
     const int64_t S = P.S;
-    // zero the slice (both types are 8 bytes wide)
+    // zero the slice (8 bytes per code for both types)
     int64_t* z = (int64_t*)smem_raw;
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x) z[s] = 0;
     __syncthreads();
-    if (P.f64) dense_task_body<double, false>(P, tk, (double*)smem_raw, ct);
-    else if (P.coef32) dense_task_body<int64_t, true>(P, tk, (int64_t*)smem_raw, ct);
-    else dense_task_body<int64_t, false>(P, tk, (int64_t*)smem_raw, ct);
-    __syncthreads();
-    if (P.f64) dense_flush<double>(P, tk, (double*)smem_raw);
-    else dense_flush<int64_t>(P, tk, (int64_t*)smem_raw);
+    if (P.f64) {
+      const Slice<double> sl(smem_raw, S);
+      dense_task_body<double, false>(P, tk, sl, ct);
+      __syncthreads();
+      dense_flush<double>(P, tk, sl);
+    } else {
+      const Slice<int64_t> sl(smem_raw, S);
+      if (P.coef32) dense_task_body<int64_t, true>(P, tk, sl, ct);
+      else dense_task_body<int64_t, false>(P, tk, sl, ct);
+      __syncthreads();
+      dense_flush<int64_t>(P, tk, sl);
+    }
     __syncthreads();
   }
 }

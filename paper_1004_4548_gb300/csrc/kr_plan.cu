@@ -4,6 +4,12 @@
 
 #include "kr_plan.h"
 
+// dense path: tasks per resident CTA (more: a shorter tail of the dynamic
+// task queue; fewer: less zeroing and flushing of block slices)
+#ifndef KR_TASKS_PER_CTA
+#define KR_TASKS_PER_CTA 6
+#endif
+
 namespace kr {
 
 int bits_for(uint64_t range) {
@@ -232,7 +238,7 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     // ~6 tasks per resident CTA so the dynamic task queue evens out the
     // uneven (diamond-shaped) work per output block
     const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, (227 * 1024) / (S * 8 + 11264)));
-    const double tgt = pairs / (double)(num_sms * per_sm * 6);
+    const double tgt = pairs / (double)(num_sms * per_sm * KR_TASKS_PER_CTA);
     P.work_target = (int64_t)std::max(tgt, (double)(2 * S));
     pl.dense_task_cap = P.nblocks * 64;
     // bucket index over g's codes: at most 65536 buckets
