@@ -362,6 +362,15 @@ kr_status kron_dense_product_static(const int64_t* fcode, const void* fcoef, int
  * small device buffer; synchronises the device's default stream. */
 double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t reps);
 
+/* Chip-wide rate of conflict-free int64 accumulates into shared memory in the
+ * form the dense path's kernel uses (a 32-bit atomic add of the low word that
+ * returns the old value, the carry, a 32-bit atomic add of the high word),
+ * with a negative addend so that both adds happen: best of `reps` launches, in
+ * accumulates per second; < 0 on failure.  The dense path's ceiling for int64
+ * coefficients.  Allocates and frees a small device buffer; synchronises the
+ * device's default stream. */
+double kr_probe_smem_accumulate_rate(int32_t device, int32_t reps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,7 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_double)]),
     "kr_ctx_launch_count": (_i64, [_vp]),
     "kr_probe_smem_atomic_rate": (ctypes.c_double, [_i32, _i32, _i32]),
+    "kr_probe_smem_accumulate_rate": (ctypes.c_double, [_i32, _i32]),
     "kron_dense_product_static": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_int, _i64,
                                                  _vp, _vp]),
     "kron_plan": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
@@ -258,6 +259,12 @@ def _alloc(shape, dtype, device, host):
 def kr_probe_smem_atomic_rate(device: int = 0, f64: bool = False, reps: int = 5) -> float:
     """Shared-memory 64-bit atomic adds per second, whole chip (measured)."""
     return float(load().kr_probe_smem_atomic_rate(device, int(f64), reps))
+
+
+def kr_probe_smem_accumulate_rate(device: int = 0, reps: int = 5) -> float:
+    """Measured conflict-free rate of the dense kernel's int64 shared-memory
+    accumulate (two 32-bit atomics with a carry), accumulates per second."""
+    return float(load().kr_probe_smem_accumulate_rate(device, reps))
 
 
 def kron_plan(emin, emax):

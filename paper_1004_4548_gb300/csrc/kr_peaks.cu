@@ -2,8 +2,10 @@
 // multiplication by its clock cycles per monomial-by-monomial multiplication
 // (Sec. 5) and calls a kernel optimal when that count approaches the cost of
 // one coefficient multiply-add.  On the GPU the dense path's multiply-add is a
-// shared-memory atomic add of a product, so its ceiling is the chip-wide rate
-// of conflict-free shared-memory atomic adds, measured here.
+// shared-memory atomic accumulate of a product, so its ceiling is the
+// chip-wide rate of conflict-free accumulates, measured here: plain 64-bit
+// atomic adds (int64 or float64), and the int64 accumulate in the form the
+// dense kernel uses (two 32-bit atomics with a carry).
 #include <algorithm>
 
 #include "kr_internal.cuh"
@@ -51,9 +53,66 @@ __global__ void __launch_bounds__(PK_THREADS) k_probe_smem_atomic<int64_t>(int64
   if (acc == ~0ull) sink[blockIdx.x] = (int64_t)acc;
 }
 
+// The dense path's int64 accumulate as the kernel performs it: a 32-bit add
+// of the low word returning the old value, the carry, and a 32-bit add of the
+// high word (nonzero here, as for any negative addend).
+__global__ void __launch_bounds__(PK_THREADS) k_probe_smem_split64(int64_t* __restrict__ sink, int64_t inc) {
+  __shared__ uint32_t s[2 * PK_SLOTS];
+  for (int i = threadIdx.x; i < 2 * PK_SLOTS; i += blockDim.x) s[i] = 0;
+  __syncthreads();
+  const uint64_t u = (uint64_t)inc;
+  const uint32_t l = (uint32_t)u, h0 = (uint32_t)(u >> 32);
+  int a = threadIdx.x;
+#pragma unroll 16
+  for (int it = 0; it < PK_ITERS; ++it) {
+    const uint32_t old = atomicAdd(&s[a], l);
+    const uint32_t h = h0 + ((uint32_t)(old + l) < old ? 1u : 0u);
+    if (h) atomicAdd(&s[PK_SLOTS + a], h);
+    a = (a + PK_THREADS) & (PK_SLOTS - 1);
+  }
+  __syncthreads();
+  uint64_t acc = 0;
+  for (int i = threadIdx.x; i < PK_SLOTS; i += blockDim.x) acc += ((uint64_t)s[PK_SLOTS + i] << 32) | s[i];
+  if (acc == ~0ull) sink[blockIdx.x] = (int64_t)acc;
+}
+
 }  // namespace kr
 
 using namespace kr;
+
+extern "C" double kr_probe_smem_accumulate_rate(int32_t device, int32_t reps) {
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return -1.0; }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_smem_split64, PK_THREADS, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int grid = sms * per_sm;
+  void* sink = nullptr;
+  double best = -1.0;
+  cudaEvent_t a, b;
+  if (cudaMalloc(&sink, (size_t)grid * 8) != cudaSuccess) { cudaGetLastError(); cudaSetDevice(prev); return -1.0; }
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int r = 0; r < (reps > 0 ? reps : 5) + 1; ++r) {
+    cudaEventRecord(a, 0);
+    k_probe_smem_split64<<<grid, PK_THREADS>>>((int64_t*)sink, -1);
+    cudaEventRecord(b, 0);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double ops = (double)grid * PK_THREADS * PK_ITERS;
+    if (r > 0 && ms > 0.f) best = std::max(best, ops / (ms * 1e-3));
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (cudaGetLastError() != cudaSuccess) best = -1.0;
+  cudaSetDevice(prev);
+  return best;
+}
 
 extern "C" double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t reps) {
   int prev = 0;

@@ -294,3 +294,12 @@ def test_encode_decode_roundtrip(kron):
     with pytest.raises(kron.KronError) as e:
         kron.kron_encode(allp, lo, hi - 1)
     assert e.value.status == kron.KR_ERR_RANGE
+
+
+def test_peak_probes_report_rates(kron):
+    """The roofline denominators: positive chip-wide rates, and the int64
+    accumulate in two 32-bit atomics no slower than one 64-bit atomic add."""
+    r64 = kron.kr_probe_smem_atomic_rate(0, False, 2)
+    rsplit = kron.kr_probe_smem_accumulate_rate(0, 2)
+    assert r64 > 1e10 and rsplit > 1e10
+    assert rsplit > 0.8 * r64
