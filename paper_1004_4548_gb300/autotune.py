@@ -25,7 +25,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(HERE, "tuned.json")
 
-DENSE_S = (2048, 4096, 8192, 16384)
+# dense block sizes: a batch's dense products share one launch whose shared
+# memory per CTA is set by its largest block, so larger blocks would lower the
+# occupancy of every product in the batch
+DENSE_S = (2048, 4096, 8192)
 HASH_ALPHA = (0.3, 0.5, 0.7)
 
 _table_cache: dict | None = None
