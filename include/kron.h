@@ -62,7 +62,8 @@ typedef enum {
   KR_ERR_DUP = 4,        /* an input series repeats a term key */
   KR_ERR_OOM = 5,        /* device or pinned-host allocation failed */
   KR_ERR_CAPACITY = 6,   /* output buffers too small; required count returned */
-  KR_ERR_TIMEOUT = 7,    /* a bounded device wait gave up */
+  KR_ERR_TIMEOUT = 7,    /* a bounded device wait gave up (the compaction's wait on a
+                            preceding chunk); the call's results are unreliable */
   KR_ERR_CUDA = 8,       /* a CUDA runtime call failed; see kr_last_error */
   KR_ERR_TABLE_FULL = 9, /* hash table full after every allowed regrowth */
   KR_ERR_TOO_LARGE = 10  /* the problem exceeds a fixed limit of the entry point */
@@ -370,6 +371,14 @@ double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t reps);
  * coefficients.  Allocates and frees a small device buffer; synchronises the
  * device's default stream. */
 double kr_probe_smem_accumulate_rate(int32_t device, int32_t reps);
+
+/* Self-test of the library's bounded device waits (the compaction's look-back
+ * over preceding chunks): runs the wait against a predecessor that never
+ * publishes, on CUDA device `device`, and returns KR_ERR_TIMEOUT when the wait
+ * gave up and reported it as it must (KR_OK would mean it did not; KR_ERR_CUDA
+ * on a CUDA failure).  The wait ends by itself after roughly 0.1 to 1 s; the
+ * device stays usable.  Allocates and frees 128 bytes; synchronises the device. */
+kr_status kr_selftest_bounded_wait(int32_t device);
 
 #ifdef __cplusplus
 }

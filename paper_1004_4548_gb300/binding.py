@@ -76,6 +76,7 @@ SIGNATURES = {
     "kr_ctx_launch_count": (_i64, [_vp]),
     "kr_probe_smem_atomic_rate": (ctypes.c_double, [_i32, _i32, _i32]),
     "kr_probe_smem_accumulate_rate": (ctypes.c_double, [_i32, _i32]),
+    "kr_selftest_bounded_wait": (ctypes.c_int, [_i32]),
     "kron_dense_product_static": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_int, _i64,
                                                  _vp, _vp]),
     "kron_plan": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
@@ -259,6 +260,12 @@ def _alloc(shape, dtype, device, host):
 def kr_probe_smem_atomic_rate(device: int = 0, f64: bool = False, reps: int = 5) -> float:
     """Shared-memory 64-bit atomic adds per second, whole chip (measured)."""
     return float(load().kr_probe_smem_atomic_rate(device, int(f64), reps))
+
+
+def kr_selftest_bounded_wait(device: int = 0) -> int:
+    """Status of the bounded-wait self-test: KR_ERR_TIMEOUT when a wait on a
+    predecessor that never publishes gave up and was reported."""
+    return int(load().kr_selftest_bounded_wait(device))
 
 
 def kr_probe_smem_accumulate_rate(device: int = 0, reps: int = 5) -> float:

@@ -533,7 +533,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     h_chunk_begin[nlive] = nchunks_total;
     struct B2 {
       int64_t* chunk_begin; int64_t* counts; int64_t* scan; int64_t* bins; uint64_t *okey, *oval, *okey2, *oval2;
-      int64_t* counters; char* zero; size_t zero_bytes;
+      int64_t* counters; uint64_t* cstat; char* zero; size_t zero_bytes;
     } Z{};
     for (int pass = 0; pass < 2; ++pass) {
       Bump b(pass ? ctx->acc : nullptr);
@@ -549,7 +549,8 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       b.off = (b.off + 255) / 256 * 256;
       const size_t zero_start = b.off;
       Z.zero = b.base ? b.base + zero_start : nullptr;
-      Z.counters = b.take<int64_t>(4);
+      Z.counters = b.take<int64_t>(4);   // dense task queue (2), compaction ticket and error flag
+      Z.cstat = b.take<uint64_t>(nchunks_total + 1);
       for (int p : live_ids) {
         Plan& pl = plans[p];
         if (pl.p.path == PATH_DENSE) pl.p.dense = (void*)b.take<uint64_t>(pl.p.kspan);
@@ -592,10 +593,10 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       ctx->launches += 1;
       mark(ctx, s, "hash_insert");
     }
-    ck(ctx, launch_compact(A.lprods, nlive, Z.chunk_begin, nchunks_total, Z.counts, Z.okey, Z.oval,
-                           out_total, s),
+    ck(ctx, launch_compact(A.lprods, nlive, Z.chunk_begin, nchunks_total, Z.counts, Z.cstat, Z.counters + 2,
+                           Z.okey, Z.oval, out_total, s),
        "compaction");
-    ctx->launches += nchunks_total > 0 ? 4 : 1;
+    ctx->launches += nchunks_total == 0 ? 1 : (nchunks_total <= 1024 ? 2 : 4);
     mark(ctx, s, "compact");
     if (ctx->replay) {
       // counts and positions of the prepared run (the replayed compaction
@@ -603,8 +604,15 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       for (int q = 0; q < nlive; ++q) hl2[q] = plans[live_ids[q]].p;
     } else {
       ck(ctx, cudaMemcpyAsync(hl2, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
+      int64_t* herr = hb2.take<int64_t>(1);
+      ck(ctx, cudaMemcpyAsync(herr, Z.counters + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "download");
       ck(ctx, cudaStreamSynchronize(s), "sync results");
       collect_stages(ctx);
+      if (*herr) {   // a bounded wait of the compaction gave up: no result is reliable
+        ctx->err = "compaction: a wait for a preceding chunk timed out";
+        for (int q = 0; q < nlive; ++q) res[live_ids[q]].st = KR_ERR_TIMEOUT;
+        return;
+      }
     }
     bool retry = false;
     for (int q = 0; q < nlive; ++q) {

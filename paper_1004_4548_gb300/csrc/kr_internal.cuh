@@ -253,8 +253,11 @@ cudaError_t launch_split_sample(const Prod* dprods, int prod, int nbins, int64_t
 cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
                                int nhash, int grid, cudaStream_t s);
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
+// cstat: nchunks zeroed words of scan state; sync: two zeroed int64 (a
+// ticket counter, then an error flag set when a bounded wait gave up).
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
-                           int64_t* dcounts, uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s);
+                           int64_t* dcounts, uint64_t* dcstat, int64_t* dsync, uint64_t* okey, uint64_t* oval,
+                           int64_t cap, cudaStream_t s);
 cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, cudaStream_t s);
 
 // Device-wide LSD radix sort of (key, 8-byte payload) pairs over the low

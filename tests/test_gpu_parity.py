@@ -303,3 +303,13 @@ def test_peak_probes_report_rates(kron):
     rsplit = kron.kr_probe_smem_accumulate_rate(0, 2)
     assert r64 > 1e10 and rsplit > 1e10
     assert rsplit > 0.8 * r64
+
+
+def test_bounded_wait_gives_up_and_reports(kron):
+    """A look-back wait on a chunk that never publishes ends by itself with
+    KR_ERR_TIMEOUT, and the device stays usable for the next product."""
+    assert kron.kr_selftest_bounded_wait(0) == kron.KR_ERR_TIMEOUT
+    f, g = workload_cfg1()
+    r = oracle.poly_mul(f, g)
+    ex, cf = run_poly(kron, f, g)
+    assert_poly_equal(ex, cf, r, "after the self-test")
