@@ -33,6 +33,11 @@ struct kr_ctx {
   // replay (prepared batches): run the device work of the saved plans again,
   // without host planning or synchronisation, so that it can be captured
   bool replay = false;
+  // deferred counts: a single product whose caller decodes into device memory
+  // may skip the synchronisations after phases B1 and B2 when nothing on the
+  // host depends on them (no hash table to size or regrow); its term count
+  // then stays on the device until the decode (ProdResult::n = -1)
+  bool allow_deferred = false;
   // split histogram (kron_split_hist): the pipeline stops after phase B1 and
   // samples the keys of product 0 into split_hist (host) instead
   int32_t split_nbins = 0;
@@ -48,7 +53,8 @@ struct kr_ctx {
   Prod* res_dprod = nullptr;   // device copy of res_prod (in the work arena)
   const uint64_t* res_key = nullptr;
   const uint64_t* res_val = nullptr;
-  int64_t res_n = 0;
+  int64_t res_n = 0;                    // -1 until a deferred count is read
+  const int64_t* res_err = nullptr;     // deferred: the compaction's wait error word
   // stage timing (CUDA events on the call's stream) and launch counting
   bool profile = false;
   std::vector<cudaEvent_t> ev;
@@ -163,11 +169,12 @@ kr_status status_to_kr(uint32_t st) {
 // Result of one product of a pipeline run.
 struct ProdResult {
   kr_status st = KR_OK;
-  int64_t n = 0;
+  int64_t n = 0;               // -1: the count is on the device (dprod->nout, dprod->status)
   const uint64_t* key = nullptr;
   const uint64_t* val = nullptr;
   Prod prod{};
   Prod* dprod = nullptr;
+  const int64_t* err = nullptr;   // deferred: the compaction's wait error word (device)
 };
 
 // Host input of one product before staging (pointers may be host or device).
@@ -268,8 +275,9 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       hops[2 * p] = OpRef{p, 0};
       hops[2 * p + 1] = OpRef{p, 1};
     }
-    ck(ctx, cudaMemcpyAsync(dprods, hprods, sizeof(Prod) * nprod, cudaMemcpyHostToDevice, s), "upload");
-    ck(ctx, cudaMemcpyAsync(dops, hops, sizeof(OpRef) * nops, cudaMemcpyHostToDevice, s), "upload");
+    // products and operand list, laid out alike on both sides: one copy
+    ck(ctx, cudaMemcpyAsync(dprods, hprods, (size_t)((char*)(dops + nops) - (char*)dprods),
+                            cudaMemcpyHostToDevice, s), "upload");
     mark(ctx, s, "begin");
     ck(ctx, launch_range_scan(dprods, dops, nops, max_n, drs, dranges, s), "range scan");
     ctx->launches += 2;
@@ -326,20 +334,22 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   struct B1 {
     Prod* lprods; OpRef* oplists; int32_t* dense_ids; int64_t* block_begin; int32_t* hash_ids;
     int64_t* task_begin; int64_t* scan; DenseTask* tasks; uint32_t* hll; size_t hll_bytes;
-    int32_t* hll_ids; int64_t* hll_task_begin; unsigned long long* split;
+    int32_t* hll_ids; int64_t* hll_task_begin; unsigned long long* split; char* up_end;
   } A{};
   for (int pass = 0; pass < 2; ++pass) {
     Bump b(pass ? ctx->work : nullptr);
+    // the arrays uploaded from the host first and contiguous: one copy
     A.lprods = b.take<Prod>(nlive);
     A.oplists = b.take<OpRef>(3 * (int64_t)nops);
     A.dense_ids = b.take<int32_t>((int64_t)dense_ids.size() + 1);
     A.block_begin = b.take<int64_t>((int64_t)dense_ids.size() + 1);
     A.hash_ids = b.take<int32_t>((int64_t)hash_ids.size() + 1);
     A.task_begin = b.take<int64_t>((int64_t)hash_ids.size() + 1);
-    A.scan = b.take<int64_t>(scan_b1 + 1);
-    A.tasks = b.take<DenseTask>(dense_tasks_total);
     A.hll_ids = b.take<int32_t>((int64_t)hll_ids.size() + 1);
     A.hll_task_begin = b.take<int64_t>((int64_t)hll_ids.size() + 1);
+    A.up_end = b.base ? b.base + b.off : nullptr;
+    A.scan = b.take<int64_t>(scan_b1 + 1);
+    A.tasks = b.take<DenseTask>(dense_tasks_total);
     A.hll = b.take<uint32_t>((int64_t)hll_ids.size() * HLL_M);
     A.hll_bytes = sizeof(uint32_t) * hll_ids.size() * HLL_M;
     A.split = ctx->split_hist ? b.take<unsigned long long>(ctx->split_nbins) : nullptr;
@@ -397,25 +407,31 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   std::vector<OpRef> lists = all;
   lists.insert(lists.end(), bm.begin(), bm.end());
   lists.insert(lists.end(), bt.begin(), bt.end());
-  ensure_pinned(ctx, sizeof(Prod) * (size_t)(nlive + 1) * 2 + sizeof(OpRef) * lists.size() +
-                         16 * (h_block_begin.size() + h_task_begin.size() + 4 * (size_t)nlive) + 65536, s);
+  ensure_pinned(ctx, sizeof(Prod) * (size_t)(nlive + 1) * 3 + sizeof(OpRef) * lists.size() +
+                         16 * (h_block_begin.size() + h_task_begin.size() + 4 * (size_t)nlive) +
+                         (size_t)(A.up_end - (char*)A.lprods) + 65536, s);
   Bump hb(ctx->pinned);
-  Prod* hl = hb.take<Prod>(nlive);
-  auto up = [&](void* dst, const void* src, size_t bytes) {
-    if (bytes == 0) return;
-    void* st = hb.take<char>((int64_t)bytes);
-    memcpy(st, src, bytes);
-    ck(ctx, cudaMemcpyAsync(dst, st, bytes, cudaMemcpyHostToDevice, s), "upload plan");
-  };
-  for (int q = 0; q < nlive; ++q) hl[q] = plans[live_ids[q]].p;
-  ck(ctx, cudaMemcpyAsync(A.lprods, hl, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
-  up(A.oplists, lists.data(), sizeof(OpRef) * lists.size());
-  up(A.dense_ids, h_dense_local.data(), 4 * h_dense_local.size());
-  up(A.block_begin, h_block_begin.data(), 8 * h_block_begin.size());
-  up(A.hash_ids, h_hash_local.data(), 4 * h_hash_local.size());
-  up(A.task_begin, h_task_begin.data(), 8 * h_task_begin.size());
-  up(A.hll_ids, h_hll_local.data(), 4 * h_hll_local.size());
-  up(A.hll_task_begin, h_hll_task_begin.data(), 8 * h_hll_task_begin.size());
+  Prod* hl = hb.take<Prod>(nlive);   // download area for phase B1's results
+  {
+    // the plan and every list, laid out in pinned memory as on the device,
+    // then one copy (a handful of small copies cost more host time than data)
+    char* dbase = (char*)A.lprods;
+    const size_t span = (size_t)(A.up_end - dbase);
+    char* st = hb.take<char>((int64_t)span);
+    auto put = [&](const void* dst, const void* src, size_t bytes) {
+      if (bytes) memcpy(st + ((const char*)dst - dbase), src, bytes);
+    };
+    for (int q = 0; q < nlive; ++q) hl[q] = plans[live_ids[q]].p;
+    put(A.lprods, hl, sizeof(Prod) * nlive);
+    put(A.oplists, lists.data(), sizeof(OpRef) * lists.size());
+    put(A.dense_ids, h_dense_local.data(), 4 * h_dense_local.size());
+    put(A.block_begin, h_block_begin.data(), 8 * h_block_begin.size());
+    put(A.hash_ids, h_hash_local.data(), 4 * h_hash_local.size());
+    put(A.task_begin, h_task_begin.data(), 8 * h_task_begin.size());
+    put(A.hll_ids, h_hll_local.data(), 4 * h_hll_local.size());
+    put(A.hll_task_begin, h_hll_task_begin.data(), 8 * h_hll_task_begin.size());
+    ck(ctx, cudaMemcpyAsync(dbase, st, span, cudaMemcpyHostToDevice, s), "upload plan");
+  }
   const OpRef* d_all = A.oplists;
   const OpRef* d_bm = d_all + all.size();
   const OpRef* d_bt = d_bm + bm.size();
@@ -480,7 +496,11 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       mark(ctx, s, "hll");
     }
   }
-  if (!ctx->replay) {
+  // deferred: one product, no hash table (nothing to size from the estimate or
+  // to regrow), not a prepared or split run
+  const bool deferred = ctx->allow_deferred && !ctx->replay && !ctx->split_hist && nlive == 1 &&
+                        nprod == 1 && hll_ids.empty();
+  if (!ctx->replay && !deferred) {
     ck(ctx, cudaMemcpyAsync(hl, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
     ck(ctx, cudaStreamSynchronize(s), "sync b1");
     collect_stages(ctx);
@@ -533,11 +553,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     h_chunk_begin[nlive] = nchunks_total;
     struct B2 {
       int64_t* chunk_begin; int64_t* counts; int64_t* scan; int64_t* bins; uint64_t *okey, *oval, *okey2, *oval2;
-      int64_t* counters; uint64_t* cstat; char* zero; size_t zero_bytes;
+      int64_t* counters; uint64_t* cstat; Prod* stage; char* zero; size_t zero_bytes;
     } Z{};
     for (int pass = 0; pass < 2; ++pass) {
       Bump b(pass ? ctx->acc : nullptr);
       Z.chunk_begin = b.take<int64_t>(nlive + 1);
+      Z.stage = b.take<Prod>(nlive);
       Z.counts = b.take<int64_t>(nchunks_total + 1);
       Z.scan = b.take<int64_t>(scan_b2 + 1);
       Z.bins = b.take<int64_t>(bins_total);
@@ -561,10 +582,18 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     }
     // a replay is captured without synchronisation: its B2 staging must not
     // overwrite B1's, so it continues after it
-    Bump hb2 = ctx->replay ? hb : Bump(ctx->pinned);
+    Bump hb2 = (ctx->replay || deferred) ? hb : Bump(ctx->pinned);
     Prod* hl2 = hb2.take<Prod>(nlive);
     for (int q = 0; q < nlive; ++q) hl2[q] = plans[live_ids[q]].p;
-    ck(ctx, cudaMemcpyAsync(A.lprods, hl2, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
+    if (deferred) {
+      // phase B1's status and kept-term counts are still on the device only:
+      // upload the new plan beside it and merge, keeping those
+      ck(ctx, cudaMemcpyAsync(Z.stage, hl2, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
+      ck(ctx, launch_merge_plan(A.lprods, Z.stage, nlive, s), "merge plan");
+      ctx->launches += 1;
+    } else {
+      ck(ctx, cudaMemcpyAsync(A.lprods, hl2, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
+    }
     {
       int64_t* st = hb2.take<int64_t>(nlive + 1);
       memcpy(st, h_chunk_begin.data(), 8 * (size_t)(nlive + 1));
@@ -598,6 +627,19 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
        "compaction");
     ctx->launches += nchunks_total == 0 ? 1 : (nchunks_total <= 1024 ? 2 : 4);
     mark(ctx, s, "compact");
+    if (deferred) {
+      // the count, the status and the position (0: the only product) stay on
+      // the device; the decode reads them there
+      const int p = live_ids[0];
+      res[p].st = KR_OK;
+      res[p].n = -1;
+      res[p].prod = plans[p].p;
+      res[p].dprod = A.lprods;
+      res[p].key = Z.okey;
+      res[p].val = Z.oval;
+      res[p].err = Z.counters + 3;
+      return;
+    }
     if (ctx->replay) {
       // counts and positions of the prepared run (the replayed compaction
       // writes the same ones; the caller verifies after the launch)
@@ -718,6 +760,8 @@ void copy_out(kr_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_
   ck(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s), "copy output");
 }
 
+kr_status settle_deferred(kr_ctx* ctx, cudaStream_t s);
+
 kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
   const Prod& P = ctx->res_prod;
   const int64_t n = ctx->res_n;
@@ -730,6 +774,19 @@ kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
   if (P.graded) {   // a truncated product: the range of the variable itself
     h->omin[P.gvar] = P.gvar_min;
     h->omax[P.gvar] = P.gvar_max;
+  }
+  if (n < 0) {
+    // deferred count (device outputs only): decode up to the capacity, read
+    // the count, then report it
+    ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->capacity, h->codes, s,
+                               true, ctx->res_val, (uint64_t*)h->coef),
+       "decode");
+    ctx->launches += 1;
+    mark(ctx, s, "decode");
+    const kr_status st = settle_deferred(ctx, s);
+    h->nterms = st == KR_OK ? ctx->res_n : 0;
+    if (st != KR_OK) return st;
+    return ctx->res_n > h->capacity ? KR_ERR_CAPACITY : KR_OK;
   }
   if (n > h->capacity) return KR_ERR_CAPACITY;
   if (n == 0) return KR_OK;
@@ -768,6 +825,18 @@ kr_status emit_pseries(kr_ctx* ctx, kr_pseries_out* h, cudaStream_t s) {
   const Prod& P = ctx->res_prod;
   const int64_t n = ctx->res_n;
   h->nterms = n;
+  if (n < 0) {
+    // deferred count (device outputs only), as in emit_poly
+    ck(ctx, launch_decode_pseries(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->trig, h->kind,
+                                  h->capacity, h->codes, s, true, ctx->res_val, (uint64_t*)h->coef),
+       "decode");
+    ctx->launches += 1;
+    mark(ctx, s, "decode");
+    const kr_status st = settle_deferred(ctx, s);
+    h->nterms = st == KR_OK ? ctx->res_n : 0;
+    if (st != KR_OK) return st;
+    return ctx->res_n > h->capacity ? KR_ERR_CAPACITY : KR_OK;
+  }
   if (n > h->capacity) return KR_ERR_CAPACITY;
   if (n == 0) return KR_OK;
   const bool any_host = (h->exps && !is_device_ptr(h->exps)) || (h->trig && !is_device_ptr(h->trig)) ||
@@ -811,6 +880,31 @@ void keep_result(kr_ctx* ctx, const ProdResult& r, bool poisson) {
   ctx->res_key = r.key;
   ctx->res_val = r.val;
   ctx->res_n = r.n;
+  ctx->res_err = r.err;
+}
+
+// After a deferred run: the device-side count, status and wait error of the
+// kept product, read once its decode has been queued.  Synchronises.
+kr_status settle_deferred(kr_ctx* ctx, cudaStream_t s) {
+  ensure_pinned(ctx, 4096, s);
+  Bump hp(ctx->pinned);
+  Prod* hp_prod = hp.take<Prod>(1);
+  int64_t* herr = hp.take<int64_t>(1);
+  ck(ctx, cudaMemcpyAsync(hp_prod, ctx->res_dprod, sizeof(Prod), cudaMemcpyDeviceToHost, s), "download");
+  ck(ctx, cudaMemcpyAsync(herr, ctx->res_err, sizeof(int64_t), cudaMemcpyDeviceToHost, s), "download");
+  ck(ctx, cudaStreamSynchronize(s), "sync output");
+  collect_stages(ctx);
+  if (*herr) {
+    ctx->err = "compaction: a wait for a preceding chunk timed out";
+    ctx->has_result = false;
+    return KR_ERR_TIMEOUT;
+  }
+  if (hp_prod->status) {
+    ctx->has_result = false;
+    return status_to_kr(hp_prod->status);
+  }
+  ctx->res_n = hp_prod->nout;
+  return KR_OK;
 }
 
 }  // namespace
@@ -1035,7 +1129,16 @@ kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out*
     in.ge = g->exps; in.gc = g->coef; in.ng = g->nterms;
     if (opts) in.opts = *opts;
     std::vector<ProdResult> res;
-    run_pipeline(ctx, {in}, s, res);
+    // device outputs: the term count may stay on the device until the decode
+    ctx->allow_deferred = is_device_ptr(h->coef) && (!h->exps || is_device_ptr(h->exps)) &&
+                          (!h->codes || is_device_ptr(h->codes));
+    try {
+      run_pipeline(ctx, {in}, s, res);
+    } catch (...) {
+      ctx->allow_deferred = false;
+      throw;
+    }
+    ctx->allow_deferred = false;
     if (res[0].st != KR_OK) return res[0].st;
     keep_result(ctx, res[0], false);
     return emit_poly(ctx, h, s);
@@ -1074,7 +1177,16 @@ kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g, kr_
     in.ge = g->exps; in.gt = g->trig; in.gk = g->kind; in.gc = g->coef; in.ng = g->nterms;
     if (opts) in.opts = *opts;
     std::vector<ProdResult> res;
-    run_pipeline(ctx, {in}, s, res);
+    ctx->allow_deferred = is_device_ptr(h->coef) && (!h->exps || is_device_ptr(h->exps)) &&
+                          (!h->trig || is_device_ptr(h->trig)) && (!h->kind || is_device_ptr(h->kind)) &&
+                          (!h->codes || is_device_ptr(h->codes));
+    try {
+      run_pipeline(ctx, {in}, s, res);
+    } catch (...) {
+      ctx->allow_deferred = false;
+      throw;
+    }
+    ctx->allow_deferred = false;
     if (res[0].st != KR_OK) return res[0].st;
     keep_result(ctx, res[0], true);
     return emit_pseries(ctx, h, s);

@@ -291,25 +291,34 @@ cudaError_t launch_gather(Prod* dprods, const OpRef* dops, int nops, cudaStream_
 // ---------------------------------------------------------------------------
 // decoding of output keys (inverse of the coding: mixed-radix digits)
 // ---------------------------------------------------------------------------
+// n: terms to decode; with dev_count, at most n of the product's device-side
+// count (Prod::nout, 0 for a failed product).  vals/coef: when coef is given,
+// the coefficients are copied too.
 __global__ void __launch_bounds__(256) k_decode_poly(const Prod* __restrict__ prods, int prod,
                                                      const uint64_t* __restrict__ okey, int64_t n,
                                                      int32_t* __restrict__ exps, int64_t ld,
-                                                     int64_t* __restrict__ codes) {
+                                                     int64_t* __restrict__ codes, int dev_count,
+                                                     const uint64_t* __restrict__ vals,
+                                                     uint64_t* __restrict__ coef) {
   const Prod& P = prods[prod];
+  if (dev_count) n = P.status ? 0 : min(n, P.nout);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t code = (int64_t)okey[q] + P.klo;   // keys are relative to the key window
     if (codes) codes[q] = code;
     if (exps) decode_poly_part(P, code, exps, ld, q);
+    if (coef) coef[q] = vals[q];
   }
 }
 
 cudaError_t launch_decode_poly(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
-                               int32_t* exps, int64_t ld, int64_t* codes, cudaStream_t s) {
+                               int32_t* exps, int64_t ld, int64_t* codes, cudaStream_t s,
+                               bool dev_count, const uint64_t* vals, uint64_t* coef) {
   if (n > 0) {
     int64_t grid = (n + 255) / 256;
     if (grid > 152 * 16) grid = 152 * 16;
-    k_decode_poly<<<(unsigned)grid, 256, 0, s>>>(dprods, prod, okey, n, exps, ld, codes);
+    k_decode_poly<<<(unsigned)grid, 256, 0, s>>>(dprods, prod, okey, n, exps, ld, codes, dev_count ? 1 : 0,
+                                                 vals, coef);
   }
   return cudaGetLastError();
 }
@@ -319,14 +328,18 @@ __global__ void __launch_bounds__(256) k_decode_pseries(const Prod* __restrict__
                                                         int32_t* __restrict__ exps,
                                                         int32_t* __restrict__ trig,
                                                         uint8_t* __restrict__ kind, int64_t ld,
-                                                        int64_t* __restrict__ codes) {
+                                                        int64_t* __restrict__ codes, int dev_count,
+                                                        const uint64_t* __restrict__ vals,
+                                                        uint64_t* __restrict__ coef) {
   const Prod& P = prods[prod];
+  if (dev_count) n = P.status ? 0 : min(n, P.nout);
   const int64_t per_kind = P.T2 * P.Wp;
   const int64_t half = P.T2 - 1;   // sum_k c_k R_k
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t key = (int64_t)okey[q] + P.klo;   // keys are relative to the key window
     if (codes) codes[q] = key;
+    if (coef) coef[q] = vals[q];
     const int64_t kd = key >= per_kind ? 1 : 0;   // keys lie below 2 * per_kind
     int64_t pc;
     const int64_t T = divmod_nn(key - kd * per_kind, P.Wp, &pc);
@@ -345,13 +358,33 @@ __global__ void __launch_bounds__(256) k_decode_pseries(const Prod* __restrict__
 
 cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
                                   int32_t* exps, int32_t* trig, uint8_t* kind, int64_t ld,
-                                  int64_t* codes, cudaStream_t s) {
+                                  int64_t* codes, cudaStream_t s, bool dev_count, const uint64_t* vals,
+                                  uint64_t* coef) {
   if (n > 0) {
     int64_t grid = (n + 255) / 256;
     if (grid > 152 * 16) grid = 152 * 16;
     k_decode_pseries<<<(unsigned)grid, 256, 0, s>>>(dprods, prod, okey, n, exps, trig, kind, ld,
-                                                    codes);
+                                                    codes, dev_count ? 1 : 0, vals, coef);
   }
+  return cudaGetLastError();
+}
+
+// A new plan for products whose phase-B1 results are still on the device
+// only: dst = src, keeping dst's status and kept-term counts.
+__global__ void k_merge_plan(Prod* __restrict__ dst, const Prod* __restrict__ src, int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const uint32_t st = dst[q].status;
+  const int64_t fk = dst[q].f.nkeep, gk = dst[q].g.nkeep;
+  Prod p = src[q];
+  p.status = st;
+  p.f.nkeep = fk;
+  p.g.nkeep = gk;
+  dst[q] = p;
+}
+
+cudaError_t launch_merge_plan(Prod* dst, const Prod* src, int n, cudaStream_t s) {
+  if (n > 0) k_merge_plan<<<(n + 63) / 64, 64, 0, s>>>(dst, src, n);
   return cudaGetLastError();
 }
 

@@ -284,11 +284,19 @@ cudaError_t order_by_bitmap(const uint64_t* key, const uint64_t* val, uint64_t* 
 cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
                           int64_t krange, int64_t* bins, cudaStream_t s);
 
+// Decode of one product's sorted terms.  With dev_count, n is a capacity and
+// the count is the product's device-side nout (0 when its status is set);
+// given coef, the coefficients (vals) are copied too.
 cudaError_t launch_decode_poly(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
-                               int32_t* exps, int64_t ld, int64_t* codes, cudaStream_t s);
+                               int32_t* exps, int64_t ld, int64_t* codes, cudaStream_t s,
+                               bool dev_count = false, const uint64_t* vals = nullptr,
+                               uint64_t* coef = nullptr);
 cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* okey, int64_t n,
                                   int32_t* exps, int32_t* trig, uint8_t* kind, int64_t ld,
-                                  int64_t* codes, cudaStream_t s);
+                                  int64_t* codes, cudaStream_t s, bool dev_count = false,
+                                  const uint64_t* vals = nullptr, uint64_t* coef = nullptr);
+// dst[q] = src[q] keeping dst[q]'s status and kept-term counts
+cudaError_t launch_merge_plan(Prod* dst, const Prod* src, int n, cudaStream_t s);
 // Where a batched decode writes one product's terms ([nvars][n] layouts).
 struct ResDesc {
   int32_t* exps;
