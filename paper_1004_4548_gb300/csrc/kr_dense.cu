@@ -202,6 +202,12 @@ struct ChunkTable {
 // every term of a tile, so the window search, the g loads and the walk
 // bookkeeping are paid once per TILE_R term-products.  The tile's g-window is
 // the union of its terms' windows, at most S / 8 codes wider than one.
+#ifndef KR_FULL_TILE_FAST
+#define KR_FULL_TILE_FAST 1
+#endif
+#ifndef KR_ACC_MIN_BLOCKS
+#define KR_ACC_MIN_BLOCKS 3
+#endif
 #ifndef KR_TILE_R
 #define KR_TILE_R 8
 #endif
@@ -318,6 +324,20 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
         const T cg = CG[j];
         const int rk = ct.run[k];
         const T* __restrict__ cf = CF + (ib + k);
+#if KR_FULL_TILE_FAST
+        if (rk == TILE_R) {   // the common case: a full tile, the loop fully unrolled
+#pragma unroll
+          for (int a = 0; a < TILE_R; ++a) {
+            const int2 e = ct.fc[k + a];
+            const int32_t off = e.x + gc;
+            if ((uint32_t)off < (uint32_t)S) {
+              if constexpr (C32) acc.add(off, (T)((int64_t)e.y * (int64_t)(int32_t)cg));
+              else acc.add(off, mul<T, C32>(cf[a], cg));
+            }
+          }
+          continue;
+        }
+#endif
 #pragma unroll 4
         for (int a = 0; a < rk; ++a) {
           const int2 e = ct.fc[k + a];
@@ -348,7 +368,7 @@ __device__ __forceinline__ void dense_flush(const Prod& P, const DenseTask& tk, 
   }
 }
 
-__global__ void __launch_bounds__(ACC_THREADS, 3) k_dense_accum(const Prod* __restrict__ prods,
+__global__ void __launch_bounds__(ACC_THREADS, KR_ACC_MIN_BLOCKS) k_dense_accum(const Prod* __restrict__ prods,
                                                              const DenseTask* __restrict__ tasks,
                                                              const int64_t* __restrict__ task_count,
                                                              int64_t task_cap,
