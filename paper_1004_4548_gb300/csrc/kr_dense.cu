@@ -165,13 +165,13 @@ template <>
 struct Slice<int64_t> {
   uint32_t* lo;
   uint32_t* hi;
-  __device__ __forceinline__ Slice(void* base, int64_t S) : lo((uint32_t*)base), hi((uint32_t*)base + S) {}
+  uint32_t lo_sh;    // shared-memory address of the low words
+  uint32_t hi_dist;  // bytes from a low word to its high word (4 S)
+  __device__ __forceinline__ Slice(void* base, int64_t S)
+      : lo((uint32_t*)base), hi((uint32_t*)base + S), lo_sh((uint32_t)__cvta_generic_to_shared(base)),
+        hi_dist((uint32_t)(4 * S)) {}
   __device__ __forceinline__ void add(int32_t off, int64_t v) const {
-    const uint64_t u = (uint64_t)v;
-    const uint32_t l = (uint32_t)u;
-    const uint32_t old = atomicAdd(&lo[off], l);
-    const uint32_t h = (uint32_t)(u >> 32) + ((uint32_t)(old + l) < old ? 1u : 0u);
-    if (h) atomicAdd(&hi[off], h);
+    smem_acc_split64(lo_sh + (uint32_t)off * 4u, hi_dist, (uint64_t)v);
   }
   __device__ __forceinline__ int64_t get(int64_t s) const {
     return (int64_t)(((uint64_t)hi[s] << 32) | (uint64_t)lo[s]);

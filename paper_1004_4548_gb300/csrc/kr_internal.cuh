@@ -200,6 +200,20 @@ __device__ __forceinline__ void decode_poly_part(const Prod& P, int64_t pc, int3
   exps[(int64_t)P.gvar * ld + q] = (int32_t)(pc + P.omin[P.gvar] - deg_rest);
 }
 
+// int64 accumulate into shared memory as two 32-bit words (the low word at
+// shared address a, the high word hi_dist bytes further): a 32-bit atomic add
+// of the low half returning the old value, its carry by add-with-carry, and a
+// 32-bit add of high half and carry when nonzero.  Exact modulo 2^64 whatever
+// the order of the adds: each carry is seen by exactly the add that makes it.
+__device__ __forceinline__ void smem_acc_split64(uint32_t a, uint32_t hi_dist, uint64_t u) {
+  const uint32_t l = (uint32_t)u;
+  uint32_t old, h;
+  asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(l) : "memory");
+  asm("{\n\t.reg .u32 t;\n\tadd.cc.u32 t, %1, %2;\n\taddc.u32 %0, %3, 0;\n\t}"
+      : "=r"(h) : "r"(old), "r"(l), "r"((uint32_t)(u >> 32)));
+  if (h) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a + hi_dist), "r"(h) : "memory");
+}
+
 // 64-bit mixing function (the finaliser of MurmurHash3, Appleby) for table slots
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   k ^= k >> 33;

@@ -60,14 +60,11 @@ __global__ void __launch_bounds__(PK_THREADS) k_probe_smem_split64(int64_t* __re
   __shared__ uint32_t s[2 * PK_SLOTS];
   for (int i = threadIdx.x; i < 2 * PK_SLOTS; i += blockDim.x) s[i] = 0;
   __syncthreads();
-  const uint64_t u = (uint64_t)inc;
-  const uint32_t l = (uint32_t)u, h0 = (uint32_t)(u >> 32);
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(s);
   int a = threadIdx.x;
 #pragma unroll 16
   for (int it = 0; it < PK_ITERS; ++it) {
-    const uint32_t old = atomicAdd(&s[a], l);
-    const uint32_t h = h0 + ((uint32_t)(old + l) < old ? 1u : 0u);
-    if (h) atomicAdd(&s[PK_SLOTS + a], h);
+    smem_acc_split64(base + 4u * (uint32_t)a, 4u * PK_SLOTS, (uint64_t)inc);
     a = (a + PK_THREADS) & (PK_SLOTS - 1);
   }
   __syncthreads();
