@@ -616,10 +616,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       mark(ctx, s, "dense_accum");
     }
     if (!hash_ids.empty()) {
-      ck(ctx, launch_hash_insert(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(),
-                                 ctx->num_sms * 8, s),
+      bool any_poly = false, any_pseries = false;
+      for (int p : hash_ids) (plans[p].p.nt > 0 ? any_pseries : any_poly) = true;
+      ck(ctx, launch_hash_insert(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(), any_poly,
+                                 any_pseries, ctx->num_sms * 8, s),
          "hash insert");
-      ctx->launches += 1;
+      ctx->launches += (any_poly ? 1 : 0) + (any_pseries ? 1 : 0);
       mark(ctx, s, "hash_insert");
     }
     ck(ctx, launch_compact(A.lprods, nlive, Z.chunk_begin, nchunks_total, Z.counts, Z.cstat, Z.counters + 2,

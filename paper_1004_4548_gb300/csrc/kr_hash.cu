@@ -471,30 +471,49 @@ cudaError_t launch_hll_estimate(Prod* dprods, const int32_t* dhash_prods, int nh
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(HASH_THREADS, 3) k_hash_insert(Prod* __restrict__ prods,
-                                                              const int32_t* __restrict__ hash_prods,
-                                                              const int64_t* __restrict__ task_begin,
-                                                              int nhash) {
+// Two kernels over the same task list, each skipping the other kind's
+// products: polynomial tiles need fewer registers than the Poisson tiles, so
+// their kernel keeps more warps, and thus more inserts, in flight per SM.
+#ifndef KR_HASH_POLY_MIN_BLOCKS
+#define KR_HASH_POLY_MIN_BLOCKS 4
+#endif
+
+__global__ void __launch_bounds__(HASH_THREADS, KR_HASH_POLY_MIN_BLOCKS)
+    k_hash_insert_poly(Prod* __restrict__ prods, const int32_t* __restrict__ hash_prods,
+                       const int64_t* __restrict__ task_begin, int nhash) {
   const int64_t ntasks = task_begin[nhash];
   for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x) {
     const HashTile h = find_tile(prods, hash_prods, task_begin, nhash, t);
     Prod& P = prods[h.pid];
+    if (P.nt > 0) continue;
     if (*(volatile uint32_t*)&P.status) continue;   // failed product: skip its remaining tiles
-    bool ok;
-    if (P.nt > 0) {
-      if (P.path == PATH_DENSE) { pseries_dense_tile(P, h); ok = true; }
-      else ok = pseries_tile(P, h);
-    }
-    else if (P.f64) ok = poly_tile<double>(P, h);
-    else ok = poly_tile<int64_t>(P, h);
+    const bool ok = P.f64 ? poly_tile<double>(P, h) : poly_tile<int64_t>(P, h);
+    if (!ok) atomicOr(&P.status, ST_TABLE_FULL);
+  }
+}
+
+__global__ void __launch_bounds__(HASH_THREADS, 3) k_hash_insert_pseries(Prod* __restrict__ prods,
+                                                                      const int32_t* __restrict__ hash_prods,
+                                                                      const int64_t* __restrict__ task_begin,
+                                                                      int nhash) {
+  const int64_t ntasks = task_begin[nhash];
+  for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x) {
+    const HashTile h = find_tile(prods, hash_prods, task_begin, nhash, t);
+    Prod& P = prods[h.pid];
+    if (P.nt == 0) continue;
+    if (*(volatile uint32_t*)&P.status) continue;
+    bool ok = true;
+    if (P.path == PATH_DENSE) pseries_dense_tile(P, h);
+    else ok = pseries_tile(P, h);
     if (!ok) atomicOr(&P.status, ST_TABLE_FULL);
   }
 }
 
 cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
-                               int nhash, int grid, cudaStream_t s) {
+                               int nhash, bool poly, bool pseries, int grid, cudaStream_t s) {
   if (nhash <= 0) return cudaSuccess;
-  k_hash_insert<<<grid, HASH_THREADS, 0, s>>>(dprods, dhash_prods, dtask_begin, nhash);
+  if (poly) k_hash_insert_poly<<<grid, HASH_THREADS, 0, s>>>(dprods, dhash_prods, dtask_begin, nhash);
+  if (pseries) k_hash_insert_pseries<<<grid, HASH_THREADS, 0, s>>>(dprods, dhash_prods, dtask_begin, nhash);
   return cudaGetLastError();
 }
 

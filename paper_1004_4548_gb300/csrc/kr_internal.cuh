@@ -264,8 +264,10 @@ cudaError_t launch_hll_estimate(Prod* dprods, const int32_t* dhash_prods, int nh
 // product over nbins equal slices of [0, krange) (hist zeroed by the caller).
 cudaError_t launch_split_sample(const Prod* dprods, int prod, int nbins, int64_t nsamples, uint64_t seed,
                                 unsigned long long* dhist, cudaStream_t s);
+// accumulation of every hash-path product's tiles (and Poisson tiles on the
+// dense path): poly / pseries say which kinds the list holds
 cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
-                               int nhash, int grid, cudaStream_t s);
+                               int nhash, bool poly, bool pseries, int grid, cudaStream_t s);
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
 // cstat: nchunks zeroed words of scan state; sync: two zeroed int64 (a
 // ticket counter, then an error flag set when a bounded wait gave up).
