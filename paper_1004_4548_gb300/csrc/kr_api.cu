@@ -537,7 +537,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       const int64_t nb = order_bins(pl.p.kspan);
       if (pl.p.kspan <= ORDER_BITMAP_MAX)
         bins_total = std::max(bins_total, (order_bitmap_bytes(pl.p.kspan) + 7) / 8);
-      else if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, 2 * (nb + 1));
+      else if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, order_bins_scratch(pl.p.kspan));
       else scan_b2 = std::max(scan_b2, radix_scan_entries(pl.out_cap));
     }
     std::vector<int64_t> h_chunk_begin(nlive + 1, 0);
@@ -560,7 +560,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Z.chunk_begin = b.take<int64_t>(nlive + 1);
       Z.stage = b.take<Prod>(nlive);
       Z.counts = b.take<int64_t>(nchunks_total + 1);
-      Z.scan = b.take<int64_t>(scan_b2 + 1);
+      Z.scan = b.take<int64_t>(std::max(scan_b2, scan_scratch_entries(nchunks_total)) + 1);
       Z.bins = b.take<int64_t>(bins_total);
       Z.okey = b.take<uint64_t>(out_total);
       Z.oval = b.take<uint64_t>(out_total);
@@ -625,7 +625,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       mark(ctx, s, "hash_insert");
     }
     ck(ctx, launch_compact(A.lprods, nlive, Z.chunk_begin, nchunks_total, Z.counts, Z.cstat, Z.counters + 2,
-                           Z.okey, Z.oval, out_total, s),
+                           Z.scan, Z.okey, Z.oval, out_total, s),
        "compaction");
     ctx->launches += nchunks_total == 0 ? 1 : (nchunks_total <= 1024 ? 2 : 4);
     mark(ctx, s, "compact");

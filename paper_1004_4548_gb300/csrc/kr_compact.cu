@@ -341,8 +341,8 @@ __global__ void k_finish_counts(Prod* __restrict__ prods, int nprod,
 }
 
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
-                           int64_t* dcounts, uint64_t* dcstat, int64_t* dsync, uint64_t* okey, uint64_t* oval,
-                           int64_t cap, cudaStream_t s) {
+                           int64_t* dcounts, uint64_t* dcstat, int64_t* dsync, int64_t* dscan,
+                           uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s) {
   if (nchunks > 0) {
     // persistent grid: every CTA that fits on the GPU at once
     int dev = 0, sms = 152, per = 0;
@@ -366,7 +366,7 @@ cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin,
       const int64_t gc = std::min<int64_t>(nchunks, (int64_t)sms * std::max(pc, 1));
       const int64_t gs = std::min<int64_t>(nchunks, (int64_t)sms * std::max(ps, 1));
       k_compact_count<<<(unsigned)gc, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts);
-      cudaError_t e = launch_scan_exclusive(dcounts, nchunks, dcounts + nchunks, s);
+      cudaError_t e = launch_scan_exclusive(dcounts, nchunks, dcounts + nchunks, dscan, s);
       if (e != cudaSuccess) return e;
       k_compact_scatter<<<(unsigned)gs, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts, cap, okey,
                                                            oval);

@@ -270,11 +270,15 @@ cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const i
                                int nhash, bool poly, bool pseries, int grid, cudaStream_t s);
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
 // cstat: nchunks zeroed words of scan state; sync: two zeroed int64 (a
-// ticket counter, then an error flag set when a bounded wait gave up).
+// ticket counter, then an error flag set when a bounded wait gave up); scan:
+// scan_scratch_entries(nchunks) int64 for the two-pass form.
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
-                           int64_t* dcounts, uint64_t* dcstat, int64_t* dsync, uint64_t* okey, uint64_t* oval,
-                           int64_t cap, cudaStream_t s);
-cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, cudaStream_t s);
+                           int64_t* dcounts, uint64_t* dcstat, int64_t* dsync, int64_t* dscan,
+                           uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s);
+// exclusive scan of d[0, n) in place, *dtotal = sum; long arrays use several
+// CTAs and scratch of scan_scratch_entries(n) int64 (null: one CTA)
+int64_t scan_scratch_entries(int64_t n);
+cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, int64_t* scratch, cudaStream_t s);
 
 // Device-wide LSD radix sort of (key, 8-byte payload) pairs over the low
 // `bits` bits of the key.  key/val and key_tmp/val_tmp ping-pong; after the
@@ -291,6 +295,7 @@ cudaError_t radix_sort_pairs(uint64_t* key, uint64_t* val, uint64_t* key_tmp, ui
 // bins 2 * (order_bins(krange) + 1) int64.  Result in key/val.
 constexpr int64_t ORDER_MAX_BINS = int64_t(1) << 24;
 int64_t order_bins(int64_t krange);
+int64_t order_bins_scratch(int64_t krange);   // int64 entries of order_by_bins' scratch
 // Bitmap-rank ordering for code ranges up to ORDER_BITMAP_MAX codes: result in
 // key2/val2; scratch of order_bitmap_bytes(krange).
 constexpr int64_t ORDER_BITMAP_MAX = int64_t(1) << 35;

@@ -114,6 +114,10 @@ __global__ void __launch_bounds__(ORD_THREADS) k_seg_sort(const uint64_t* __rest
 }
 
 int64_t order_bins(int64_t krange) { return (krange + ORD_C - 1) / ORD_C; }
+int64_t order_bins_scratch(int64_t krange) {
+  const int64_t nb = order_bins(krange);
+  return 2 * (nb + 1) + scan_scratch_entries(nb);
+}
 
 // ---------------------------------------------------------------------------
 // bitmap rank ordering
@@ -128,7 +132,9 @@ static int64_t bm_sblocks(int64_t krange) { return (bm_words(krange) + BM_SB - 1
 
 int64_t order_bitmap_bytes(int64_t krange) {
   const int64_t w = bm_sblocks(krange) * BM_SB;
-  return w * 8 + w * 4 + (bm_sblocks(krange) + 1) * 8 + 3 * 256;
+  // bitmap, word prefixes, superblock prefixes (+ total), the scan's block sums
+  return w * 8 + w * 4 + (bm_sblocks(krange) + 1) * 8 + scan_scratch_entries(bm_sblocks(krange)) * 8 +
+         4 * 256;
 }
 
 __global__ void __launch_bounds__(256) k_bm_set(const uint64_t* __restrict__ key, int64_t n, int64_t krange,
@@ -206,7 +212,7 @@ cudaError_t order_by_bitmap(const uint64_t* key, const uint64_t* val, uint64_t* 
   if (grid > 152 * 16) grid = 152 * 16;
   k_bm_set<<<(unsigned)grid, 256, 0, s>>>(key, n, krange, bits);
   k_bm_prefix<<<(unsigned)nsb, BM_SB, 0, s>>>(bits, wpre, spre);
-  e = launch_scan_exclusive(spre, nsb, spre + nsb, s);
+  e = launch_scan_exclusive(spre, nsb, spre + nsb, spre + nsb + 1, s);
   if (e != cudaSuccess) return e;
   k_bm_scatter<<<(unsigned)grid, 256, 0, s>>>(key, val, n, krange, bits, wpre, spre, key2, val2);
   return cudaGetLastError();
@@ -214,7 +220,7 @@ cudaError_t order_by_bitmap(const uint64_t* key, const uint64_t* val, uint64_t* 
 
 // Sorts (key, val)[0, n) by key, keys distinct and < krange.  Uses key2/val2
 // as the binned copy and writes the sorted terms back to key/val.  bins:
-// 2 * (order_bins(krange) + 1) int64 of scratch.
+// order_bins_scratch(krange) int64 of scratch.
 cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
                           int64_t krange, int64_t* bins, cudaStream_t s) {
   if (n <= 1) return cudaSuccess;
@@ -226,7 +232,7 @@ cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t
   int64_t grid = (n + 255) / 256;
   if (grid > 152 * 16) grid = 152 * 16;
   k_bin_count<<<(unsigned)grid, 256, 0, s>>>(key, n, nb, (unsigned long long*)off);
-  e = launch_scan_exclusive(off, nb, off + nb, s);
+  e = launch_scan_exclusive(off, nb, off + nb, bins + 2 * (nb + 1), s);
   if (e != cudaSuccess) return e;
   k_bin_scatter<<<(unsigned)grid, 256, 0, s>>>(key, val, n, nb, off, cur, key2, val2);
   const int64_t nseg = (n + ORD_C - 1) / ORD_C;

@@ -62,8 +62,59 @@ __global__ void __launch_bounds__(1024) k_scan_exclusive(int64_t* __restrict__ d
   if (threadIdx.x == 0 && total) *total = tot;
 }
 
-cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, cudaStream_t s) {
-  k_scan_exclusive<<<1, 1024, 0, s>>>(d, n, dtotal);
+// ---------------------------------------------------------------------------
+// multi-CTA exclusive scan for long arrays: block sums, a scan of the sums,
+// then each block scanned with its offset.  scratch: scan_scratch_entries(n).
+// ---------------------------------------------------------------------------
+constexpr int SC_THREADS = 1024;
+constexpr int SC_ITEMS = 8;
+constexpr int64_t SC_BLOCK = (int64_t)SC_THREADS * SC_ITEMS;
+constexpr int64_t SC_ONE_CTA_MAX = 65536;
+
+int64_t scan_scratch_entries(int64_t n) { return (n + SC_BLOCK - 1) / SC_BLOCK + 1; }
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_sums(const int64_t* __restrict__ d, int64_t n,
+                                                          int64_t* __restrict__ sums) {
+  const int64_t b0 = blockIdx.x * SC_BLOCK;
+  int64_t s = 0;
+#pragma unroll
+  for (int r = 0; r < SC_ITEMS; ++r) {
+    const int64_t i = b0 + (int64_t)r * SC_THREADS + threadIdx.x;
+    if (i < n) s += d[i];
+  }
+  int64_t tot;
+  block_exclusive_scan<SC_THREADS>(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_blocks(int64_t* __restrict__ d, int64_t n,
+                                                            const int64_t* __restrict__ sums) {
+  // each thread scans SC_ITEMS consecutive values
+  const int64_t i0 = blockIdx.x * SC_BLOCK + (int64_t)threadIdx.x * SC_ITEMS;
+  int64_t v[SC_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int r = 0; r < SC_ITEMS; ++r) {
+    v[r] = i0 + r < n ? d[i0 + r] : 0;
+    s += v[r];
+  }
+  int64_t run = sums[blockIdx.x] + block_exclusive_scan<SC_THREADS>(s, nullptr);
+#pragma unroll
+  for (int r = 0; r < SC_ITEMS; ++r) {
+    if (i0 + r < n) d[i0 + r] = run;
+    run += v[r];
+  }
+}
+
+cudaError_t launch_scan_exclusive(int64_t* d, int64_t n, int64_t* dtotal, int64_t* scratch, cudaStream_t s) {
+  if (n <= SC_ONE_CTA_MAX || !scratch) {
+    k_scan_exclusive<<<1, 1024, 0, s>>>(d, n, dtotal);
+    return cudaGetLastError();
+  }
+  const int64_t nb = (n + SC_BLOCK - 1) / SC_BLOCK;
+  k_scan_sums<<<(unsigned)nb, SC_THREADS, 0, s>>>(d, n, scratch);
+  k_scan_exclusive<<<1, 1024, 0, s>>>(scratch, nb, dtotal);   // offsets of the blocks, and the total
+  k_scan_blocks<<<(unsigned)nb, SC_THREADS, 0, s>>>(d, n, scratch);
   return cudaGetLastError();
 }
 
@@ -261,7 +312,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
 }
 
 int64_t radix_scan_entries(int64_t n) {
-  return 256 * ((n + RADIX_TILE - 1) / RADIX_TILE) + 1;
+  const int64_t e = 256 * ((n + RADIX_TILE - 1) / RADIX_TILE);
+  return e + 1 + scan_scratch_entries(e);   // digit counts, their total, the scan's block sums
 }
 
 cudaError_t radix_sort_pairs(uint64_t* key, uint64_t* val, uint64_t* key_tmp, uint64_t* val_tmp,
@@ -274,7 +326,8 @@ cudaError_t radix_sort_pairs(uint64_t* key, uint64_t* val, uint64_t* key_tmp, ui
   uint64_t *ki = key, *vi = val, *ko = key_tmp, *vo = val_tmp;
   for (int shift = 0; shift < bits; shift += 8) {
     k_rs_hist<<<grid, RS_THREADS, 0, s>>>(ki, n, shift, ntiles, dscan);
-    k_scan_exclusive<<<1, 1024, 0, s>>>(dscan, 256 * ntiles, dscan + 256 * ntiles);
+    cudaError_t e = launch_scan_exclusive(dscan, 256 * ntiles, dscan + 256 * ntiles, dscan + 256 * ntiles + 1, s);
+    if (e != cudaSuccess) return e;
     k_rs_scatter<<<grid, RS_THREADS, 0, s>>>(ki, vi, n, shift, ntiles, dscan, ko, vo);
     uint64_t* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
