@@ -19,9 +19,10 @@ A batch is also capped in work (term-products): the oldest waiting request
 always starts the batch, and later requests join it only while the cap holds,
 so a small request never waits behind a very large one in the same batch
 and can overtake it on the other worker.  A request above `giant` term
-products runs in a batch of its own and no other batch starts while it runs,
-so that the largest products, which set the tail latency, share the GPU with
-at most the batch already running.  A worker releases its
+products runs in a batch of its own: it waits at the head of the queue until
+no batch is running (with giant_alone) and no other batch starts while it
+runs, so that the largest products, which set the tail latency, have the GPU
+to themselves.  A worker releases its
 context's cached scratch after a batch when it holds more than `trim_bytes`.
 A worker whose batch runs out of device memory releases its context's cached
 scratch, holds off new batches, waits until the other workers are idle and
@@ -90,10 +91,11 @@ class Server:
 
     def __init__(self, device: int = 0, workers: int = 2, mem_budget: float = 64e9,
                  max_batch: int = 256, wave_pairs: int = 0, work_cap: float = 2e8,
-                 giant: float = 5e7, trim_bytes: float = 24e9):
+                 giant: float = 5e7, trim_bytes: float = 24e9, giant_alone: bool = True):
         self.device = device
         self.work_cap = work_cap
         self.giant = giant
+        self.giant_alone = giant_alone
         self.trim_bytes = trim_bytes
         self.exclusive = False
         self.hold = 0             # workers retrying alone after running out of memory
@@ -215,9 +217,14 @@ class Server:
                     room = self.mem_budget - self.in_flight_bytes
                 batch, used, work = [], 0.0, 0.0
                 idle = all(not w.busy for w in self.workers)
+                if pending[0].pairs > self.giant and not idle and self.giant_alone:
+                    # the oldest request is very large: no new batch starts
+                    # until the GPU is free, then it runs alone
+                    time.sleep(0.0002)
+                    continue
                 if pending[0].pairs > self.giant:
                     # the oldest request is very large: it starts on the free
-                    # worker at once and no new batch starts until it is done
+                    # worker and no new batch starts until it is done
                     batch.append(pending[0])
                     used += self.predict_bytes(pending[0])
                 for r in ([] if pending[0].pairs > self.giant else pending):
