@@ -53,7 +53,7 @@
 
 namespace {
 
-constexpr int MAXK = 16;   // components per key: poly vars, or 1 + trig + poly
+constexpr int MAXK = 17;   // components per key: poly vars, or 1 + trig + poly (at most 16 variables)
 
 struct Key {
   int32_t c[MAXK];

@@ -313,3 +313,74 @@ def test_bounded_wait_gives_up_and_reports(kron):
     r = oracle.poly_mul(f, g)
     ex, cf = run_poly(kron, f, g)
     assert_poly_equal(ex, cf, r, "after the self-test")
+
+
+# ---------------------------------------------------------------------------
+# limits: the most variables, exponents near the int32 ends, code ranges near
+# 2^63, int64 wrap on the hash path
+# ---------------------------------------------------------------------------
+
+def test_sixteen_variables(kron):
+    """KR_MAXV polynomial variables (product width 3 per variable: W = 3^16)."""
+    f = random_poly(16, 900, 0, 1, 5100)
+    g = random_poly(16, 700, 0, 1, 5101)
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    for path in (kron.KR_PATH_DENSE, kron.KR_PATH_HASH):
+        ex, cf = run_poly(kron, f, g, path=path)
+        assert_poly_equal(ex, cf, r, f"16 variables path={path}")
+
+
+def test_poisson_sixteen_variables(kron):
+    f = random_pseries(6, 10, 600, 1, 1, 5200)
+    g = random_pseries(6, 10, 500, 1, 1, 5201)
+    r = oracle.poisson_mul(f, g, nthreads=NT, keep_zero=True)
+    for path in (kron.KR_PATH_AUTO, kron.KR_PATH_HASH):
+        out = run_pseries(kron, f, g, path=path)
+        assert_pseries_close(out, r, REL, f"16 poisson variables path={path}")
+
+
+def test_exponents_near_int32_ends(kron):
+    """Boxes far from the origin: the codes use offsets, the decode restores them."""
+    big = (1 << 30) - 20
+    f = random_poly(3, 400, [-big, big - 8, 0], [-big + 6, big, 9], 5300)
+    g = random_poly(3, 300, [-big, big - 8, -4], [-big + 9, big, 3], 5301)
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    assert r.exps[0].min() < -(1 << 31) + 100 and r.exps[1].max() > (1 << 31) - 100
+    for path in (kron.KR_PATH_DENSE, kron.KR_PATH_HASH):
+        ex, cf = run_poly(kron, f, g, path=path)
+        assert_poly_equal(ex, cf, r, f"int32 ends path={path}")
+    # one step further and the product's exponents leave int32
+    h = Poly(np.array([[(1 << 30) + 5]], np.int32), np.array([1], np.int64))
+    with pytest.raises(kron.KronError) as e:
+        run_poly(kron, h, h)
+    assert e.value.status == kron.KR_ERR_OVERFLOW
+
+
+def test_code_range_near_two_to_63(kron):
+    """A product whose code range is just below 2^63 (hash path), and one just above."""
+    # widths 2^21 - 1 in three variables: W = (2^21 - 1)^3 = 2^63 - 3 * 2^42 + 3 * 2^21 - 1
+    hi = (1 << 20) - 1
+    f = Poly(np.array([[0, hi, 5, 0], [0, 7, hi, 3], [0, 1, 2, hi]], np.int32), np.array([1, -2, 3, 4], np.int64))
+    g = Poly(np.array([[0, hi, 9], [0, 0, hi], [hi, 4, 0]], np.int32), np.array([5, 6, -7], np.int64))
+    r = oracle.poly_mul(f, g)
+    ex, cf = run_poly(kron, f, g)
+    assert_poly_equal(ex, cf, r, "code range near 2^63")
+    g2 = Poly(g.exps.copy(), g.coef.copy())
+    g2.exps[0, 0] = -4   # w_0 = 2^21 + 3: the range passes 2^63 - 1
+    with pytest.raises(kron.KronError) as e:
+        run_poly(kron, f, g2)
+    assert e.value.status == kron.KR_ERR_OVERFLOW
+
+
+def test_int64_wrap_on_hash_path(kron):
+    """Sums beyond int64 wrap modulo 2^64 on the hash path as on the dense path."""
+    rng = Rng(5400)
+    f = random_poly(3, 300, -2, 2, 5401)
+    g = random_poly(3, 250, -2, 2, 5402)
+    f.coef[:] = rng.ints(1 << 61, (1 << 62) - 1, f.n)
+    g.coef[:] = rng.ints(-(1 << 62), -(1 << 61), g.n)
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    assert r.overflow
+    for path in (kron.KR_PATH_DENSE, kron.KR_PATH_HASH):
+        ex, cf = run_poly(kron, f, g, path=path)
+        assert_poly_equal(ex, cf, r, f"wrap path={path}")
