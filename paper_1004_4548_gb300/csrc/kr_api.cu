@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <chrono>
+
 #include "kr_plan.h"
 
 using namespace kr;
@@ -142,6 +144,22 @@ void mark(kr_ctx* ctx, cudaStream_t s, const char* name) {
   ctx->nev++;
 }
 
+// Host time of a planning step (profiling only), reported as a stage named
+// "host_<step>" beside the device stages.
+struct HostSpan {
+  kr_ctx* ctx;
+  const char* name;
+  std::chrono::steady_clock::time_point t0;
+  HostSpan(kr_ctx* c, const char* n) : ctx(c), name(n), t0(std::chrono::steady_clock::now()) {}
+  void done() {
+    if (!ctx || !ctx->profile) return;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ctx->stage_ms.push_back(ms);
+    ctx->stage_name.push_back(name);
+    ctx = nullptr;
+  }
+};
+
 // After a synchronisation: turn the recorded marks into per-stage times.
 void collect_stages(kr_ctx* ctx) {
   if (!ctx->profile) return;
@@ -212,6 +230,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   res.assign(nprod, ProdResult());
   const int nops = 2 * nprod;
   std::vector<Job> jobs(nprod);
+  HostSpan plan_span(nullptr, "host_plan");
   // ---------------- phase A: staged inputs, metadata, range scan
   if (ctx->replay) {
     for (int p = 0; p < nprod; ++p) res[p].st = ctx->plans[p].st;
@@ -287,6 +306,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     ck(ctx, cudaStreamSynchronize(s), "sync ranges");
     collect_stages(ctx);
     // ---------------- host planning
+    plan_span = HostSpan(ctx, "host_plan");
     std::vector<Plan> plans_tmp(nprod);
     ctx->plans.assign(nprod, Plan());
     for (int p = 0; p < nprod; ++p) {
@@ -436,6 +456,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   const OpRef* d_bm = d_all + all.size();
   const OpRef* d_bt = d_bm + bm.size();
   // ---------------- phase B1 device work
+  plan_span.done();
   mark(ctx, s, "plan_upload");
   if (A.hll_bytes) ck(ctx, cudaMemsetAsync(A.hll, 0, A.hll_bytes, s), "memset hll");
   ck(ctx, launch_encode(A.lprods, d_all, (int)all.size(), s), "encode");
@@ -529,6 +550,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   // ---------------- phase B2, repeated for products whose table filled up
   std::vector<int> regrows(nprod, 0);
   for (;;) {
+    HostSpan b2_span(ctx, "host_b2");
     int64_t out_total = 0, nchunks_total = 0, bins_total = 0, scan_b2 = 0, max_hash_out = 0;
     for (int p : hll_ids) {
       Plan& pl = plans[p];
@@ -600,6 +622,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       ck(ctx, cudaMemcpyAsync(Z.chunk_begin, st, 8 * (size_t)(nlive + 1), cudaMemcpyHostToDevice, s),
          "upload chunks");
     }
+    b2_span.done();
     mark(ctx, s, "plan_upload");
     ck(ctx, cudaMemsetAsync(Z.zero, 0, Z.zero_bytes, s), "memset accumulators");
     mark(ctx, s, "zero_accumulators");
