@@ -238,7 +238,12 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     // ~6 tasks per resident CTA so the dynamic task queue evens out the
     // uneven (diamond-shaped) work per output block
     const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, (227 * 1024) / (S * 8 + 11264)));
-    const double tgt = pairs / (double)(num_sms * per_sm * KR_TASKS_PER_CTA);
+    // tasks per resident CTA: at least KR_TASKS_PER_CTA, more for large
+    // products (tasks of about 50,000 term-products, at most 24 per CTA), so
+    // that the last tasks, which set the run's tail, stay short
+    const double ctas = (double)num_sms * (double)per_sm;
+    const double per_cta = std::min(24.0, std::max((double)KR_TASKS_PER_CTA, pairs / (ctas * 5e4)));
+    const double tgt = pairs / (ctas * per_cta);
     P.work_target = (int64_t)std::max(tgt, (double)(2 * S));
     pl.dense_task_cap = P.nblocks * 64;
     // bucket index over g's codes: at most 65536 buckets
