@@ -27,7 +27,10 @@
 namespace kr {
 
 constexpr int HASH_THREADS = 256;
-constexpr int HGROUP_R = 4;   // f terms per warp step, polynomial tiles
+#ifndef KR_HGROUP_R
+#define KR_HGROUP_R 2
+#endif
+constexpr int HGROUP_R = KR_HGROUP_R;   // f terms per warp step, polynomial tiles
 constexpr int PGROUP_R = 2;   // f terms per warp step, Poisson tiles (two keys each)
 
 template <typename T>
