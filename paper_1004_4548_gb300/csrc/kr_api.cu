@@ -415,18 +415,38 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   for (size_t q = 0; q < hll_ids.size(); ++q)
     h_hll_task_begin[q + 1] = h_hll_task_begin[q] + plans[hll_ids[q]].p.ntasks;
   std::vector<OpRef> all, bm, bt;
-  for (int q = 0; q < nlive; ++q) {
-    const Prod& P = plans[live_ids[q]].p;
+  // large bitmap operands of a call with few of them: the cluster front end
+  // (encode, rank and gather by CL_CTAS CTAs each); the rest one CTA each
+  std::vector<OpRef> cl;
+  int nbitmap = 0;
+  int64_t cl_range = 0;
+  for (int q = 0; q < nlive; ++q)
     for (int which = 0; which < 2; ++which) {
-      const Operand& op = which ? P.g : P.f;
+      const Operand& op = which ? plans[live_ids[q]].p.g : plans[live_ids[q]].p.f;
+      nbitmap += op.sort_method == SORT_BITMAP || op.sort_method == SORT_CLUSTER;
+    }
+  for (int q = 0; q < nlive; ++q) {
+    Prod& P = plans[live_ids[q]].p;
+    for (int which = 0; which < 2; ++which) {
+      Operand& op = which ? P.g : P.f;
+      if (op.sort_method == SORT_BITMAP && op.n >= CL_MIN_N && op.n <= CL_MAX_N && nbitmap <= CL_MAX_OPS)
+        op.sort_method = SORT_CLUSTER;
+      if (op.sort_method == SORT_CLUSTER) {
+        cl.push_back(OpRef{q, which});
+        cl_range = std::max(cl_range, op.key_range);
+        continue;
+      }
       all.push_back(OpRef{q, which});
       if (op.sort_method == SORT_BITMAP) bm.push_back(OpRef{q, which});
       if (op.sort_method == SORT_BITONIC) bt.push_back(OpRef{q, which});
     }
   }
+  bool gindex_needed = false;
+  for (int p : dense_ids) gindex_needed |= plans[p].p.g.sort_method != SORT_CLUSTER;
   std::vector<OpRef> lists = all;
   lists.insert(lists.end(), bm.begin(), bm.end());
   lists.insert(lists.end(), bt.begin(), bt.end());
+  lists.insert(lists.end(), cl.begin(), cl.end());
   ensure_pinned(ctx, sizeof(Prod) * (size_t)(nlive + 1) * 3 + sizeof(OpRef) * lists.size() +
                          16 * (h_block_begin.size() + h_task_begin.size() + 4 * (size_t)nlive) +
                          (size_t)(A.up_end - (char*)A.lprods) + 65536, s);
@@ -455,13 +475,21 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   const OpRef* d_all = A.oplists;
   const OpRef* d_bm = d_all + all.size();
   const OpRef* d_bt = d_bm + bm.size();
+  const OpRef* d_cl = d_bt + bt.size();
   // ---------------- phase B1 device work
   plan_span.done();
   mark(ctx, s, "plan_upload");
   if (A.hll_bytes) ck(ctx, cudaMemsetAsync(A.hll, 0, A.hll_bytes, s), "memset hll");
-  ck(ctx, launch_encode(A.lprods, d_all, (int)all.size(), s), "encode");
-  ctx->launches += 1;
-  mark(ctx, s, "encode");
+  if (!cl.empty()) {
+    ck(ctx, launch_front_cluster(A.lprods, d_cl, (int)cl.size(), cl_range, s), "cluster front end");
+    ctx->launches += 1;
+    mark(ctx, s, "front");
+  }
+  if (!all.empty()) {
+    ck(ctx, launch_encode(A.lprods, d_all, (int)all.size(), s), "encode");
+    ctx->launches += 1;
+    mark(ctx, s, "encode");
+  }
   if (!bm.empty()) {
     int64_t mx = 0;
     for (auto& r : bm) {
@@ -497,11 +525,13 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       ctx->launches += 3 * ((bits + 7) / 8);
     }
   }
-  mark(ctx, s, "sort");
-  ck(ctx, launch_gather(A.lprods, d_all, (int)all.size(), s), "gather");
-  ctx->launches += 1;
-  mark(ctx, s, "gather");
-  if (!dense_ids.empty()) {
+  if (!all.empty()) {
+    mark(ctx, s, "sort");
+    ck(ctx, launch_gather(A.lprods, d_all, (int)all.size(), s), "gather");
+    ctx->launches += 1;
+    mark(ctx, s, "gather");
+  }
+  if (gindex_needed) {
     ck(ctx, launch_build_gindex(A.lprods, A.dense_ids, (int)dense_ids.size(), max_ng_dense, s), "g index");
     ctx->launches += 1;
   }
@@ -596,10 +626,13 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       Z.cstat = b.take<uint64_t>(nchunks_total + 1);
       for (int p : live_ids) {
         Plan& pl = plans[p];
-        if (pl.p.path == PATH_DENSE) pl.p.dense = (void*)b.take<uint64_t>(pl.p.kspan);
-        else pl.p.table = b.take<uint64_t>(2 * pl.p.slots);
+        if (pl.p.path == PATH_DENSE && pl.p.nt > 0) pl.p.dense = (void*)b.take<uint64_t>(pl.p.kspan);
+        else if (pl.p.path != PATH_DENSE) pl.p.table = b.take<uint64_t>(2 * pl.p.slots);
       }
       Z.zero_bytes = b.off - zero_start;
+      // the block-accumulated arrays are cleared by the dense planning kernel
+      // (the blocks that its flushes do not write whole)
+      for (int p : dense_ids) plans[p].p.dense = (void*)b.take<uint64_t>(plans[p].p.kspan);
       if (!pass) ensure(ctx, &ctx->acc, &ctx->acc_cap, b.off + 1, s);
     }
     // a replay is captured without synchronisation: its B2 staging must not

@@ -20,8 +20,11 @@ constexpr int PLAN_SAMPLES = 32;   // sampled i per block for the work estimate
 constexpr int MAX_SPLIT = 64;      // tasks per block at most
 constexpr int ACC_THREADS = 512;
 
-// One warp per (dense product, block): i-range by binary search, sampled work
-// estimate, then 1..MAX_SPLIT tasks over equal i-slices.
+// One warp per (dense product, block): i-range by warp-wide search, sampled
+// work estimate, then 1..MAX_SPLIT tasks over equal i-slices.  A block that
+// gets one task is written whole by its flush; every other block (several
+// tasks adding into it, or none) is zeroed here, so the accumulation array
+// needs no separate clearing.
 __global__ void __launch_bounds__(256) k_dense_plan(const Prod* __restrict__ prods,
                                                    const int32_t* __restrict__ dense_prods,
                                                    const int64_t* __restrict__ block_begin,
@@ -39,46 +42,59 @@ __global__ void __launch_bounds__(256) k_dense_plan(const Prod* __restrict__ pro
   }
   const int pid = dense_prods[lo];
   const Prod& P = prods[pid];
-  if (P.status) return;
   const int64_t b = gw - block_begin[lo];
   // blocks tile the key window [klo, klo + kspan); its end may fall inside the last block
   const int64_t B = P.klo + b * P.S, E = min(B + P.S, P.klo + P.kspan);
+  int64_t k = 0;
   const int64_t* F = P.f.code;
   const int64_t* G = P.g.code;
   const int64_t nf = P.f.nkeep, ng = P.g.nkeep;   // dropped terms sort last
-  if (nf <= 0 || ng <= 0) return;
-  const int64_t i_lo = lower_bound_i64(F, nf, B - G[ng - 1]);
-  const int64_t i_hi = lower_bound_i64(F, nf, E - G[0]);
-  const int32_t* gx = P.gidx;
-  const int64_t gn = P.gidx_n;
-  const int gsh = P.gshift;
-  if (i_lo >= i_hi) return;
-  const int64_t span = i_hi - i_lo;
-  int64_t cnt = 0;
-  const int ns = span < PLAN_SAMPLES ? (int)span : PLAN_SAMPLES;
-  if (lane < ns) {
-    const int64_t i = i_lo + (span * lane) / ns;
-    cnt = g_lower_bound(G, ng, gx, gn, gsh, E - F[i]) - g_lower_bound(G, ng, gx, gn, gsh, B - F[i]);
+  if (!P.status && nf > 0 && ng > 0) {
+    const int64_t i_lo = warp_lower_bound(F, nf, B - G[ng - 1]);
+    const int64_t i_hi = warp_lower_bound(F, nf, E - G[0]);
+    if (i_lo < i_hi) {
+      const int32_t* gx = P.gidx;
+      const int64_t gn = P.gidx_n;
+      const int gsh = P.gshift;
+      const int64_t span = i_hi - i_lo;
+      int64_t cnt = 0;
+      const int ns = span < PLAN_SAMPLES ? (int)span : PLAN_SAMPLES;
+      if (lane < ns) {
+        const int64_t i = i_lo + (span * lane) / ns;
+        cnt = g_lower_bound(G, ng, gx, gn, gsh, E - F[i]) - g_lower_bound(G, ng, gx, gn, gsh, B - F[i]);
+      }
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      // a zero estimate does not prove an empty block (the samples may all miss),
+      // so every block with a nonempty i-range gets at least one task
+      const double est = (double)cnt * (double)span / (double)ns;
+      k = (int64_t)(est / (double)P.work_target) + 1;
+      if (k > MAX_SPLIT) k = MAX_SPLIT;
+      if (k > span) k = span;
+      int64_t base = 0;
+      if (lane == 0) base = (int64_t)atomicAdd((unsigned long long*)task_count, (unsigned long long)k);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      for (int64_t t = lane; t < k; t += 32) {
+        if (base + t >= task_cap) break;
+        DenseTask T;
+        T.prod = pid;
+        T.pad = 0;
+        T.block = b;
+        T.i0 = i_lo + (span * t) / k;
+        T.i1 = i_lo + (span * (t + 1)) / k;
+        T.single = (k == 1);
+        tasks[base + t] = T;
+      }
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (lane != 0) return;
-  // a zero estimate does not prove an empty block (the samples may all miss),
-  // so every block with a nonempty i-range gets at least one task
-  const double est = (double)cnt * (double)span / (double)ns;
-  int64_t k = (int64_t)(est / (double)P.work_target) + 1;
-  if (k > MAX_SPLIT) k = MAX_SPLIT;
-  if (k > span) k = span;
-  const int64_t base = (int64_t)atomicAdd((unsigned long long*)task_count, (unsigned long long)k);
-  for (int64_t t = 0; t < k; ++t) {
-    if (base + t >= task_cap) break;
-    DenseTask T;
-    T.prod = pid;
-    T.pad = 0;
-    T.block = b;
-    T.i0 = i_lo + (span * t) / k;
-    T.i1 = i_lo + (span * (t + 1)) / k;
-    T.single = (k == 1);
-    tasks[base + t] = T;
+  if (k != 1 && P.dense) {
+    // 16-byte stores over the block's slots, with an 8-byte store for a slot
+    // before the first 16-byte boundary and for an unpaired last slot
+    uint64_t* out = (uint64_t*)P.dense + (B - P.klo);
+    const int64_t len = E - B;
+    const int64_t head = ((uintptr_t)out & 15) ? 1 : 0;
+    if (head && lane == 0 && len > 0) out[0] = 0;
+    for (int64_t s = head + 2 * lane; s + 1 < len; s += 64) *(uint4*)(out + s) = make_uint4(0, 0, 0, 0);
+    if (len > head && ((len - head) & 1) && lane == 0) out[len - 1] = 0;
   }
 }
 
@@ -101,6 +117,7 @@ cudaError_t launch_dense_plan(const Prod* dprods, const int32_t* ddense_prods,
 __global__ void __launch_bounds__(256) k_build_gindex(const Prod* __restrict__ prods,
                                                      const int32_t* __restrict__ dense_prods) {
   const Prod& P = prods[dense_prods[blockIdx.y]];
+  if (P.g.sort_method == SORT_CLUSTER) return;   // the cluster front end built it
   const int64_t* G = P.g.code;
   const int64_t ng = P.g.n;
   const int sh = P.gshift;
@@ -361,10 +378,8 @@ __device__ __forceinline__ void dense_flush(const Prod& P, const DenseTask& tk, 
   T* out = (T*)P.dense + B;
   for (int64_t s = threadIdx.x; s < lim; s += blockDim.x) {
     const T v = acc.get(s);
-    if (v != (T)0) {
-      if (tk.single) out[s] = v;
-      else smem_add<T>(&out[s], v);   // generic atomicAdd works on global memory too
-    }
+    if (tk.single) out[s] = v;   // the block's only task: every slot, zeros included
+    else if (v != (T)0) smem_add<T>(&out[s], v);   // generic atomicAdd works on global memory too
   }
 }
 

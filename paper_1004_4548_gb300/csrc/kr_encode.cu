@@ -12,6 +12,8 @@
 // highest-index nonzero entry, which is what the canonical form looks at.
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "kr_internal.cuh"
 
 namespace kr {
@@ -170,6 +172,7 @@ __device__ __forceinline__ TermCode encode_term(const Prod& P, const Operand& O,
   TermCode tc;
   tc.pcode = 0; tc.tcode = 0; tc.kind = 0; tc.bad = 0; tc.drop = false;
   int64_t deg = 0;
+#pragma unroll 4
   for (int k = 0; k < P.np; ++k) {
     int32_t e = O.e[(int64_t)k * O.n + i];
     if (P.graded) {
@@ -186,6 +189,7 @@ __device__ __forceinline__ TermCode encode_term(const Prod& P, const Operand& O,
     else tc.pcode += P.c[r] * (deg - O.emin[r]);
   }
   if (P.nt > 0) {
+#pragma unroll 4
     for (int k = 0; k < P.nt; ++k) {
       int32_t t = O.t[(int64_t)k * O.n + i];
       int32_t a = t < 0 ? -t : t;
@@ -285,6 +289,189 @@ __global__ void __launch_bounds__(256) k_gather(Prod* __restrict__ prods, const 
 
 cudaError_t launch_gather(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s) {
   if (nops > 0) k_gather<<<dim3(8, nops), 256, 0, s>>>(dprods, dops);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// cluster front end (SORT_CLUSTER operands): one cluster of CL_CTAS CTAs per
+// operand.  The operand's key range is cut into CL_CTAS slices; CTA r holds
+// slice r of the key bitmap and, per bitmap word, the number of set bits of
+// the slice before it, in its shared memory.  Term i belongs to thread
+// (i mod CL_CTAS * CL_THREADS) of the cluster, which holds at most CL_K terms
+// (the host sends larger operands elsewhere) in registers throughout.
+//   1. each thread encodes its terms (every load issued before any is used)
+//      and sets their bits in the owning CTA's slice (atomicOr through
+//      distributed shared memory; a bit already set is a repeated key);
+//   2. each CTA turns its slice into per-word prefix counts (block scan), and
+//      the slices' totals give every slice its first rank;
+//   3. each thread ranks its keys with two loads from the owning CTA (the
+//      word's prefix and the word) and writes the terms in sorted position
+//      (the gather); each CTA fills the dense g bucket index of its slice.
+// It replaces the encode, sort and gather launches (one CTA per operand for
+// the sort) by one launch whose every phase is spread over CL_CTAS SMs.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+__global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
+    k_front_cluster(Prod* __restrict__ prods, const OpRef* __restrict__ ops) {
+  extern __shared__ uint32_t csm[];
+  __shared__ uint32_t wsum[CL_THREADS / 32];
+  __shared__ unsigned long long s_tot, s_drop;
+  __shared__ int64_t s_base[CL_CTAS + 1];
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned me = cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const OpRef r = ops[blockIdx.x / CL_CTAS];
+  Prod& P = prods[r.prod];
+  Operand& O = r.which ? P.g : P.f;
+  const int64_t R = O.key_range, n = O.n;
+  const int64_t Lw = cluster_slice_words(R);
+  const uint64_t L = (uint64_t)Lw * 32;
+  uint32_t* bits = csm;
+  uint32_t* pre = csm + Lw;   // set bits of the slice before each word
+  for (int64_t w = tid; w < Lw; w += CL_THREADS) bits[w] = 0;
+  if (tid == 0) s_drop = 0;
+  cl.sync();   // every slice is clear before any thread of the cluster sets a bit
+  const int64_t first = (int64_t)me * CL_THREADS + tid, stride = (int64_t)CL_CTAS * CL_THREADS;
+  uint64_t key[CL_K];
+  uint32_t bad = 0;
+  unsigned long long ndrop = 0;
+#pragma unroll
+  for (int k = 0; k < CL_K; ++k) {
+    const int64_t i = first + k * stride;
+    key[k] = 0;
+    if (i < n) {
+      TermCode tc = encode_term(P, O, i);
+      uint64_t kk = tc.drop ? (uint64_t)(O.sent + i) : term_key(P, tc);
+      if (!tc.bad && kk >= (uint64_t)R) tc.bad |= ST_RANGE;   // keeps the slice index in bounds
+      if (tc.bad) kk = 0;   // the status fails the product
+      bad |= tc.bad;
+      ndrop += tc.drop ? 1 : 0;
+      key[k] = kk;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CL_K; ++k) {
+    if (first + k * stride < n) {
+      const unsigned owner = (unsigned)(key[k] / L);
+      const uint64_t off = key[k] - (uint64_t)owner * L;
+      const uint32_t bit = 1u << (off & 31);
+      if (atomicOr(cl.map_shared_rank(bits, owner) + (off >> 5), bit) & bit) bad |= ST_DUP;
+    }
+  }
+  cl.sync();   // every key's bit is set
+  // per-word prefix counts of this slice: each thread a contiguous run of words
+  const int64_t per = (Lw + CL_THREADS - 1) / CL_THREADS;
+  const int64_t wa = min(Lw, per * tid), wb = min(Lw, wa + per);
+  uint32_t cnt = 0;
+  for (int64_t w = wa; w < wb; ++w) cnt += __popc(bits[w]);
+  uint32_t x = cnt;   // block exclusive scan of the counts (a slice holds < 2^32 bits)
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  for (int o = 16; o > 0; o >>= 1) ndrop += __shfl_xor_sync(0xffffffffu, ndrop, o);
+  if (lane == 0 && ndrop) atomicAdd(&s_drop, ndrop);
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    wsum[lane] = v;
+    if (lane == 31) s_tot = v;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? wsum[warp - 1] : 0) + x - cnt;
+  for (int64_t w = wa; w < wb; ++w) {
+    pre[w] = run;
+    run += __popc(bits[w]);
+  }
+  cl.sync();   // every slice's prefix counts, total and dropped count are final
+  if (warp == 0) {
+    unsigned long long t = 0, d = 0;
+    if (lane < CL_CTAS) {
+      t = *cl.map_shared_rank(&s_tot, (unsigned)lane);
+      d = *cl.map_shared_rank(&s_drop, (unsigned)lane);
+    }
+    unsigned long long inc = t;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane < CL_CTAS) s_base[lane] = (int64_t)(inc - t);
+    if (lane == CL_CTAS - 1) s_base[CL_CTAS] = (int64_t)inc;
+    // terms past the degree bound sort last: the kept prefix
+    if (me == 0 && lane == 0) O.nkeep = n - (int64_t)d;
+  }
+  __syncthreads();
+  int64_t q[CL_K];
+#pragma unroll
+  for (int k = 0; k < CL_K; ++k) {
+    q[k] = n;
+    if (first + k * stride < n) {
+      const unsigned owner = (unsigned)(key[k] / L);
+      const uint64_t off = key[k] - (uint64_t)owner * L;
+      const uint32_t wv = cl.map_shared_rank(bits, owner)[off >> 5];
+      const uint32_t pv = cl.map_shared_rank(pre, owner)[off >> 5];
+      q[k] = s_base[owner] + pv + __popc(wv & ((1u << (off & 31)) - 1u));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CL_K; ++k) {
+    const int64_t i = first + k * stride;
+    if (i >= n) continue;
+    if (q[k] >= n) { bad |= ST_DUP; continue; }
+    if (P.nt == 0) {
+      O.code[q[k]] = (int64_t)key[k];
+      if (O.code32) O.code32[q[k]] = (int32_t)key[k];
+      if (P.f64) ((double*)O.coef)[q[k]] = ((const double*)O.c)[i];
+      else ((int64_t*)O.coef)[q[k]] = ((const int64_t*)O.c)[i];
+    } else {
+      TermCode tc = encode_term(P, O, i);
+      if (key[k] >= (uint64_t)O.sent) { tc.pcode = TRUNC_PSENT; tc.tcode = 0; tc.kind = 0; }
+      O.code[q[k]] = tc.pcode;
+      O.tcode[q[k]] = tc.tcode;
+      O.kind[q[k]] = (uint8_t)tc.kind;
+      const double c = ((const double*)O.c)[i];
+      ((double*)O.coef)[q[k]] = r.which == 0 ? 0.5 * c : c;   // the 1/2 of the product-to-sum identities
+    }
+  }
+  // the g bucket index of a dense product: gidx[b] = number of keys below
+  // b << gshift, for the buckets that start in this slice (the last CTA also
+  // takes the buckets past every slice)
+  if (r.which == 1 && P.nt == 0 && P.path == PATH_DENSE && P.gidx) {
+    const int sh = P.gshift;
+    const int64_t gn = P.gidx_n;
+    const int64_t lo = (int64_t)me * (int64_t)L;
+    const int64_t b0 = (lo + (int64_t(1) << sh) - 1) >> sh;
+    const int64_t b1 = me == CL_CTAS - 1 ? gn + 1 : min(gn + 1, (lo + (int64_t)L + (int64_t(1) << sh) - 1) >> sh);
+    for (int64_t b = b0 + tid; b < b1; b += CL_THREADS) {
+      const int64_t off = (b << sh) - lo;
+      int64_t v = s_base[CL_CTAS];
+      if (off < (int64_t)L) {
+        const int64_t w = off >> 5;
+        v = s_base[me] + pre[w] + __popc(bits[w] & ((1u << (off & 31)) - 1u));
+      }
+      P.gidx[b] = (int32_t)v;
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (bad && lane == 0) atomicOr(&P.status, bad);
+  cl.sync();   // other CTAs read this CTA's slice until here
+}
+
+cudaError_t launch_front_cluster(Prod* dprods, const OpRef* dops, int nops, int64_t max_key_range,
+                                 cudaStream_t s) {
+  if (nops <= 0) return cudaSuccess;
+  const int64_t lw = cluster_slice_words(max_key_range);
+  const size_t smem = (size_t)(2 * lw) * 4;
+  cudaError_t e = cudaFuncSetAttribute(k_front_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_front_cluster<<<(unsigned)(nops * CL_CTAS), CL_THREADS, smem, s>>>(dprods, dops);
   return cudaGetLastError();
 }
 

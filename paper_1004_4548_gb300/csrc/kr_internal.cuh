@@ -33,6 +33,22 @@ constexpr uint32_t ST_OUTCAP = 16u;     // compaction found more terms than rese
 constexpr int SORT_BITMAP = 1;   // key range fits an on-chip bitmap
 constexpr int SORT_BITONIC = 2;  // n fits a shared-memory bitonic network
 constexpr int SORT_RADIX = 3;    // device-wide LSD radix sort
+constexpr int SORT_CLUSTER = 4;  // bitmap over a cluster's shared memory: encode, rank and
+                                 // gather in one kernel (large operands, few per call)
+
+// cluster front end: CL_CTAS CTAs per operand, each holding one slice of the
+// operand's key bitmap (and per-word prefix counts) in its shared memory
+constexpr int CL_CTAS = 8;
+constexpr int CL_THREADS = 1024;
+constexpr int CL_K = 4;              // terms per thread at most
+constexpr int64_t CL_MIN_N = 2048;   // smaller operands keep the one-CTA bitmap sort
+constexpr int64_t CL_MAX_N = (int64_t)CL_CTAS * CL_THREADS * CL_K;
+constexpr int CL_MAX_OPS = 64;       // more bitmap operands in a call: one CTA each
+__host__ __device__ inline int64_t cluster_slice_words(int64_t key_range) {
+  const int64_t words = (key_range + 31) >> 5;
+  const int64_t per = (words + CL_CTAS - 1) / CL_CTAS;
+  return (per + 7) & ~int64_t(7);
+}
 
 // One input series on the device.
 struct Operand {
@@ -145,6 +161,26 @@ __device__ __forceinline__ int64_t lower_bound_i64(const int64_t* a, int64_t n, 
   return lo;
 }
 
+// lower_bound by a whole warp (every lane calls it with the same arguments and
+// gets the answer): 32 probes per round cut the range 32-fold, so a search
+// costs a few dependent loads instead of log2(n)
+__device__ __forceinline__ int64_t warp_lower_bound(const int64_t* a, int64_t n, int64_t x) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;   // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) >> 5;
+    const int64_t p = lo + lane * step;
+    // sorted input: the probes below x are a prefix of the lanes
+    const int c = __popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
+    if (c == 0) return lo;
+    const int64_t pc = lo + (int64_t)c * step;
+    lo = lo + (int64_t)(c - 1) * step + 1;
+    if (c < 32 && pc < hi) hi = pc;
+  }
+  const int64_t p = lo + lane;
+  return lo + __popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
+}
+
 // lower_bound over the sorted g codes through the coarse bucket index: the
 // answer for x lies in [gidx[x >> gshift], gidx[(x >> gshift) + 1]].
 __device__ __forceinline__ int64_t g_lower_bound(const int64_t* G, int64_t ng, const int32_t* gidx,
@@ -241,6 +277,10 @@ cudaError_t launch_encode(Prod* dprods, const OpRef* dops, int nops, cudaStream_
 cudaError_t launch_sort_small(Prod* dprods, const OpRef* dops, int nops, int method,
                               size_t smem, cudaStream_t s);
 cudaError_t launch_gather(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s);
+// SORT_CLUSTER operands: encode, bitmap rank and gather (and the g bucket
+// index of a dense product) in one launch of one cluster per operand
+cudaError_t launch_front_cluster(Prod* dprods, const OpRef* dops, int nops, int64_t max_key_range,
+                                 cudaStream_t s);
 
 cudaError_t launch_dense_plan(const Prod* dprods, const int32_t* ddense_prods,
                               const int64_t* dblock_begin, int ndense, int64_t nblocks_total,
