@@ -239,6 +239,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   OpRef* dops = nullptr;
   int32_t* dranges = nullptr;
   char* drs = nullptr;
+  unsigned int* ddone = nullptr;   // the range scan's per-operand counters, uploaded as zeros
   int64_t max_n = 1;
   for (const JobIn& in : ins) max_n = std::max(max_n, std::max(in.nf, in.ng));
   for (int pass = 0; pass < 2; ++pass) {
@@ -267,15 +268,18 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     }
     dprods = b.take<Prod>(nprod);
     dops = b.take<OpRef>(nops);
+    ddone = b.take<unsigned int>(nops);
     dranges = b.take<int32_t>((int64_t)nops * RANGE_STRIDE);
     drs = b.take<char>((int64_t)range_scan_scratch_bytes(nops, max_n));
     if (!pass) ensure(ctx, &ctx->in_arena, &ctx->in_cap, b.off + 1, s);
   }
-  ensure_pinned(ctx, (sizeof(Prod) + 2 * sizeof(OpRef) + 2 * RANGE_STRIDE * 4) * (size_t)nprod + 65536, s);
+  ensure_pinned(ctx, (sizeof(Prod) + 2 * sizeof(OpRef) + 8 + 2 * RANGE_STRIDE * 4) * (size_t)nprod + 65536, s);
   {
     Bump hp(ctx->pinned);
     Prod* hprods = hp.take<Prod>(nprod);
     OpRef* hops = hp.take<OpRef>(nops);
+    unsigned int* hdone = hp.take<unsigned int>(nops);
+    memset(hdone, 0, sizeof(unsigned int) * (size_t)nops);
     int32_t* hranges = hp.take<int32_t>((int64_t)nops * RANGE_STRIDE);
     for (int p = 0; p < nprod; ++p) {
       Prod P{};
@@ -294,12 +298,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       hops[2 * p] = OpRef{p, 0};
       hops[2 * p + 1] = OpRef{p, 1};
     }
-    // products and operand list, laid out alike on both sides: one copy
-    ck(ctx, cudaMemcpyAsync(dprods, hprods, (size_t)((char*)(dops + nops) - (char*)dprods),
+    // products, operand list and counters, laid out alike on both sides: one copy
+    ck(ctx, cudaMemcpyAsync(dprods, hprods, (size_t)((char*)(ddone + nops) - (char*)dprods),
                             cudaMemcpyHostToDevice, s), "upload");
     mark(ctx, s, "begin");
-    ck(ctx, launch_range_scan(dprods, dops, nops, max_n, drs, dranges, s), "range scan");
-    ctx->launches += 2;
+    ck(ctx, launch_range_scan(dprods, dops, nops, max_n, drs, ddone, dranges, s), "range scan");
+    ctx->launches += 1;
     mark(ctx, s, "range_scan");
     ck(ctx, cudaMemcpyAsync(hranges, dranges, sizeof(int32_t) * nops * RANGE_STRIDE,
                             cudaMemcpyDeviceToHost, s), "download ranges");
@@ -342,6 +346,12 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   for (int p : hash_ids) h_hash_local.push_back(local[p]);
   std::vector<int32_t> h_hll_local;
   for (int p : hll_ids) h_hll_local.push_back(local[p]);
+  // deferred: one product, no hash table (nothing to size from the estimate or
+  // to regrow), not a prepared or split run.  Its whole plan (phases B1 and
+  // B2) goes to the device in one copy, and no step waits for the device
+  // before the output count is read.
+  const bool deferred = ctx->allow_deferred && !ctx->replay && !ctx->split_hist && nlive == 1 &&
+                        nprod == 1 && hll_ids.empty();
   // ---------------- phase B1 layout (work arena)
   int64_t dense_tasks_total = 0, nblocks_total = 0, scan_b1 = 0, max_ng_dense = 0, max_S = 0;
   for (int p : dense_ids) {
@@ -354,7 +364,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   struct B1 {
     Prod* lprods; OpRef* oplists; int32_t* dense_ids; int64_t* block_begin; int32_t* hash_ids;
     int64_t* task_begin; int64_t* scan; DenseTask* tasks; uint32_t* hll; size_t hll_bytes;
-    int32_t* hll_ids; int64_t* hll_task_begin; unsigned long long* split; char* up_end;
+    int32_t* hll_ids; int64_t* hll_task_begin; int64_t* chunk_begin; unsigned long long* split; char* up_end;
   } A{};
   for (int pass = 0; pass < 2; ++pass) {
     Bump b(pass ? ctx->work : nullptr);
@@ -367,6 +377,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     A.task_begin = b.take<int64_t>((int64_t)hash_ids.size() + 1);
     A.hll_ids = b.take<int32_t>((int64_t)hll_ids.size() + 1);
     A.hll_task_begin = b.take<int64_t>((int64_t)hll_ids.size() + 1);
+    A.chunk_begin = b.take<int64_t>((int64_t)nlive + 1);   // used by a deferred product
     A.up_end = b.base ? b.base + b.off : nullptr;
     A.scan = b.take<int64_t>(scan_b1 + 1);
     A.tasks = b.take<DenseTask>(dense_tasks_total);
@@ -414,6 +425,70 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   std::vector<int64_t> h_hll_task_begin(hll_ids.size() + 1, 0);
   for (size_t q = 0; q < hll_ids.size(); ++q)
     h_hll_task_begin[q + 1] = h_hll_task_begin[q] + plans[hll_ids[q]].p.ntasks;
+  // ---------------- phase B2 layout (accumulation arena): table sizes, output
+  // room, chunk ranges, accumulators; a deferred product lays it out now
+  struct B2 {
+    int64_t* chunk_begin; int64_t* counts; int64_t* scan; int64_t* bins; uint64_t *okey, *oval, *okey2, *oval2;
+    int64_t* counters; uint64_t* cstat; char* zero; size_t zero_bytes;
+  } Z{};
+  int64_t out_total = 0, nchunks_total = 0, bins_total = 0, scan_b2 = 0, max_hash_out = 0;
+  std::vector<int64_t> h_chunk_begin(nlive + 1, 0);
+  auto layout_b2 = [&]() {
+    out_total = 0, nchunks_total = 0, bins_total = 0, scan_b2 = 0, max_hash_out = 0;
+    for (int p : hll_ids) {
+      Plan& pl = plans[p];
+      finish_hash_sizes(ins[p].opts, &pl);
+      max_hash_out = std::max(max_hash_out, pl.out_cap);
+      const int64_t nb = order_bins(pl.p.kspan);
+      if (pl.p.kspan <= ORDER_BITMAP_MAX)
+        bins_total = std::max(bins_total, (order_bitmap_bytes(pl.p.kspan) + 7) / 8);
+      else if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, order_bins_scratch(pl.p.kspan));
+      else scan_b2 = std::max(scan_b2, radix_scan_entries(pl.out_cap));
+    }
+    std::fill(h_chunk_begin.begin(), h_chunk_begin.end(), 0);
+    for (int q = 0; q < nlive; ++q) {
+      Plan& pl = plans[live_ids[q]];
+      pl.p.out_cap = pl.out_cap;
+      pl.p.out_begin = out_total;
+      pl.p.chunk_begin = nchunks_total;
+      h_chunk_begin[q] = nchunks_total;
+      out_total += pl.out_cap;
+      nchunks_total += pl.p.nchunks;
+    }
+    h_chunk_begin[nlive] = nchunks_total;
+    Z = B2{};
+    for (int pass = 0; pass < 2; ++pass) {
+      Bump b(pass ? ctx->acc : nullptr);
+      Z.chunk_begin = b.take<int64_t>(nlive + 1);
+      Z.counts = b.take<int64_t>(nchunks_total + 1);
+      Z.scan = b.take<int64_t>(std::max(scan_b2, scan_scratch_entries(nchunks_total)) + 1);
+      Z.bins = b.take<int64_t>(bins_total);
+      Z.okey = b.take<uint64_t>(out_total);
+      Z.oval = b.take<uint64_t>(out_total);
+      // ordering scratch: one hash product at a time
+      Z.okey2 = b.take<uint64_t>(max_hash_out);
+      Z.oval2 = b.take<uint64_t>(max_hash_out);
+      b.off = (b.off + 255) / 256 * 256;
+      const size_t zero_start = b.off;
+      Z.zero = b.base ? b.base + zero_start : nullptr;
+      Z.counters = b.take<int64_t>(4);   // dense task queue (2), compaction ticket and error flag
+      Z.cstat = b.take<uint64_t>(nchunks_total + 1);
+      for (int p : live_ids) {
+        Plan& pl = plans[p];
+        if (pl.p.path == PATH_DENSE && pl.p.nt > 0) pl.p.dense = (void*)b.take<uint64_t>(pl.p.kspan);
+        else if (pl.p.path != PATH_DENSE) pl.p.table = b.take<uint64_t>(2 * pl.p.slots);
+      }
+      Z.zero_bytes = b.off - zero_start;
+      // the block-accumulated arrays are cleared by the dense planning kernel
+      // (the blocks that its flushes do not write whole)
+      for (int p : dense_ids) plans[p].p.dense = (void*)b.take<uint64_t>(plans[p].p.kspan);
+      if (!pass) ensure(ctx, &ctx->acc, &ctx->acc_cap, b.off + 1, s);
+    }
+  };
+  if (deferred) {
+    layout_b2();
+    Z.chunk_begin = A.chunk_begin;   // uploaded with phase B1's plan
+  }
   std::vector<OpRef> all, bm, bt;
   // large bitmap operands of a call with few of them: the cluster front end
   // (encode, rank and gather by CL_CTAS CTAs each); the rest one CTA each
@@ -470,6 +545,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     put(A.task_begin, h_task_begin.data(), 8 * h_task_begin.size());
     put(A.hll_ids, h_hll_local.data(), 4 * h_hll_local.size());
     put(A.hll_task_begin, h_hll_task_begin.data(), 8 * h_hll_task_begin.size());
+    put(A.chunk_begin, h_chunk_begin.data(), 8 * h_chunk_begin.size());
     ck(ctx, cudaMemcpyAsync(dbase, st, span, cudaMemcpyHostToDevice, s), "upload plan");
   }
   const OpRef* d_all = A.oplists;
@@ -547,10 +623,6 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       mark(ctx, s, "hll");
     }
   }
-  // deferred: one product, no hash table (nothing to size from the estimate or
-  // to regrow), not a prepared or split run
-  const bool deferred = ctx->allow_deferred && !ctx->replay && !ctx->split_hist && nlive == 1 &&
-                        nprod == 1 && hll_ids.empty();
   if (!ctx->replay && !deferred) {
     ck(ctx, cudaMemcpyAsync(hl, A.lprods, sizeof(Prod) * nlive, cudaMemcpyDeviceToHost, s), "download");
     ck(ctx, cudaStreamSynchronize(s), "sync b1");
@@ -579,77 +651,18 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   }
   // ---------------- phase B2, repeated for products whose table filled up
   std::vector<int> regrows(nprod, 0);
+  bool first_b2 = true;
   for (;;) {
     HostSpan b2_span(ctx, "host_b2");
-    int64_t out_total = 0, nchunks_total = 0, bins_total = 0, scan_b2 = 0, max_hash_out = 0;
-    for (int p : hll_ids) {
-      Plan& pl = plans[p];
-      finish_hash_sizes(ins[p].opts, &pl);
-      max_hash_out = std::max(max_hash_out, pl.out_cap);
-      const int64_t nb = order_bins(pl.p.kspan);
-      if (pl.p.kspan <= ORDER_BITMAP_MAX)
-        bins_total = std::max(bins_total, (order_bitmap_bytes(pl.p.kspan) + 7) / 8);
-      else if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, order_bins_scratch(pl.p.kspan));
-      else scan_b2 = std::max(scan_b2, radix_scan_entries(pl.out_cap));
-    }
-    std::vector<int64_t> h_chunk_begin(nlive + 1, 0);
-    for (int q = 0; q < nlive; ++q) {
-      Plan& pl = plans[live_ids[q]];
-      pl.p.out_cap = pl.out_cap;
-      pl.p.out_begin = out_total;
-      pl.p.chunk_begin = nchunks_total;
-      h_chunk_begin[q] = nchunks_total;
-      out_total += pl.out_cap;
-      nchunks_total += pl.p.nchunks;
-    }
-    h_chunk_begin[nlive] = nchunks_total;
-    struct B2 {
-      int64_t* chunk_begin; int64_t* counts; int64_t* scan; int64_t* bins; uint64_t *okey, *oval, *okey2, *oval2;
-      int64_t* counters; uint64_t* cstat; Prod* stage; char* zero; size_t zero_bytes;
-    } Z{};
-    for (int pass = 0; pass < 2; ++pass) {
-      Bump b(pass ? ctx->acc : nullptr);
-      Z.chunk_begin = b.take<int64_t>(nlive + 1);
-      Z.stage = b.take<Prod>(nlive);
-      Z.counts = b.take<int64_t>(nchunks_total + 1);
-      Z.scan = b.take<int64_t>(std::max(scan_b2, scan_scratch_entries(nchunks_total)) + 1);
-      Z.bins = b.take<int64_t>(bins_total);
-      Z.okey = b.take<uint64_t>(out_total);
-      Z.oval = b.take<uint64_t>(out_total);
-      // ordering scratch: one hash product at a time
-      Z.okey2 = b.take<uint64_t>(max_hash_out);
-      Z.oval2 = b.take<uint64_t>(max_hash_out);
-      b.off = (b.off + 255) / 256 * 256;
-      const size_t zero_start = b.off;
-      Z.zero = b.base ? b.base + zero_start : nullptr;
-      Z.counters = b.take<int64_t>(4);   // dense task queue (2), compaction ticket and error flag
-      Z.cstat = b.take<uint64_t>(nchunks_total + 1);
-      for (int p : live_ids) {
-        Plan& pl = plans[p];
-        if (pl.p.path == PATH_DENSE && pl.p.nt > 0) pl.p.dense = (void*)b.take<uint64_t>(pl.p.kspan);
-        else if (pl.p.path != PATH_DENSE) pl.p.table = b.take<uint64_t>(2 * pl.p.slots);
-      }
-      Z.zero_bytes = b.off - zero_start;
-      // the block-accumulated arrays are cleared by the dense planning kernel
-      // (the blocks that its flushes do not write whole)
-      for (int p : dense_ids) plans[p].p.dense = (void*)b.take<uint64_t>(plans[p].p.kspan);
-      if (!pass) ensure(ctx, &ctx->acc, &ctx->acc_cap, b.off + 1, s);
-    }
+    if (!(deferred && first_b2)) layout_b2();
+    first_b2 = false;
     // a replay is captured without synchronisation: its B2 staging must not
     // overwrite B1's, so it continues after it
     Bump hb2 = (ctx->replay || deferred) ? hb : Bump(ctx->pinned);
     Prod* hl2 = hb2.take<Prod>(nlive);
-    for (int q = 0; q < nlive; ++q) hl2[q] = plans[live_ids[q]].p;
-    if (deferred) {
-      // phase B1's status and kept-term counts are still on the device only:
-      // upload the new plan beside it and merge, keeping those
-      ck(ctx, cudaMemcpyAsync(Z.stage, hl2, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
-      ck(ctx, launch_merge_plan(A.lprods, Z.stage, nlive, s), "merge plan");
-      ctx->launches += 1;
-    } else {
+    if (!deferred) {   // a deferred product's phase B2 plan went up with phase B1's
+      for (int q = 0; q < nlive; ++q) hl2[q] = plans[live_ids[q]].p;
       ck(ctx, cudaMemcpyAsync(A.lprods, hl2, sizeof(Prod) * nlive, cudaMemcpyHostToDevice, s), "upload plan");
-    }
-    {
       int64_t* st = hb2.take<int64_t>(nlive + 1);
       memcpy(st, h_chunk_begin.data(), 8 * (size_t)(nlive + 1));
       ck(ctx, cudaMemcpyAsync(Z.chunk_begin, st, 8 * (size_t)(nlive + 1), cudaMemcpyHostToDevice, s),

@@ -10,6 +10,7 @@
 // |t_k| <= R_k; sums and differences of such codes are the codes of the sums
 // and differences of the vectors, and the sign of a code is the sign of the
 // highest-index nonzero entry, which is what the canonical form looks at.
+#include <algorithm>
 #include <climits>
 
 #include <cooperative_groups.h>
@@ -23,12 +24,13 @@ namespace kr {
 // whether every int64 coefficient fits in int32, and (truncated products) the
 // degree range.  ranges layout per operand: [0, MAXV) min, [MAXV, 2 MAXV) max,
 // [2 MAXV, 3 MAXV) max|t|, then the flags described with RANGE_STRIDE.
-// Two launches: RS_SPLIT CTAs per operand each reduce a slice of the terms to
-// a partial record, then one CTA per operand combines the partials.
+// One launch: `split` CTAs per operand each reduce a slice of the terms to a
+// partial record; the last CTA of an operand to finish (a counter per operand,
+// zero at launch) combines the partials.
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
-constexpr int RS_SPLIT_MAX = 64;
-constexpr int64_t RS_TERMS_PER_CTA = 1024;
+constexpr int RS_SPLIT_MAX = 256;
+constexpr int RS_CTA_BUDGET = 2048;   // CTAs of one launch, about 13 per SM
 
 struct RangePart {
   int32_t lo[MAXV], hi[MAXV], tmax[MAXV];
@@ -37,18 +39,22 @@ struct RangePart {
   long long dlo, dhi;
 };
 
-int range_scan_splits(int64_t max_n) {
-  int64_t k = (max_n + RS_TERMS_PER_CTA - 1) / RS_TERMS_PER_CTA;
-  return (int)(k < 1 ? 1 : (k > RS_SPLIT_MAX ? RS_SPLIT_MAX : k));
+int range_scan_splits(int nops, int64_t max_n) {
+  int64_t k = (max_n + RS_THREADS - 1) / RS_THREADS;   // one term per thread
+  const int64_t budget = std::max<int64_t>(1, RS_CTA_BUDGET / std::max(1, nops));
+  k = std::min<int64_t>(k, std::min<int64_t>(budget, RS_SPLIT_MAX));
+  return (int)(k < 1 ? 1 : k);
 }
 
 size_t range_scan_scratch_bytes(int nops, int64_t max_n) {
-  return sizeof(RangePart) * (size_t)nops * (size_t)range_scan_splits(max_n);
+  return sizeof(RangePart) * (size_t)nops * (size_t)range_scan_splits(nops, max_n);
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_range_partial(const Prod* __restrict__ prods,
-                                                              const OpRef* __restrict__ ops,
-                                                              RangePart* __restrict__ parts) {
+__global__ void __launch_bounds__(RS_THREADS) k_range_scan(const Prod* __restrict__ prods,
+                                                           const OpRef* __restrict__ ops,
+                                                           RangePart* __restrict__ parts,
+                                                           unsigned int* __restrict__ done,
+                                                           int32_t* __restrict__ ranges) {
   const OpRef r = ops[blockIdx.y];
   const Prod& P = prods[r.prod];
   const Operand& O = r.which ? P.g : P.f;
@@ -56,29 +62,42 @@ __global__ void __launch_bounds__(RS_THREADS) k_range_partial(const Prod* __rest
   __shared__ int32_t smin[MAXV][RS_THREADS / 32], smax[MAXV][RS_THREADS / 32];
   __shared__ int sfits[RS_THREADS / 32];
   __shared__ long long sdlo[RS_THREADS / 32], sdhi[RS_THREADS / 32];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nvar = P.np + P.nt;
-  for (int k = 0; k < nvar; ++k) {
-    const bool is_trig = k >= P.np;
-    const int32_t* row = is_trig ? O.t + (int64_t)(k - P.np) * O.n : O.e + (int64_t)k * O.n;
-    int32_t lo = INT32_MAX, hi = INT32_MIN;
+  int fits = P.f64 ? 0 : 1;
+  // variables four at a time, every load of a group issued before any is used
+  for (int k0 = 0; k0 < max(nvar, 1); k0 += 4) {   // once at least: the coefficient check
+    int32_t lo[4], hi[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { lo[j] = INT32_MAX; hi[j] = INT32_MIN; }
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      int32_t x = row[i];
-      if (is_trig) x = x < 0 ? -x : x;
-      lo = min(lo, x);
-      hi = max(hi, x);
+      int32_t x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + j;
+        x[j] = 0;
+        if (k < P.np) x[j] = O.e[(int64_t)k * O.n + i];
+        else if (k < nvar) x[j] = O.t[(int64_t)(k - P.np) * O.n + i];
+      }
+      if (k0 == 0 && !P.f64) {
+        const int64_t c = ((const int64_t*)O.c)[i];
+        if (c < INT32_MIN || c > INT32_MAX) fits = 0;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int32_t v = x[j];
+        if (k0 + j >= P.np) v = v < 0 ? -v : v;
+        lo[j] = min(lo[j], v);
+        hi[j] = max(hi[j], v);
+      }
     }
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    if (lane == 0) { smin[k][warp] = lo; smax[k][warp] = hi; }
-  }
-  int fits = 1;
-  if (!P.f64) {
-    const int64_t* c = (const int64_t*)O.c;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
-      if (c[i] < INT32_MIN || c[i] > INT32_MAX) fits = 0;
-  } else {
-    fits = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int32_t a = __reduce_min_sync(0xffffffffu, lo[j]);
+      const int32_t b = __reduce_max_sync(0xffffffffu, hi[j]);
+      if (lane == 0 && k0 + j < nvar) { smin[k0 + j][warp] = a; smax[k0 + j][warp] = b; }
+    }
   }
   fits = __all_sync(0xffffffffu, fits);
   long long dlo = LLONG_MAX, dhi = LLONG_MIN;
@@ -97,7 +116,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_range_partial(const Prod* __rest
   }
   if (lane == 0) { sfits[warp] = fits; sdlo[warp] = dlo; sdhi[warp] = dhi; }
   __syncthreads();
-  RangePart& out = parts[(int64_t)blockIdx.y * gridDim.x + blockIdx.x];
+  RangePart* pp = parts + (int64_t)blockIdx.y * gridDim.x;
+  RangePart& out = pp[blockIdx.x];
   if (threadIdx.x < nvar) {
     const int k = threadIdx.x;
     int32_t lo = INT32_MAX, hi = INT32_MIN;
@@ -113,44 +133,47 @@ __global__ void __launch_bounds__(RS_THREADS) k_range_partial(const Prod* __rest
     out.dlo = a;
     out.dhi = b;
   }
-}
-
-__global__ void __launch_bounds__(32) k_range_reduce(const Prod* __restrict__ prods,
-                                                     const OpRef* __restrict__ ops, int nsplit,
-                                                     const RangePart* __restrict__ parts,
-                                                     int32_t* __restrict__ ranges) {
-  const OpRef r = ops[blockIdx.x];
-  const Prod& P = prods[r.prod];
-  const RangePart* pp = parts + (int64_t)blockIdx.x * nsplit;
-  int32_t* out = ranges + (int64_t)blockIdx.x * RANGE_STRIDE;
+  // the partial is published before the count; the CTA that counts last
+  // sees every partial of its operand
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&done[blockIdx.y], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nsplit = gridDim.x;
+  int32_t* res = ranges + (int64_t)blockIdx.y * RANGE_STRIDE;
   const int k = threadIdx.x;
-  if (k < P.np + P.nt) {
+  if (k < nvar) {
     int32_t lo = INT32_MAX, hi = INT32_MIN;
-    for (int s = 0; s < nsplit; ++s) { lo = min(lo, pp[s].lo[k]); hi = max(hi, pp[s].hi[k]); }
-    if (k < P.np) { out[k] = lo; out[MAXV + k] = hi; }
-    else { out[2 * MAXV + (k - P.np)] = hi; }
+    for (int q = 0; q < nsplit; ++q) { lo = min(lo, __ldcg(&pp[q].lo[k])); hi = max(hi, __ldcg(&pp[q].hi[k])); }
+    if (k < P.np) { res[k] = lo; res[MAXV + k] = hi; }
+    else { res[2 * MAXV + (k - P.np)] = hi; }
   }
   if (k == 0) {
     int f = 1;
     long long a = LLONG_MAX, b = LLONG_MIN;
-    for (int s = 0; s < nsplit; ++s) { f &= pp[s].fits; a = min(a, pp[s].dlo); b = max(b, pp[s].dhi); }
-    out[3 * MAXV] = f;
+    for (int q = 0; q < nsplit; ++q) {
+      f &= __ldcg(&pp[q].fits);
+      a = min(a, __ldcg(&pp[q].dlo));
+      b = max(b, __ldcg(&pp[q].dhi));
+    }
+    res[3 * MAXV] = f;
     if (P.gmask) {
       const bool over = a < INT32_MIN || b > INT32_MAX;
-      out[3 * MAXV + 1] = over ? 0 : (int32_t)a;
-      out[3 * MAXV + 2] = over ? 0 : (int32_t)b;
-      out[3 * MAXV + 3] = over ? 1 : 0;
+      res[3 * MAXV + 1] = over ? 0 : (int32_t)a;
+      res[3 * MAXV + 2] = over ? 0 : (int32_t)b;
+      res[3 * MAXV + 3] = over ? 1 : 0;
     }
+    done[blockIdx.y] = 0;   // ready for another launch over the same counters
   }
 }
 
 cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int64_t max_n, void* scratch,
-                              int32_t* dranges, cudaStream_t s) {
+                              unsigned int* ddone, int32_t* dranges, cudaStream_t s) {
   if (nops > 0) {
-    const int split = range_scan_splits(max_n);
-    RangePart* parts = (RangePart*)scratch;
-    k_range_partial<<<dim3(split, nops), RS_THREADS, 0, s>>>(dprods, dops, parts);
-    k_range_reduce<<<nops, 32, 0, s>>>(dprods, dops, split, parts, dranges);
+    const int split = range_scan_splits(nops, max_n);
+    k_range_scan<<<dim3(split, nops), RS_THREADS, 0, s>>>(dprods, dops, (RangePart*)scratch, ddone, dranges);
   }
   return cudaGetLastError();
 }
@@ -553,25 +576,6 @@ cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* 
     k_decode_pseries<<<(unsigned)grid, 256, 0, s>>>(dprods, prod, okey, n, exps, trig, kind, ld,
                                                     codes, dev_count ? 1 : 0, vals, coef);
   }
-  return cudaGetLastError();
-}
-
-// A new plan for products whose phase-B1 results are still on the device
-// only: dst = src, keeping dst's status and kept-term counts.
-__global__ void k_merge_plan(Prod* __restrict__ dst, const Prod* __restrict__ src, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const uint32_t st = dst[q].status;
-  const int64_t fk = dst[q].f.nkeep, gk = dst[q].g.nkeep;
-  Prod p = src[q];
-  p.status = st;
-  p.f.nkeep = fk;
-  p.g.nkeep = gk;
-  dst[q] = p;
-}
-
-cudaError_t launch_merge_plan(Prod* dst, const Prod* src, int n, cudaStream_t s) {
-  if (n > 0) k_merge_plan<<<(n + 63) / 64, 64, 0, s>>>(dst, src, n);
   return cudaGetLastError();
 }
 

@@ -271,8 +271,9 @@ struct OpRef {      // (product, operand) pair addressed by a per-operand kernel
 // Range records of every operand (min / max exponents, max |t|, flags); the
 // scratch holds range_scan_scratch_bytes(nops, max_n) bytes.
 size_t range_scan_scratch_bytes(int nops, int64_t max_n);
+// ddone: nops counters, zero at launch (and zero again after it).
 cudaError_t launch_range_scan(const Prod* dprods, const OpRef* dops, int nops, int64_t max_n, void* scratch,
-                              int32_t* dranges, cudaStream_t s);
+                              unsigned int* ddone, int32_t* dranges, cudaStream_t s);
 cudaError_t launch_encode(Prod* dprods, const OpRef* dops, int nops, cudaStream_t s);
 cudaError_t launch_sort_small(Prod* dprods, const OpRef* dops, int nops, int method,
                               size_t smem, cudaStream_t s);
@@ -356,8 +357,6 @@ cudaError_t launch_decode_pseries(const Prod* dprods, int prod, const uint64_t* 
                                   int32_t* exps, int32_t* trig, uint8_t* kind, int64_t ld,
                                   int64_t* codes, cudaStream_t s, bool dev_count = false,
                                   const uint64_t* vals = nullptr, uint64_t* coef = nullptr);
-// dst[q] = src[q] keeping dst[q]'s status and kept-term counts
-cudaError_t launch_merge_plan(Prod* dst, const Prod* src, int n, cudaStream_t s);
 // Where a batched decode writes one product's terms ([nvars][n] layouts).
 struct ResDesc {
   int32_t* exps;
