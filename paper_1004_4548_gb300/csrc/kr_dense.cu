@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(256) k_dense_plan(const Prod* __restrict__ pro
   const int64_t* G = P.g.code;
   const int64_t nf = P.f.nkeep, ng = P.g.nkeep;   // dropped terms sort last
   if (!P.status && nf > 0 && ng > 0) {
-    const int64_t i_lo = warp_lower_bound(F, nf, B - G[ng - 1]);
-    const int64_t i_hi = warp_lower_bound(F, nf, E - G[0]);
+    int64_t i_lo, i_hi;
+    warp_lower_bound2(F, nf, B - G[ng - 1], E - G[0], &i_lo, &i_hi);
     if (i_lo < i_hi) {
       const int32_t* gx = P.gidx;
       const int64_t gn = P.gidx_n;
@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(256) k_dense_plan(const Prod* __restrict__ pro
       const int ns = span < PLAN_SAMPLES ? (int)span : PLAN_SAMPLES;
       if (lane < ns) {
         const int64_t i = i_lo + (span * lane) / ns;
-        cnt = g_lower_bound(G, ng, gx, gn, gsh, E - F[i]) - g_lower_bound(G, ng, gx, gn, gsh, B - F[i]);
+        int64_t a, c;
+        g_lower_bound2(G, ng, gx, gn, gsh, B - F[i], E - F[i], &a, &c);
+        cnt = c - a;
       }
       for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
       // a zero estimate does not prove an empty block (the samples may all miss),

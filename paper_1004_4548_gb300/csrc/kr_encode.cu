@@ -340,6 +340,7 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
   extern __shared__ uint32_t csm[];
   __shared__ uint32_t wsum[CL_THREADS / 32];
   __shared__ unsigned long long s_tot, s_drop;
+  __shared__ unsigned long long s_all[2][CL_CTAS];   // every slice's total and dropped count
   __shared__ int64_t s_base[CL_CTAS + 1];
   cg::cluster_group cl = cg::this_cluster();
   const unsigned me = cl.block_rank();
@@ -407,6 +408,13 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
     if (lane == 31) s_tot = v;
   }
   __syncthreads();
+  // every CTA gets this slice's total and dropped count (remote stores, seen
+  // after the cluster barrier), so that no one waits on a remote load for them
+  if (tid < CL_CTAS) {
+    unsigned long long* dst = cl.map_shared_rank(&s_all[0][0], (unsigned)tid);
+    dst[me] = s_tot;
+    dst[CL_CTAS + me] = s_drop;
+  }
   uint32_t run = (warp ? wsum[warp - 1] : 0) + x - cnt;
   for (int64_t w = wa; w < wb; ++w) {
     pre[w] = run;
@@ -416,8 +424,8 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
   if (warp == 0) {
     unsigned long long t = 0, d = 0;
     if (lane < CL_CTAS) {
-      t = *cl.map_shared_rank(&s_tot, (unsigned)lane);
-      d = *cl.map_shared_rank(&s_drop, (unsigned)lane);
+      t = s_all[0][lane];
+      d = s_all[1][lane];
     }
     unsigned long long inc = t;
     for (int o = 1; o < 32; o <<= 1) {
@@ -484,7 +492,9 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
   }
   bad = __reduce_or_sync(0xffffffffu, bad);
   if (bad && lane == 0) atomicOr(&P.status, bad);
-  cl.sync();   // other CTAs read this CTA's slice until here
+  // other CTAs read this CTA's slice until here; every such read has been
+  // used before its thread arrives, so the arrival needs no release
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
 cudaError_t launch_front_cluster(Prod* dprods, const OpRef* dops, int nops, int64_t max_key_range,

@@ -181,6 +181,42 @@ __device__ __forceinline__ int64_t warp_lower_bound(const int64_t* a, int64_t n,
   return lo + __popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
 }
 
+// two lower_bounds over the same array by a whole warp, their rounds interleaved
+__device__ __forceinline__ void warp_lower_bound2(const int64_t* a, int64_t n, int64_t x1, int64_t x2,
+                                                  int64_t* r1, int64_t* r2) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo1 = 0, hi1 = n, lo2 = 0, hi2 = n;   // answers in [lo, hi]
+  bool done1 = false, done2 = false;
+  while ((!done1 && hi1 - lo1 > 32) || (!done2 && hi2 - lo2 > 32)) {
+    const bool s1 = !done1 && hi1 - lo1 > 32, s2 = !done2 && hi2 - lo2 > 32;
+    const int64_t st1 = (hi1 - lo1 + 31) >> 5, st2 = (hi2 - lo2 + 31) >> 5;
+    const int64_t p1 = lo1 + lane * st1, p2 = lo2 + lane * st2;
+    const bool b1 = s1 && p1 < hi1 && a[p1] < x1;
+    const bool b2 = s2 && p2 < hi2 && a[p2] < x2;
+    const int c1 = __popc(__ballot_sync(0xffffffffu, b1));
+    const int c2 = __popc(__ballot_sync(0xffffffffu, b2));
+    if (s1) {
+      if (c1 == 0) { hi1 = lo1; done1 = true; }
+      else {
+        const int64_t pc = lo1 + (int64_t)c1 * st1;
+        lo1 = lo1 + (int64_t)(c1 - 1) * st1 + 1;
+        if (c1 < 32 && pc < hi1) hi1 = pc;
+      }
+    }
+    if (s2) {
+      if (c2 == 0) { hi2 = lo2; done2 = true; }
+      else {
+        const int64_t pc = lo2 + (int64_t)c2 * st2;
+        lo2 = lo2 + (int64_t)(c2 - 1) * st2 + 1;
+        if (c2 < 32 && pc < hi2) hi2 = pc;
+      }
+    }
+  }
+  const int64_t p1 = lo1 + lane, p2 = lo2 + lane;
+  *r1 = lo1 + __popc(__ballot_sync(0xffffffffu, p1 < hi1 && a[p1] < x1));
+  *r2 = lo2 + __popc(__ballot_sync(0xffffffffu, p2 < hi2 && a[p2] < x2));
+}
+
 // lower_bound over the sorted g codes through the coarse bucket index: the
 // answer for x lies in [gidx[x >> gshift], gidx[(x >> gshift) + 1]].
 __device__ __forceinline__ int64_t g_lower_bound(const int64_t* G, int64_t ng, const int32_t* gidx,
@@ -194,6 +230,31 @@ __device__ __forceinline__ int64_t g_lower_bound(const int64_t* G, int64_t ng, c
     if (G[mid] < x) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// two g_lower_bound searches at once, their probes interleaved so that the
+// loads of both are in flight together
+__device__ __forceinline__ void g_lower_bound2(const int64_t* G, int64_t ng, const int32_t* gidx,
+                                               int64_t gidx_n, int gshift, int64_t x1, int64_t x2,
+                                               int64_t* r1, int64_t* r2) {
+  int64_t lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
+  if (x1 > 0) {
+    const int64_t b = x1 >> gshift;
+    if (b >= gidx_n) lo1 = hi1 = ng; else { lo1 = gidx[b]; hi1 = gidx[b + 1]; }
+  }
+  if (x2 > 0) {
+    const int64_t b = x2 >> gshift;
+    if (b >= gidx_n) lo2 = hi2 = ng; else { lo2 = gidx[b]; hi2 = gidx[b + 1]; }
+  }
+  while (lo1 < hi1 || lo2 < hi2) {
+    const int64_t m1 = (lo1 + hi1) >> 1, m2 = (lo2 + hi2) >> 1;
+    const bool a1 = lo1 < hi1, a2 = lo2 < hi2;
+    const int64_t v1 = a1 ? G[m1] : 0, v2 = a2 ? G[m2] : 0;
+    if (a1) { if (v1 < x1) lo1 = m1 + 1; else hi1 = m1; }
+    if (a2) { if (v2 < x2) lo2 = m2 + 1; else hi2 = m2; }
+  }
+  *r1 = lo1;
+  *r2 = lo2;
 }
 
 // q = x / d and *r = x % d for x >= 0, d >= 1: 32-bit division when x fits
