@@ -490,22 +490,23 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     Z.chunk_begin = A.chunk_begin;   // uploaded with phase B1's plan
   }
   std::vector<OpRef> all, bm, bt;
-  // large bitmap operands of a call with few of them: the cluster front end
-  // (encode, rank and gather by CL_CTAS CTAs each); the rest one CTA each
+  // large operands with key ranges of at most CL_MAX_BITS, in a call with
+  // few of them: the cluster front end (encode, rank and gather by CL_CTAS
+  // CTAs each); the rest: one CTA each (bitmap or bitonic) or the radix sort
   std::vector<OpRef> cl;
-  int nbitmap = 0;
+  int ncand = 0;
   int64_t cl_range = 0;
+  auto cluster_fit = [](const Operand& op) {
+    return op.sort_method == SORT_CLUSTER || (op.n >= CL_MIN_N && op.key_range <= CL_MAX_BITS);
+  };
   for (int q = 0; q < nlive; ++q)
-    for (int which = 0; which < 2; ++which) {
-      const Operand& op = which ? plans[live_ids[q]].p.g : plans[live_ids[q]].p.f;
-      nbitmap += op.sort_method == SORT_BITMAP || op.sort_method == SORT_CLUSTER;
-    }
+    for (int which = 0; which < 2; ++which)
+      ncand += cluster_fit(which ? plans[live_ids[q]].p.g : plans[live_ids[q]].p.f);
   for (int q = 0; q < nlive; ++q) {
     Prod& P = plans[live_ids[q]].p;
     for (int which = 0; which < 2; ++which) {
       Operand& op = which ? P.g : P.f;
-      if (op.sort_method == SORT_BITMAP && op.n >= CL_MIN_N && op.n <= CL_MAX_N && nbitmap <= CL_MAX_OPS)
-        op.sort_method = SORT_CLUSTER;
+      if (ncand <= CL_MAX_OPS && cluster_fit(op)) op.sort_method = SORT_CLUSTER;
       if (op.sort_method == SORT_CLUSTER) {
         cl.push_back(OpRef{q, which});
         cl_range = std::max(cl_range, op.key_range);

@@ -320,8 +320,8 @@ cudaError_t launch_gather(Prod* dprods, const OpRef* dops, int nops, cudaStream_
 // operand.  The operand's key range is cut into CL_CTAS slices; CTA r holds
 // slice r of the key bitmap and, per bitmap word, the number of set bits of
 // the slice before it, in its shared memory.  Term i belongs to thread
-// (i mod CL_CTAS * CL_THREADS) of the cluster, which holds at most CL_K terms
-// (the host sends larger operands elsewhere) in registers throughout.
+// (i mod CL_CTAS * CL_THREADS) of the cluster, which holds CL_K terms at a
+// time in registers (larger operands take several rounds).
 //   1. each thread encodes its terms (every load issued before any is used)
 //      and sets their bits in the owning CTA's slice (atomicOr through
 //      distributed shared memory; a bit already set is a repeated key);
@@ -357,30 +357,39 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
   if (tid == 0) s_drop = 0;
   cl.sync();   // every slice is clear before any thread of the cluster sets a bit
   const int64_t first = (int64_t)me * CL_THREADS + tid, stride = (int64_t)CL_CTAS * CL_THREADS;
+  const int64_t round = (int64_t)CL_K * stride;
+  // an operand of more than `round` terms takes several rounds, its keys
+  // kept in the sort-key array between the passes (each thread reads back
+  // only what it wrote); a smaller one keeps them in registers
+  const bool spill = n > round;
   uint64_t key[CL_K];
   uint32_t bad = 0;
   unsigned long long ndrop = 0;
+  for (int64_t base = first; base < n; base += round) {
 #pragma unroll
-  for (int k = 0; k < CL_K; ++k) {
-    const int64_t i = first + k * stride;
-    key[k] = 0;
-    if (i < n) {
-      TermCode tc = encode_term(P, O, i);
-      uint64_t kk = tc.drop ? (uint64_t)(O.sent + i) : term_key(P, tc);
-      if (!tc.bad && kk >= (uint64_t)R) tc.bad |= ST_RANGE;   // keeps the slice index in bounds
-      if (tc.bad) kk = 0;   // the status fails the product
-      bad |= tc.bad;
-      ndrop += tc.drop ? 1 : 0;
-      key[k] = kk;
+    for (int k = 0; k < CL_K; ++k) {
+      const int64_t i = base + k * stride;
+      key[k] = 0;
+      if (i < n) {
+        TermCode tc = encode_term(P, O, i);
+        uint64_t kk = tc.drop ? (uint64_t)(O.sent + i) : term_key(P, tc);
+        if (!tc.bad && kk >= (uint64_t)R) tc.bad |= ST_RANGE;   // keeps the slice index in bounds
+        if (tc.bad) kk = 0;   // the status fails the product
+        bad |= tc.bad;
+        ndrop += tc.drop ? 1 : 0;
+        key[k] = kk;
+      }
     }
-  }
 #pragma unroll
-  for (int k = 0; k < CL_K; ++k) {
-    if (first + k * stride < n) {
-      const unsigned owner = (unsigned)(key[k] / L);
-      const uint64_t off = key[k] - (uint64_t)owner * L;
-      const uint32_t bit = 1u << (off & 31);
-      if (atomicOr(cl.map_shared_rank(bits, owner) + (off >> 5), bit) & bit) bad |= ST_DUP;
+    for (int k = 0; k < CL_K; ++k) {
+      const int64_t i = base + k * stride;
+      if (i < n) {
+        const unsigned owner = (unsigned)(key[k] / L);
+        const uint64_t off = key[k] - (uint64_t)owner * L;
+        const uint32_t bit = 1u << (off & 31);
+        if (atomicOr(cl.map_shared_rank(bits, owner) + (off >> 5), bit) & bit) bad |= ST_DUP;
+        if (spill) O.skey[i] = key[k];
+      }
     }
   }
   cl.sync();   // every key's bit is set
@@ -439,36 +448,42 @@ __global__ void __cluster_dims__(CL_CTAS, 1, 1) __launch_bounds__(CL_THREADS)
     if (me == 0 && lane == 0) O.nkeep = n - (int64_t)d;
   }
   __syncthreads();
-  int64_t q[CL_K];
+  for (int64_t base = first; base < n; base += round) {
+    if (spill) {
 #pragma unroll
-  for (int k = 0; k < CL_K; ++k) {
-    q[k] = n;
-    if (first + k * stride < n) {
-      const unsigned owner = (unsigned)(key[k] / L);
-      const uint64_t off = key[k] - (uint64_t)owner * L;
-      const uint32_t wv = cl.map_shared_rank(bits, owner)[off >> 5];
-      const uint32_t pv = cl.map_shared_rank(pre, owner)[off >> 5];
-      q[k] = s_base[owner] + pv + __popc(wv & ((1u << (off & 31)) - 1u));
+      for (int k = 0; k < CL_K; ++k) key[k] = base + k * stride < n ? O.skey[base + k * stride] : 0;
     }
-  }
+    int64_t q[CL_K];
 #pragma unroll
-  for (int k = 0; k < CL_K; ++k) {
-    const int64_t i = first + k * stride;
-    if (i >= n) continue;
-    if (q[k] >= n) { bad |= ST_DUP; continue; }
-    if (P.nt == 0) {
-      O.code[q[k]] = (int64_t)key[k];
-      if (O.code32) O.code32[q[k]] = (int32_t)key[k];
-      if (P.f64) ((double*)O.coef)[q[k]] = ((const double*)O.c)[i];
-      else ((int64_t*)O.coef)[q[k]] = ((const int64_t*)O.c)[i];
-    } else {
-      TermCode tc = encode_term(P, O, i);
-      if (key[k] >= (uint64_t)O.sent) { tc.pcode = TRUNC_PSENT; tc.tcode = 0; tc.kind = 0; }
-      O.code[q[k]] = tc.pcode;
-      O.tcode[q[k]] = tc.tcode;
-      O.kind[q[k]] = (uint8_t)tc.kind;
-      const double c = ((const double*)O.c)[i];
-      ((double*)O.coef)[q[k]] = r.which == 0 ? 0.5 * c : c;   // the 1/2 of the product-to-sum identities
+    for (int k = 0; k < CL_K; ++k) {
+      q[k] = n;
+      if (base + k * stride < n) {
+        const unsigned owner = (unsigned)(key[k] / L);
+        const uint64_t off = key[k] - (uint64_t)owner * L;
+        const uint32_t wv = cl.map_shared_rank(bits, owner)[off >> 5];
+        const uint32_t pv = cl.map_shared_rank(pre, owner)[off >> 5];
+        q[k] = s_base[owner] + pv + __popc(wv & ((1u << (off & 31)) - 1u));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CL_K; ++k) {
+      const int64_t i = base + k * stride;
+      if (i >= n) continue;
+      if (q[k] >= n) { bad |= ST_DUP; continue; }
+      if (P.nt == 0) {
+        O.code[q[k]] = (int64_t)key[k];
+        if (O.code32) O.code32[q[k]] = (int32_t)key[k];
+        if (P.f64) ((double*)O.coef)[q[k]] = ((const double*)O.c)[i];
+        else ((int64_t*)O.coef)[q[k]] = ((const int64_t*)O.c)[i];
+      } else {
+        TermCode tc = encode_term(P, O, i);
+        if (key[k] >= (uint64_t)O.sent) { tc.pcode = TRUNC_PSENT; tc.tcode = 0; tc.kind = 0; }
+        O.code[q[k]] = tc.pcode;
+        O.tcode[q[k]] = tc.tcode;
+        O.kind[q[k]] = (uint8_t)tc.kind;
+        const double c = ((const double*)O.c)[i];
+        ((double*)O.coef)[q[k]] = r.which == 0 ? 0.5 * c : c;   // the 1/2 of the product-to-sum identities
+      }
     }
   }
   // the g bucket index of a dense product: gidx[b] = number of keys below

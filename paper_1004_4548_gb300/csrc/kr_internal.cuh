@@ -40,9 +40,11 @@ constexpr int SORT_CLUSTER = 4;  // bitmap over a cluster's shared memory: encod
 // operand's key bitmap (and per-word prefix counts) in its shared memory
 constexpr int CL_CTAS = 8;
 constexpr int CL_THREADS = 1024;
-constexpr int CL_K = 4;              // terms per thread at most
+constexpr int CL_K = 4;              // terms per thread and round
 constexpr int64_t CL_MIN_N = 2048;   // smaller operands keep the one-CTA bitmap sort
-constexpr int64_t CL_MAX_N = (int64_t)CL_CTAS * CL_THREADS * CL_K;
+// key ranges up to this many bits: a slice's bitmap and per-word prefix
+// counts (8 bytes per 32 keys) in at most 220 KB of shared memory per CTA
+constexpr int64_t CL_MAX_BITS = (int64_t)CL_CTAS * 28160 * 32;
 constexpr int CL_MAX_OPS = 64;       // more bitmap operands in a call: one CTA each
 __host__ __device__ inline int64_t cluster_slice_words(int64_t key_range) {
   const int64_t words = (key_range + 31) >> 5;

@@ -119,3 +119,43 @@ def test_graph_replay_with_cluster_front_end(kron, large):
                 assert_poly_equal(to_np(out[k]["exps"]), to_np(out[k]["coef"]), r, f"replay {it} product {k}")
     finally:
         pb.close()
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_operands_taking_several_rounds(kron, path):
+    # 40000 terms: more than one term per thread of the cluster and round, so the
+    # keys wait in the sort-key array between the passes
+    f = random_poly(3, 40000, 0, 60, 7301)
+    g = random_poly(3, 60, -5, 5, 7302)
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    ctx = kron.binding.Context()
+    ctx.set_profiling(True)
+    try:
+        ex, cf, _, _ = kron.poly_mul(dev(f.exps), dev(f.coef), dev(g.exps), dev(g.coef), ctx=ctx, path=path)
+        assert "front" in [n for n, _ in ctx.stages()]
+    finally:
+        ctx.close()
+    assert_poly_equal(to_np(ex), to_np(cf), r, f"several rounds path={path}")
+    # a repeated key found in the second round
+    exps = np.concatenate([f.exps, f.exps[:, 39990:39991]], axis=1)
+    coef = np.concatenate([f.coef, f.coef[:1]])
+    with pytest.raises(kron.KronError) as e:
+        kron.poly_mul(dev(exps), dev(coef), dev(g.exps), dev(g.coef), path=path)
+    assert e.value.status == kron.KR_ERR_DUP
+
+
+def test_fateman_operands_on_the_cluster_front_end(kron):
+    # Fateman's operands (46376 terms, key range 6.9e6 bits) are ranked by the
+    # cluster front end; the product of a slice of f with all of g is checked
+    from workloads import fateman
+    f, g = fateman()
+    fs = Poly(np.ascontiguousarray(f.exps[:, ::97]), np.ascontiguousarray(f.coef[::97]))
+    r = oracle.poly_mul(fs, g, nthreads=NT)
+    ctx = kron.binding.Context()
+    ctx.set_profiling(True)
+    try:
+        ex, cf, _, _ = kron.poly_mul(dev(fs.exps), dev(fs.coef), dev(g.exps), dev(g.coef), ctx=ctx)
+        assert "front" in [n for n, _ in ctx.stages()]
+    finally:
+        ctx.close()
+    assert_poly_equal(to_np(ex), to_np(cf), r, "Fateman slice")
