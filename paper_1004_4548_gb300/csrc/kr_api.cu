@@ -848,17 +848,53 @@ kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
     h->omax[P.gvar] = P.gvar_max;
   }
   if (n < 0) {
-    // deferred count (device outputs only): decode up to the capacity, read
-    // the count, then report it
-    ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->capacity, h->codes, s,
-                               true, ctx->res_val, (uint64_t*)h->coef),
-       "decode");
+    const bool exps_dev = !h->exps || is_device_ptr(h->exps);
+    const bool codes_dev = !h->codes || is_device_ptr(h->codes);
+    if (exps_dev && codes_dev && is_device_ptr(h->coef)) {
+      // deferred count, device outputs: decode up to the capacity, read the
+      // count, then report it
+      ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->capacity, h->codes, s,
+                                 true, ctx->res_val, (uint64_t*)h->coef),
+         "decode");
+      ctx->launches += 1;
+      mark(ctx, s, "decode");
+      const kr_status st = settle_deferred(ctx, s);
+      h->nterms = st == KR_OK ? ctx->res_n : 0;
+      if (st != KR_OK) return st;
+      return ctx->res_n > h->capacity ? KR_ERR_CAPACITY : KR_OK;
+    }
+    // deferred count, host outputs: decode into device scratch with room for
+    // every term the product can have (at most the capacity), read the count,
+    // then copy that many terms.  The scratch is the input arena: the decode
+    // runs after every kernel that reads the staged inputs, and a growth of
+    // the arena waits for the stream first.
+    const int64_t room = std::max<int64_t>(0, std::min<int64_t>(h->capacity, P.out_cap));
+    ensure(ctx, &ctx->in_arena, &ctx->in_cap, (size_t)room * (P.np * 4 + 8) + 1024, s);
+    Bump b(ctx->in_arena);
+    int32_t* exps_tmp = b.take<int32_t>(room * P.np);
+    int64_t* codes_tmp = b.take<int64_t>(room);
+    int32_t* ex = h->exps ? (exps_dev ? h->exps : exps_tmp) : nullptr;
+    int64_t* cd = h->codes ? (codes_dev ? h->codes : codes_tmp) : nullptr;
+    const int64_t ld = (h->exps && !exps_dev) ? room : h->capacity;
+    ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, room, ex, ld, cd, s, true), "decode");
     ctx->launches += 1;
     mark(ctx, s, "decode");
     const kr_status st = settle_deferred(ctx, s);
     h->nterms = st == KR_OK ? ctx->res_n : 0;
     if (st != KR_OK) return st;
-    return ctx->res_n > h->capacity ? KR_ERR_CAPACITY : KR_OK;
+    const int64_t m = ctx->res_n;
+    if (m > h->capacity) return KR_ERR_CAPACITY;
+    if (m > 0) {
+      if (h->exps && !exps_dev)
+        for (int k = 0; k < P.np; ++k)
+          copy_out(ctx, h->exps + (int64_t)k * h->capacity, exps_tmp + (int64_t)k * room, (size_t)m * 4, s);
+      if (h->codes && !codes_dev) copy_out(ctx, h->codes, codes_tmp, (size_t)m * 8, s);
+      copy_out(ctx, h->coef, ctx->res_val, (size_t)m * 8, s);
+      mark(ctx, s, "copy_out");
+      ck(ctx, cudaStreamSynchronize(s), "sync output");
+      collect_stages(ctx);
+    }
+    return KR_OK;
   }
   if (n > h->capacity) return KR_ERR_CAPACITY;
   if (n == 0) return KR_OK;
@@ -1201,9 +1237,9 @@ kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out*
     in.ge = g->exps; in.gc = g->coef; in.ng = g->nterms;
     if (opts) in.opts = *opts;
     std::vector<ProdResult> res;
-    // device outputs: the term count may stay on the device until the decode
-    ctx->allow_deferred = is_device_ptr(h->coef) && (!h->exps || is_device_ptr(h->exps)) &&
-                          (!h->codes || is_device_ptr(h->codes));
+    // the term count may stay on the device until the decode (host outputs:
+    // until the decode into scratch, whose terms are then copied)
+    ctx->allow_deferred = true;
     try {
       run_pipeline(ctx, {in}, s, res);
     } catch (...) {
