@@ -231,6 +231,10 @@ struct ChunkTable {
 #define KR_TILE_R 8
 #endif
 constexpr int TILE_R = KR_TILE_R;
+#ifndef KR_DENSE_Q
+#define KR_DENSE_Q 2
+#endif
+constexpr int DENSE_Q = KR_DENSE_Q;   // f terms examined per thread and table fill
 
 // Accumulate the pairs of one task into the shared slice acc[0, S).
 //
@@ -270,30 +274,12 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
   const T* __restrict__ CF = (const T*)P.f.coef;
   const T* __restrict__ CG = (const T*)P.g.coef;
   const int64_t ng = P.g.n;
-  for (int64_t ib = tk.i0; ib < tk.i1; ib += ACC_THREADS) {
-    const int64_t i = ib + threadIdx.x;
-    int32_t cnt = 0, l32 = 0, r = 0;
-    if (i < tk.i1) {
-      const int64_t fc = F[i];
-      // the offset of the next term too, so that the walk reads two per load
-      ct.fc[threadIdx.x] = make_int2((int32_t)(fc - B), C32 ? (int32_t)(int64_t)CF[i] : 0);
-      const bool owner = threadIdx.x == 0 || (fc >> sh) != (F[i - 1] >> sh) ||
-                         ((i - tk.i0) & (TILE_R - 1)) == 0;
-      if (owner) {
-        r = 1;
-        while (r < TILE_R && threadIdx.x + r < ACC_THREADS && i + r < tk.i1 &&
-               (F[i + r] >> sh) == (fc >> sh) && ((i + r - tk.i0) & (TILE_R - 1)) != 0)
-          ++r;
-        const int64_t l = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, B - F[i + r - 1]);
-        const int64_t h = g_lower_bound(G, ng, P.gidx, P.gidx_n, P.gshift, B + lim - fc);
-        l32 = (int32_t)l;
-        cnt = (int32_t)(h - l);
-      }
-    }
-    ct.lo[threadIdx.x] = l32;
-    ct.run[threadIdx.x] = (int16_t)r;
-    // block-wide exclusive scan of the window lengths
-    int32_t x = cnt;
+  const int32_t* __restrict__ GX = P.gidx;
+  const int64_t gn = P.gidx_n;
+  const int gsh = P.gshift;
+  // block-wide exclusive scan of one value per thread (ct.warp_sum as scratch)
+  auto block_scan = [&](int32_t v, int32_t& total) -> int32_t {
+    int32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int32_t y = __shfl_up_sync(FULL, x, o);
@@ -311,64 +297,144 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
       if (lane < NW) ct.warp_sum[lane] = w;   // inclusive over warps
     }
     __syncthreads();
-    const int32_t wbase = warp > 0 ? ct.warp_sum[warp - 1] : 0;
-    ct.excl[threadIdx.x] = wbase + x - cnt;
-    if (threadIdx.x == ACC_THREADS - 1) ct.excl[ACC_THREADS] = wbase + x;
-    __syncthreads();
-    const int32_t total = ct.excl[ACC_THREADS];
-    // this warp's share [pb, pe) of the flattened slots
-    const int32_t pb = (int32_t)(((int64_t)total * warp) / NW);
-    const int32_t pe = (int32_t)(((int64_t)total * (warp + 1)) / NW);
-    if (pb < pe) {
-      // k = the window of this lane's first slot (the last k with
-      // excl[k] <= p); p < excl[ACC_THREADS] keeps k + 1 <= ACC_THREADS below
-      int32_t p = pb + lane;
-      int k = 0, hi_k = ACC_THREADS;
+    const int32_t base = warp > 0 ? ct.warp_sum[warp - 1] : 0;
+    total = ct.warp_sum[NW - 1];
+    __syncthreads();   // the scratch is reused by the next scan
+    return base + x - v;
+  };
+  // The task's f terms are examined DENSE_Q * ACC_THREADS at a time: an f term
+  // whose g window in the block is empty (its bucket range holds no g code)
+  // takes no table entry, and the kept ones are packed into tables of
+  // ACC_THREADS entries (one or more rounds).
+  for (int64_t sb = tk.i0; sb < tk.i1; sb += (int64_t)ACC_THREADS * DENSE_Q) {
+    int64_t fv[DENSE_Q];
+    int32_t cv[DENSE_Q];
+    bool keep[DENSE_Q];
+    int32_t nk = 0;
+#pragma unroll
+    for (int q = 0; q < DENSE_Q; ++q) {
+      const int64_t i = sb + (int64_t)DENSE_Q * threadIdx.x + q;
+      fv[q] = 0;
+      cv[q] = 0;
+      if (i < tk.i1) {
+        fv[q] = F[i];
+        // the table keeps the int32 coefficient, or else the term's index
+        if constexpr (C32) cv[q] = (int32_t)(int64_t)CF[i];
+        else cv[q] = (int32_t)(i - tk.i0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < DENSE_Q; ++q) {
+      const int64_t i = sb + (int64_t)DENSE_Q * threadIdx.x + q;
+      keep[q] = false;
+      if (i < tk.i1) {
+        // the g codes in [x1, x2) pair with this term into the block; the
+        // bucket index bounds how many lie in the buckets covering that range
+        const int64_t x1 = B - fv[q], x2 = B + lim - fv[q];
+        int64_t below = 0, upto = 0;
+        if (x1 > 0) {
+          const int64_t bk = x1 >> gsh;
+          below = bk >= gn ? ng : GX[bk];
+        }
+        if (x2 > 0) {
+          const int64_t bk = (x2 - 1) >> gsh;
+          upto = bk >= gn ? ng : GX[bk + 1];
+        }
+        keep[q] = upto > below;
+      }
+      nk += keep[q] ? 1 : 0;
+    }
+    int32_t kept;
+    const int32_t pos0 = block_scan(nk, kept);
+    for (int32_t r0 = 0; r0 < kept; r0 += ACC_THREADS) {
       {
-        const int32_t ps = min(p, pe - 1);
-        while (hi_k - k > 1) {
-          const int mid = (k + hi_k) >> 1;
-          if (ct.excl[mid] <= ps) k = mid; else hi_k = mid;
+        int32_t p = pos0;
+#pragma unroll
+        for (int q = 0; q < DENSE_Q; ++q) {
+          if (keep[q]) {
+            if (p >= r0 && p < r0 + ACC_THREADS) ct.fc[p - r0] = make_int2((int32_t)(fv[q] - B), cv[q]);
+            ++p;
+          }
         }
       }
-      int32_t e0 = ct.excl[k], e1 = ct.excl[k + 1];
-      for (; p < pe; p += 32) {
-        while (p >= e1) {   // empty windows (non-owners) are skipped here too
-          ++k;
-          e0 = e1;
-          e1 = ct.excl[k + 1];
+      __syncthreads();   // the round's entries are in the table
+      const int nent = min(ACC_THREADS, kept - r0);
+      const int ent = threadIdx.x;
+      int32_t cnt = 0, l32 = 0, r = 0;
+      if (ent < nent) {
+        const int32_t off = ct.fc[ent].x;
+        const int32_t wid = off >> sh;   // floor: tiles stay within aligned windows of 2^sh codes
+        const bool owner = ent == 0 || wid != (ct.fc[ent - 1].x >> sh) || (ent & (TILE_R - 1)) == 0;
+        if (owner) {
+          r = 1;
+          while (r < TILE_R && ent + r < nent && (ct.fc[ent + r].x >> sh) == wid && ((ent + r) & (TILE_R - 1)) != 0)
+            ++r;
+          int64_t l, h;
+          g_lower_bound2(G, ng, GX, gn, gsh, -(int64_t)ct.fc[ent + r - 1].x, lim - off, &l, &h);
+          l32 = (int32_t)l;
+          cnt = (int32_t)(h - l);
         }
-        const int64_t j = (int64_t)ct.lo[k] + (p - e0);
-        const int32_t gc = G32 ? G32[j] : (int32_t)G[j];
-        const T cg = CG[j];
-        const int rk = ct.run[k];
-        const T* __restrict__ cf = CF + (ib + k);
+      }
+      ct.lo[ent] = l32;
+      ct.run[ent] = (int16_t)r;
+      int32_t wtotal;
+      ct.excl[ent] = block_scan(cnt, wtotal);
+      if (ent == 0) ct.excl[ACC_THREADS] = wtotal;
+      __syncthreads();
+      const int32_t total = ct.excl[ACC_THREADS];
+      // this warp's share [pb, pe) of the flattened slots
+      const int32_t pb = (int32_t)(((int64_t)total * warp) / NW);
+      const int32_t pe = (int32_t)(((int64_t)total * (warp + 1)) / NW);
+      if (pb < pe) {
+        // k = the window of this lane's first slot (the last k with
+        // excl[k] <= p); p < excl[ACC_THREADS] keeps k + 1 <= ACC_THREADS below
+        int32_t p = pb + lane;
+        int k = 0, hi_k = ACC_THREADS;
+        {
+          const int32_t ps = min(p, pe - 1);
+          while (hi_k - k > 1) {
+            const int mid = (k + hi_k) >> 1;
+            if (ct.excl[mid] <= ps) k = mid; else hi_k = mid;
+          }
+        }
+        int32_t e0 = ct.excl[k], e1 = ct.excl[k + 1];
+        for (; p < pe; p += 32) {
+          while (p >= e1) {   // empty windows (non-owners) are skipped here too
+            ++k;
+            e0 = e1;
+            e1 = ct.excl[k + 1];
+          }
+          const int64_t j = (int64_t)ct.lo[k] + (p - e0);
+          const int32_t gc = G32 ? G32[j] : (int32_t)G[j];
+          const T cg = CG[j];
+          const int rk = ct.run[k];
 #if KR_FULL_TILE_FAST
-        if (rk == TILE_R) {   // the common case: a full tile, the loop fully unrolled
+          if (rk == TILE_R) {   // the common case: a full tile, the loop fully unrolled
 #pragma unroll
-          for (int a = 0; a < TILE_R; ++a) {
+            for (int a = 0; a < TILE_R; ++a) {
+              const int2 e = ct.fc[k + a];
+              const int32_t off = e.x + gc;
+              if ((uint32_t)off < (uint32_t)S) {
+                if constexpr (C32) acc.add(off, (T)((int64_t)e.y * (int64_t)(int32_t)cg));
+                else acc.add(off, mul<T, C32>(CF[tk.i0 + e.y], cg));
+              }
+            }
+            continue;
+          }
+#endif
+#pragma unroll 4
+          for (int a = 0; a < rk; ++a) {
             const int2 e = ct.fc[k + a];
             const int32_t off = e.x + gc;
             if ((uint32_t)off < (uint32_t)S) {
               if constexpr (C32) acc.add(off, (T)((int64_t)e.y * (int64_t)(int32_t)cg));
-              else acc.add(off, mul<T, C32>(cf[a], cg));
+              else acc.add(off, mul<T, C32>(CF[tk.i0 + e.y], cg));
             }
-          }
-          continue;
-        }
-#endif
-#pragma unroll 4
-        for (int a = 0; a < rk; ++a) {
-          const int2 e = ct.fc[k + a];
-          const int32_t off = e.x + gc;
-          if ((uint32_t)off < (uint32_t)S) {
-            if constexpr (C32) acc.add(off, (T)((int64_t)e.y * (int64_t)(int32_t)cg));
-            else acc.add(off, mul<T, C32>(cf[a], cg));
           }
         }
       }
+      __syncthreads();   // the table is rewritten by the next round
     }
-    __syncthreads();   // the table is rewritten by the next chunk
   }
 }
 
