@@ -10,8 +10,9 @@
 // block is accumulated by one CTA in a shared-memory slice (atomic adds on
 // int64 or float64), then flushed to device memory once.  Heavy blocks are
 // split into several tasks over disjoint i-ranges; their flushes combine with
-// global atomic adds into a zeroed array.  Tasks are fetched dynamically by a
-// persistent grid.
+// global atomic adds into the array, which the planning kernel has cleared
+// for those blocks (a block with one task is written whole by its flush).
+// Tasks are fetched dynamically by a persistent grid.
 #include "kr_internal.cuh"
 
 namespace kr {
@@ -238,8 +239,10 @@ constexpr int DENSE_Q = KR_DENSE_Q;   // f terms examined per thread and table f
 
 // Accumulate the pairs of one task into the shared slice acc[0, S).
 //
-// The task's f terms are taken ACC_THREADS at a time.  The thread of the first
-// term of a tile (see TILE_R) finds the tile's exact g-window: the g terms
+// The task's f terms are examined DENSE_Q * ACC_THREADS at a time; those whose
+// g window in the block may hold a term (by the g bucket index) are packed
+// into tables of ACC_THREADS entries.  The thread of the first entry of a
+// tile (see TILE_R) finds the tile's exact g-window: the g terms
 // whose product with some term of the tile can land in the block.  A
 // block-wide prefix sum flattens the windows into one range of (tile, g term)
 // slots, cut into equal contiguous shares, one per warp, so that every warp
