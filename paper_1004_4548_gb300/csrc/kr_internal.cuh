@@ -163,27 +163,9 @@ __device__ __forceinline__ int64_t lower_bound_i64(const int64_t* a, int64_t n, 
   return lo;
 }
 
-// lower_bound by a whole warp (every lane calls it with the same arguments and
-// gets the answer): 32 probes per round cut the range 32-fold, so a search
-// costs a few dependent loads instead of log2(n)
-__device__ __forceinline__ int64_t warp_lower_bound(const int64_t* a, int64_t n, int64_t x) {
-  const int lane = threadIdx.x & 31;
-  int64_t lo = 0, hi = n;   // the answer lies in [lo, hi]
-  while (hi - lo > 32) {
-    const int64_t step = (hi - lo + 31) >> 5;
-    const int64_t p = lo + lane * step;
-    // sorted input: the probes below x are a prefix of the lanes
-    const int c = __popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
-    if (c == 0) return lo;
-    const int64_t pc = lo + (int64_t)c * step;
-    lo = lo + (int64_t)(c - 1) * step + 1;
-    if (c < 32 && pc < hi) hi = pc;
-  }
-  const int64_t p = lo + lane;
-  return lo + __popc(__ballot_sync(0xffffffffu, p < hi && a[p] < x));
-}
-
-// two lower_bounds over the same array by a whole warp, their rounds interleaved
+// two lower_bounds over the same sorted array by a whole warp (every lane calls
+// it with the same arguments and gets both answers): 32 probes per round cut
+// each range 32-fold, the two searches' rounds interleaved
 __device__ __forceinline__ void warp_lower_bound2(const int64_t* a, int64_t n, int64_t x1, int64_t x2,
                                                   int64_t* r1, int64_t* r2) {
   const int lane = threadIdx.x & 31;
@@ -219,23 +201,10 @@ __device__ __forceinline__ void warp_lower_bound2(const int64_t* a, int64_t n, i
   *r2 = lo2 + __popc(__ballot_sync(0xffffffffu, p2 < hi2 && a[p2] < x2));
 }
 
-// lower_bound over the sorted g codes through the coarse bucket index: the
-// answer for x lies in [gidx[x >> gshift], gidx[(x >> gshift) + 1]].
-__device__ __forceinline__ int64_t g_lower_bound(const int64_t* G, int64_t ng, const int32_t* gidx,
-                                                 int64_t gidx_n, int gshift, int64_t x) {
-  if (x <= 0) return 0;
-  const int64_t b = x >> gshift;
-  if (b >= gidx_n) return ng;
-  int64_t lo = gidx[b], hi = gidx[b + 1];
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (G[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-// two g_lower_bound searches at once, their probes interleaved so that the
-// loads of both are in flight together
+// two lower_bound searches over the sorted g codes at once, each through the
+// coarse bucket index (the answer for x lies in [gidx[x >> gshift],
+// gidx[(x >> gshift) + 1]]), their probes interleaved so that the loads of
+// both are in flight together
 __device__ __forceinline__ void g_lower_bound2(const int64_t* G, int64_t ng, const int32_t* gidx,
                                                int64_t gidx_n, int gshift, int64_t x1, int64_t x2,
                                                int64_t* r1, int64_t* r2) {
