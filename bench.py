@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-paths", action="store_true", help="skip the secondary hash/Poisson lines")
+    ap.add_argument("--paths", default="", help="comma-separated subset of the secondary lines (default: all)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiler runs)")
     ap.add_argument("--block-slots", type=int, default=0, help="dense output block size (0 = library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched / served measurements")
@@ -331,18 +332,36 @@ def main():
     # ---- secondary paths
     paths = {}
     if not args.no_paths:
+        want = set(args.paths.split(",")) if args.paths else None
+        sel = lambda name: want is None or name in want
         ctx.set_profiling(True)
-        paths["hash_cfg3"] = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert",
-                                       max(3, args.steps // 2))
-        f4, g4 = workload_cfg4()
-        paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3)
-        paths["poisson_cfg4_hash"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3,
-                                                  path=kron.KR_PATH_HASH)
+        if sel("hash_cfg3"):
+            paths["hash_cfg3"] = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert",
+                                           max(3, args.steps // 2))
+        if sel("poisson_cfg4") or sel("poisson_cfg4_hash"):
+            f4, g4 = workload_cfg4()
+            if sel("poisson_cfg4"):
+                paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3)
+            if sel("poisson_cfg4_hash"):
+                paths["poisson_cfg4_hash"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3,
+                                                          path=kron.KR_PATH_HASH)
         fa, ga = fateman()
-        paths["fateman_full"] = time_poly(kron, ctx, fa, ga, dev, stream, flush, "dense_accum", 5)
-        paths["fateman_full"]["context"] = ("Fateman's benchmark, (1+x+y+z+t)^30 times itself plus one, "
-                                            "true coefficients modulo 2^64; the paper's Table 5: 4.29 s "
-                                            "on one Core2Quad core with double coefficients")
+        if sel("fateman_full"):
+            paths["fateman_full"] = time_poly(kron, ctx, fa, ga, dev, stream, flush, "dense_accum", 5)
+            paths["fateman_full"]["context"] = ("Fateman's benchmark, (1+x+y+z+t)^30 times itself plus one, "
+                                                "true coefficients modulo 2^64; the paper's Table 5: 4.29 s "
+                                                "on one Core2Quad core with double coefficients")
+        if sel("fateman_truncated"):
+            # the same product truncated at total degree 30 (Sec. 3): only the pairs whose degrees
+            # add up to at most 30 are multiplied; the rate counts those pairs
+            paths["fateman_truncated"] = time_poly(kron, ctx, fa, ga, dev, stream, flush, "dense_accum", 5,
+                                                   units=kept_pairs(fa, ga, 30), trunc_degree=30)
+            paths["fateman_truncated"]["context"] = ("Fateman's product truncated at total degree 30: "
+                                                     "term-products counted over the kept pairs")
+        if sel("cfg2_windows4"):
+            # the headline product as 4 output key windows of equal sampled work, one call each
+            # (what 4 ranks of a split run compute), the sampling of the split included
+            paths["cfg2_windows4"] = time_windows(kron, ctx, f, g, dev, stream, flush, 4, max(3, args.steps // 2))
         ctx.set_profiling(False)
 
     batched = None
@@ -534,23 +553,61 @@ def time_batched(kron, ctx, dev, nprod):
     return res
 
 
-def time_poly(kron, ctx, f, g, dev, stream, flush, kernel, steps):
+def kept_pairs(f, g, N):
+    """Term pairs of f * g whose total degrees add up to at most N."""
+    df = np.bincount(f.exps.sum(axis=0) - f.exps.sum(axis=0).min())
+    dg = np.bincount(g.exps.sum(axis=0) - g.exps.sum(axis=0).min())
+    lo = int(f.exps.sum(axis=0).min() + g.exps.sum(axis=0).min())
+    conv = np.convolve(df.astype(np.float64), dg.astype(np.float64))
+    return int(round(conv[:max(0, N - lo + 1)].sum()))
+
+
+def time_windows(kron, ctx, f, g, dev, stream, flush, nparts, steps):
+    import torch
+    from paper_1004_4548_gb300 import shard
+    from workloads import Poly
+    F = Poly(torch.from_numpy(f.exps).to(dev), torch.from_numpy(f.coef).to(dev))
+    G = Poly(torch.from_numpy(g.exps).to(dev), torch.from_numpy(g.coef).to(dev))
+
+    def run():
+        cuts = shard.split_points(F, G, nparts, ctx=ctx)
+        return [shard.mul_window(F, G, a, b, ctx=ctx) for a, b in zip(cuts, cuts[1:])], cuts
+
+    parts, cuts = run()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        parts, cuts = run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    tp = f.n * g.n
+    ms = statistics.mean(times)
+    return {"value": tp / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "term_products": tp,
+            "output_terms": int(sum(p[1].shape[0] for p in parts)), "windows": nparts,
+            "window_terms": [int(p[1].shape[0]) for p in parts],
+            "context": "one product as key windows of equal sampled work, computed one after another"}
+
+
+def time_poly(kron, ctx, f, g, dev, stream, flush, kernel, steps, units=None, **opts):
     import torch
     fe, fc = torch.from_numpy(f.exps).to(dev), torch.from_numpy(f.coef).to(dev)
     ge, gc = torch.from_numpy(g.exps).to(dev), torch.from_numpy(g.coef).to(dev)
     for _ in range(2):
-        ex, cf, _, _ = kron.poly_mul(fe, fc, ge, gc, ctx=ctx)
+        ex, cf, _, _ = kron.poly_mul(fe, fc, ge, gc, ctx=ctx, **opts)
     times, kt = [], []
     for _ in range(steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ex, cf, _, _ = kron.poly_mul(fe, fc, ge, gc, ctx=ctx)
+        ex, cf, _, _ = kron.poly_mul(fe, fc, ge, gc, ctx=ctx, **opts)
         b.record(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
         kt.extend(ms for n, ms in ctx.stages() if n == kernel)
-    tp = f.n * g.n
+    tp = f.n * g.n if units is None else units
     ms = statistics.mean(times)
     kms = statistics.mean(kt)
     return {"value": tp / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "term_products": tp,
