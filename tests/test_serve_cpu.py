@@ -81,3 +81,69 @@ def test_batch_failing_twice_reports_its_requests(monkeypatch):
     assert failed and all(any(x is r for x in reqs) for r in failed)
     assert st.completed + st.extra["failed"] == 40
     assert all(r.done >= 0 for r in reqs)
+
+
+def _recording_batch(log: list, lock, active: list, delay=0.0005):
+    """A fake library call that records every batch (its requests' term-product
+    counts and how many batches ran at the same time) and answers each product
+    with its own pair count, so that results can be matched to requests."""
+    import time
+
+    def run(pairs, ctx=None, stream=None, wave_pairs=0):
+        with lock:
+            active[0] += 1
+            log.append(([f.coef.shape[0] * g.coef.shape[0] for f, g in pairs], active[0]))
+        time.sleep(delay)
+        with lock:
+            active[0] -= 1
+        return [{"status": 0, "nterms": int(f.coef.shape[0] * g.coef.shape[0]),
+                 "coef": torch.ones(1)} for f, g in pairs]
+    return run
+
+
+def _mixed_requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        m = int(rng.choice([2, 5, 20, 900]))
+        f = Poly(np.zeros((1, m), np.int32), np.ones(m, np.int64))
+        g = Poly(np.zeros((1, m), np.int32), np.ones(m, np.int64))
+        reqs.append(serve.Request(f, g, arrival=0.0002 * i))
+    return reqs
+
+
+def test_giants_run_alone_and_results_match_requests(monkeypatch):
+    monkeypatch.setattr(serve, "_Worker", _FakeWorker)
+    log, lock, active = [], threading.Lock(), [0]
+    monkeypatch.setattr(B, "kron_mul_batch", _recording_batch(log, lock, active))
+    srv = serve.Server(workers=2, giant=500_000)   # 900 x 900 = 810,000 pairs: a giant
+    reqs = _mixed_requests(120)
+    st = srv.run(reqs, time_limit=60)
+    assert st.completed == 120 and st.extra["failed"] == 0
+    for sizes, concurrent in log:
+        if any(p > 500_000 for p in sizes):
+            assert len(sizes) == 1 and concurrent == 1, (sizes, concurrent)
+    assert sum(len(s) for s, _ in log) == 120
+    for r in reqs:
+        assert r.status == 0 and r.result["nterms"] == r.pairs
+
+
+def test_batches_respect_the_work_and_memory_caps(monkeypatch):
+    monkeypatch.setattr(serve, "_Worker", _FakeWorker)
+    log, lock, active = [], threading.Lock(), [0]
+    monkeypatch.setattr(B, "kron_mul_batch", _recording_batch(log, lock, active, delay=0.002))
+    work_cap, budget = 1000.0, 5e6
+    srv = serve.Server(workers=2, giant=1e12, work_cap=work_cap, mem_budget=budget, max_batch=8)
+    reqs = [serve.Request(Poly(np.zeros((1, m), np.int32), np.ones(m, np.int64)),
+                          Poly(np.zeros((1, m), np.int32), np.ones(m, np.int64)), arrival=0.0)
+            for m in [5] * 40 + [20] * 10]
+    st = srv.run(reqs, time_limit=60)
+    assert st.completed == 50
+    for sizes, _ in log:
+        assert len(sizes) <= 8
+        if len(sizes) > 1:
+            assert sum(sizes) <= work_cap
+    # a 5 MB budget admits at most four requests of the 1 MB-plus prediction at once
+    assert max(len(s) for s, _ in log) <= 4
+    # arrival order is kept among requests that fit: the first batch starts with the oldest
+    assert log[0][0][0] == 25
