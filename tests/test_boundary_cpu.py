@@ -92,3 +92,35 @@ def test_fateman_density_matches_paper():
     c, W = kron.kron_plan([0] * 4, [60] * 4)
     assert W == 61 ** 4
     assert 290 < W / rows.shape[0] < 310
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Every structure the binding passes across the C ABI has the header's
+    size and field offsets (a C program built against include/kron.h prints
+    them; a field name missing from the header fails its build)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [binding.kr_poly, binding.kr_poly_out, binding.kr_pseries, binding.kr_pseries_out,
+               binding.kr_opts, binding.kr_job, binding.kr_result]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "kron.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for fname, _ in st._fields_:
+            lines.append(f'  printf("{n}.{fname} %zu\\n", offsetof({n}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for fname, _ in st._fields_:
+            assert int(got[f"{n}.{fname}"]) == getattr(st, fname).offset, f"{n}.{fname}"
