@@ -75,6 +75,10 @@ struct AccI {
   unsigned __int128 s = 0;   // wrapping 128-bit sum of exact products
 };
 
+#ifndef ORC_PLANT
+#define ORC_PLANT 0   // 0 = the oracle; k > 0 plants mistake k (mutation tests only)
+#endif
+
 struct AccF {
   double s = 0.0, comp = 0.0, mass = 0.0;
   void add(double x) {
@@ -83,13 +87,25 @@ struct AccF {
     if ((s >= 0 ? s : -s) >= (x >= 0 ? x : -x)) comp += (s - t) + x;
     else comp += (x - t) + s;
     s = t;
+#if ORC_PLANT == 9
+    mass += 2 * (x >= 0 ? x : -x);   // planted: every contribution counted twice in the mass
+#else
     mass += (x >= 0 ? x : -x);
+#endif
   }
+  // adds another thread's partial sum of the same key: its running sum and
+  // its compensation are two more contributions; the masses add
   void merge(const AccF& o) {
     double m = mass;
+#if ORC_PLANT != 8
     add(o.s);
+#endif
     add(o.comp);
+#if ORC_PLANT == 10
+    mass = m;   // planted: the other thread's mass dropped
+#else
     mass = m + o.mass;
+#endif
   }
   double value() const { return s + comp; }
 };
@@ -168,10 +184,6 @@ bool above_bound(const Trunc& T, const int32_t* poly, int np) {
 #endif
   return d > T.N;
 }
-
-#ifndef ORC_PLANT
-#define ORC_PLANT 0   // 0 = the oracle; k > 0 plants mistake k (mutation tests only)
-#endif
 
 // ---------------------------------------------------------------------------
 // polynomial product

@@ -26,8 +26,15 @@ NT = max(1, min(16, os.cpu_count() or 1))
 # pins as functions (plant = which oracle build to check)
 # ---------------------------------------------------------------------------
 
+# thread counts every multi-threaded pin runs with: one thread takes no merge,
+# three and four split f unevenly and merge the partial maps
+THREADS = (1, 3, 4)
+
+
 def pin_bruteforce(plant=0):
-    """Small random Laurent polynomials: oracle == dense N-d convolution."""
+    """Small random Laurent polynomials: oracle == dense N-d convolution, on one
+    thread and with the f terms split over three and four threads (the float64
+    partial sums then go through the merge)."""
     errs = []
     cases = [(1, 12, -5, 6), (2, 40, -3, 4), (3, 60, [-2, 0, -4], [3, 4, 1]),
              (3, 80, 0, 5)]
@@ -35,28 +42,73 @@ def pin_bruteforce(plant=0):
         for dt in ("i64", "f64"):
             f = random_poly(v, n, lo, hi, 100 + s, dt)
             g = random_poly(v, n + 7, lo, hi, 200 + s, dt)
-            r = oracle.poly_mul(f, g, plant=plant)
-            got = as_dict(r.exps, r.coef)
             want = box_convolution(f, g)
-            if dt == "i64":
-                if got != {k: int(x) for k, x in want.items()}:
-                    errs.append(f"bruteforce mismatch v={v} {dt}")
-            else:
-                keys = set(got) | set(want)
-                bad = [k for k in keys
-                       if abs(got.get(k, 0.0) - want.get(k, 0.0)) > 1e-12 * 16 * n]
-                if bad:
-                    errs.append(f"bruteforce mismatch v={v} {dt}: {len(bad)} keys")
+            for nt in THREADS:
+                r = oracle.poly_mul(f, g, nthreads=nt, plant=plant)
+                got = as_dict(r.exps, r.coef)
+                if dt == "i64":
+                    if got != {k: int(x) for k, x in want.items()}:
+                        errs.append(f"bruteforce mismatch v={v} {dt} threads={nt}")
+                else:
+                    keys = set(got) | set(want)
+                    bad = [k for k in keys
+                           if abs(got.get(k, 0.0) - want.get(k, 0.0)) > 1e-12 * 16 * n]
+                    if bad:
+                        errs.append(f"bruteforce mismatch v={v} {dt} threads={nt}: {len(bad)} keys")
     return errs
 
 
-def pin_werner(plant=0):
-    """Single-term Poisson products against the product-to-sum identities (Eq. 6, with 1/2)."""
+def pin_mass(plant=0):
+    """The per-key mass (sum of |contribution|), the basis of the float64
+    tolerance, equals its exact value.
+
+    * Polynomials: the mass of f*g is the product of |f| and |g|, computed
+      here by dense N-d convolution (a different algorithm), on one thread
+      and on three and four (the masses of the partial maps add).
+    * Poisson series: every pair of terms emits two terms of magnitude
+      |C D| / 2 (Eq. 6 with the 1/2 of the identities), so each hand-worked
+      single-term case has mass 3 per emitted term (C D = 6), 6 where both
+      terms land on one key; and in 2 cos 3y - 2 cos y times 3 cos y the two
+      contributions to cos 2y cancel (coefficient 0, mass 6).
+    """
     errs = []
-    C, D = 2.0, 3.0
-    # (f trig, f kind, g trig, g kind, expected [(trig, kind, coef)]) with 2 trig vars.
-    # x exponents: f has x^-1, g has x^3; the product always carries x^2.
-    cases = [
+    for s, (v, n, lo, hi) in enumerate([(2, 60, -3, 4), (3, 90, [-2, 0, -4], [3, 4, 1])]):
+        f = random_poly(v, n, lo, hi, 2100 + s, "f64")
+        g = random_poly(v, n + 9, lo, hi, 2200 + s, "f64")
+        want = box_convolution(Poly(f.exps, np.abs(f.coef)), Poly(g.exps, np.abs(g.coef)))
+        for nt in THREADS:
+            r = oracle.poly_mul(f, g, nthreads=nt, plant=plant, keep_zero=True)
+            got = as_dict(r.exps, r.mass)
+            if set(got) != set(want) or any(abs(got[k] - want[k]) > 1e-13 * want[k] for k in want):
+                errs.append(f"polynomial mass differs from the |f| |g| convolution v={v} threads={nt}")
+    for tf, kf, tg, kg, terms in WERNER_CASES:
+        f = PSeries(np.array([[-1]], np.int32), np.array(tf, np.int32)[:, None],
+                    np.array([kf], np.uint8), np.array([2.0]))
+        g = PSeries(np.array([[3]], np.int32), np.array(tg, np.int32)[:, None],
+                    np.array([kg], np.uint8), np.array([3.0]))
+        r = oracle.poisson_mul(f, g, plant=plant)
+        got = sorted((tuple(int(x) for x in r.trig[:, i]), int(r.kind[i]), float(r.mass[i]))
+                     for i in range(r.coef.shape[0]))
+        want = sorted((t, k, abs(c)) for t, k, c in terms)   # no contribution cancels here
+        if got != want:
+            errs.append(f"werner mass {tf},{kf} x {tg},{kg}: got {got}, want {want}")
+    f = PSeries(np.zeros((1, 2), np.int32), np.array([[3, 1]], np.int32), np.zeros(2, np.uint8),
+                np.array([2.0, -2.0]))
+    g = PSeries(np.zeros((1, 1), np.int32), np.array([[1]], np.int32), np.zeros(1, np.uint8),
+                np.array([3.0]))
+    for nt in (1, 2):
+        r = oracle.poisson_mul(f, g, nthreads=nt, plant=plant, keep_zero=True)
+        got = {int(r.trig[0, i]): (float(r.coef[i]), float(r.mass[i])) for i in range(r.coef.shape[0])}
+        if got != {0: (-3.0, 3.0), 2: (0.0, 6.0), 4: (3.0, 3.0)}:
+            errs.append(f"cancelling Poisson mass threads={nt}: {got}")
+    return errs
+
+
+# Single-term Poisson products worked by hand from the product-to-sum
+# identities (Eq. 6 with the factor 1/2), C = 2, D = 3:
+# (f trig, f kind, g trig, g kind, expected [(trig, kind, coef)]) with 2 trig
+# vars.  x exponents: f has x^-1, g has x^3; the product always carries x^2.
+WERNER_CASES = [
         ((1, 1), 0, (0, 1), 0, [((1, 0), 0, 3.0), ((1, 2), 0, 3.0)]),           # cos cos
         ((1, 1), 0, (0, 1), 1, [((1, 2), 1, 3.0), ((1, 0), 1, -3.0)]),          # cos sin
         ((1, 1), 1, (0, 1), 0, [((1, 2), 1, 3.0), ((1, 0), 1, 3.0)]),           # sin cos
@@ -71,8 +123,14 @@ def pin_werner(plant=0):
         ((1, 0), 0, (1, 0), 0, [((0, 0), 0, 3.0), ((2, 0), 0, 3.0)]),
         ((1, 1), 0, (0, 0), 0, [((1, 1), 0, 6.0)]),                             # t_g = 0: C*D
         ((1, 0), 1, (0, 0), 0, [((1, 0), 1, 6.0)]),
-    ]
-    for tf, kf, tg, kg, want in cases:
+]
+
+
+def pin_werner(plant=0):
+    """Single-term Poisson products against the product-to-sum identities (Eq. 6, with 1/2)."""
+    errs = []
+    C, D = 2.0, 3.0
+    for tf, kf, tg, kg, want in WERNER_CASES:
         f = PSeries(np.array([[-1]], np.int32), np.array(tf, np.int32)[:, None],
                     np.array([kf], np.uint8), np.array([C]))
         g = PSeries(np.array([[3]], np.int32), np.array(tg, np.int32)[:, None],
@@ -92,16 +150,17 @@ def pin_random_angles(plant=0):
     for s, (np_, nt, n) in enumerate([(1, 1, 20), (2, 3, 60), (3, 4, 150)]):
         f = random_pseries(np_, nt, n, 3, 4, 300 + s)
         g = random_pseries(np_, nt, n + 11, 3, 4, 400 + s)
-        h = oracle.poisson_mul(f, g, plant=plant)
-        H = PSeries(h.exps, h.trig, h.kind, h.coef)
-        for _ in range(4):
-            x = 0.5 + rng.uniform(np_)
-            y = 2 * math.pi * rng.uniform(nt)
-            fv, fm = eval_pseries(f, x, y)
-            gv, gm = eval_pseries(g, x, y)
-            hv, _ = eval_pseries(H, x, y)
-            if abs(fv * gv - hv) > 1e-12 * fm * gm:
-                errs.append(f"random angles np={np_} nt={nt}: {fv * gv} vs {hv}")
+        pts = [(0.5 + rng.uniform(np_), 2 * math.pi * rng.uniform(nt)) for _ in range(4)]
+        for nth in THREADS:
+            h = oracle.poisson_mul(f, g, nthreads=nth, plant=plant)
+            H = PSeries(h.exps, h.trig, h.kind, h.coef)
+            for x, y in pts:
+                fv, fm = eval_pseries(f, x, y)
+                gv, gm = eval_pseries(g, x, y)
+                hv, _ = eval_pseries(H, x, y)
+                if abs(fv * gv - hv) > 1e-12 * fm * gm:
+                    errs.append(f"random angles np={np_} nt={nt} threads={nth}: {fv * gv} vs {hv}")
+                    break
     return errs
 
 
@@ -164,6 +223,10 @@ def test_oracle_werner_single_terms():
 
 def test_oracle_random_angles():
     assert pin_random_angles() == []
+
+
+def test_oracle_mass_exact():
+    assert pin_mass() == []
 
 
 def test_oracle_canonical_output():
@@ -354,11 +417,15 @@ PLANTS = {
     5: "last term of g skipped",
     6: "first exponent of f used twice",
     7: "degree bound applied as < N instead of <= N",
+    8: "thread merge drops the other thread's running sum",
+    9: "mass counts every contribution twice",
+    10: "thread merge drops the other thread's mass",
 }
 
 
 @pytest.mark.parametrize("plant", sorted(PLANTS))
 def test_planted_mistake_is_caught(plant):
     caught = (pin_werner(plant) + pin_canonical(plant) + pin_random_angles(plant)
-              + pin_bruteforce(plant) + pin_mod_p(plant) + pin_truncation(plant))
+              + pin_bruteforce(plant) + pin_mod_p(plant) + pin_truncation(plant)
+              + pin_mass(plant))
     assert caught, f"planted mistake {plant} ({PLANTS[plant]}) escaped every pin"
