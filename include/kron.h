@@ -328,8 +328,8 @@ kr_status kron_fetch_pseries(kr_ctx* ctx, kr_pseries_out* h, kr_stream stream);
  * synchronisation that an allocation or a free brings.
  *
  * Computes out[c] = sum over pairs with fcode[i] + gcode[j] = c of
- * fcoef[i] * gcoef[j] for c in [0, W): the dense distributed product of
- * Sec. 3.1, with the same kernels as poly_mul's dense path.
+ * fcoef[i] * gcoef[j] for c in [0, W), with the same planning and
+ * accumulation kernels as poly_mul's dense path.
  *   fcode, gcode: device int64 [nf], [ng]: Kronecker codes of both operands in
  *     the product's box (each operand offset by its own minimum, as poly_mul
  *     codes them), ascending, without repeats, with fcode[i] + gcode[j] < W.
@@ -343,8 +343,10 @@ kr_status kron_fetch_pseries(kr_ctx* ctx, kr_pseries_out* h, kr_stream stream);
  * before any stream capture.  Every call uses the same array and leaves its
  * contents behind; the call clears what must start at zero.  Calls whose work
  * overlaps on the GPU (other streams, other host threads) race on the array:
- * order them.  Asynchronous on `stream`; inputs with violated preconditions
- * give a wrong product but no access outside the caller's buffers. */
+ * order them.  Asynchronous on `stream`.  The preconditions on the codes
+ * (ascending, without repeats, in [0, W), largest pair sum below W) are
+ * checked on the device; inputs that break them leave out all zeros, and no
+ * kernel reads or writes outside the caller's buffers. */
 kr_status kron_dense_product_static(const int64_t* fcode, const void* fcoef, int64_t nf,
                                     const int64_t* gcode, const void* gcoef, int64_t ng,
                                     kr_coef_t type, int64_t W, void* out, kr_stream stream);

@@ -409,9 +409,22 @@ def kron_dense_product_static(fcode, fcoef, gcode, gcoef, W: int, out=None, stre
     """
     L = load()
     torch = _torch()
-    is_f64 = fcoef.dtype == torch.float64
+    if fcoef.dtype not in (torch.int64, torch.float64) or gcoef.dtype != fcoef.dtype:
+        raise ValueError("fcoef and gcoef must both be int64 or both float64")
+    if fcode.dtype != torch.int64 or gcode.dtype != torch.int64:
+        raise ValueError("codes must be int64")
+    if fcode.shape[0] != fcoef.shape[0] or gcode.shape[0] != gcoef.shape[0]:
+        raise ValueError("each operand needs one coefficient per code")
     if out is None:
         out = torch.empty((W,), dtype=fcoef.dtype, device=fcoef.device)
+    if out.dtype != fcoef.dtype or out.numel() < W:
+        raise ValueError(f"out must hold at least W = {W} elements of the coefficient type")
+    ts = (fcode, fcoef, gcode, gcoef, out)
+    if any(not t.is_cuda or t.device != fcoef.device for t in ts):
+        raise ValueError("every array must be a CUDA tensor on one device")
+    if any(t.dim() != 1 or not t.is_contiguous() for t in ts):
+        raise ValueError("every array must be one-dimensional and contiguous")
+    is_f64 = fcoef.dtype == torch.float64
     st = L.kron_dense_product_static(fcode.data_ptr(), fcoef.data_ptr(), int(fcode.shape[0]),
                                      gcode.data_ptr(), gcoef.data_ptr(), int(gcode.shape[0]),
                                      KR_F64 if is_f64 else KR_I64, int(W), out.data_ptr(),

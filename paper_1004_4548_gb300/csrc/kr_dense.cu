@@ -116,7 +116,8 @@ cudaError_t launch_dense_plan(const Prod* dprods, const int32_t* ddense_prods,
 // Bucket index over the sorted g codes of every dense product: bucket b
 // covers codes [b << gshift, (b + 1) << gshift); gidx[b] = lower_bound(b << gshift).
 // Each j writes the buckets whose lower bound it is; the buckets after the
-// last code get ng.
+// last code get ng.  Both ends are clamped to [0, gidx_n], so codes outside
+// [0, W) (a caller's broken precondition) never index outside the array.
 __global__ void __launch_bounds__(256) k_build_gindex(const Prod* __restrict__ prods,
                                                      const int32_t* __restrict__ dense_prods) {
   const Prod& P = prods[dense_prods[blockIdx.y]];
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256) k_build_gindex(const Prod* __restrict__ p
   const int sh = P.gshift;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= ng;
        j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t blo = j == 0 ? 0 : (G[j - 1] >> sh) + 1;
+    const int64_t blo = j == 0 ? 0 : max((G[j - 1] >> sh) + 1, (int64_t)0);
     const int64_t bhi = j == ng ? P.gidx_n : min(G[j] >> sh, P.gidx_n);
     for (int64_t b = blo; b <= bhi; ++b) P.gidx[b] = (int32_t)j;
   }

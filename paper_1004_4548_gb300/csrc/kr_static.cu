@@ -46,6 +46,46 @@ static cudaError_t static_scratch(int device, unsigned char** out) {
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+struct StaticSmall {
+  int32_t ids[2];
+  int64_t block_begin[2];
+};
+
+// Stores the product descriptor and the planner's product list into the
+// scratch array and clears the two task counters.  The descriptor travels as a
+// kernel parameter (copied by value at launch), so nothing on the host stack
+// has to outlive the call.
+__global__ void k_static_setup(const Prod P, const StaticSmall small, Prod* __restrict__ dprod,
+                               StaticSmall* __restrict__ dsmall, int64_t* __restrict__ dcnt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *dprod = P;
+    *dsmall = small;
+    dcnt[0] = 0;
+    dcnt[1] = 0;
+  }
+}
+
+// Checks the entry's preconditions on the device: both code arrays strictly
+// ascending, inside [0, W), and the largest pair sum below W.  A violation
+// marks the product invalid; the planner then makes no task and clears every
+// block, so the output is all zeros and no kernel reads past the caller's
+// arrays.
+__global__ void __launch_bounds__(256) k_static_check(Prod* __restrict__ dprod, int64_t W) {
+  const int64_t* F = dprod->f.code;
+  const int64_t* G = dprod->g.code;
+  const int64_t nf = dprod->f.n, ng = dprod->g.n;
+  bool bad = false;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nf + ng;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t* A = q < nf ? F : G;
+    const int64_t i = q < nf ? q : q - nf;
+    const int64_t c = A[i];
+    bad |= c < 0 || c >= W || (i > 0 && A[i - 1] >= c);
+    if (q == 0) bad |= F[nf - 1] + G[ng - 1] >= W;   // both < W <= 2^24 here: no overflow
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&dprod->status, ST_INVALID);
+}
+
 }  // namespace kr
 
 using namespace kr;
@@ -62,9 +102,14 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
   if (cudaGetDevice(&device) != cudaSuccess) { cudaGetLastError(); return KR_ERR_CUDA; }
   unsigned char* base = nullptr;
   if (static_scratch(device, &base) != cudaSuccess) { cudaGetLastError(); return KR_ERR_CUDA; }
-  // the product array starts at zero: blocks with several tasks add into it
-  if (cudaMemsetAsync(out, 0, (size_t)W * 8, s) != cudaSuccess) { cudaGetLastError(); return KR_ERR_CUDA; }
-  if (nf == 0 || ng == 0) return KR_OK;
+  if (nf == 0 || ng == 0) {
+    // no pair: the product is zero everywhere
+    if (cudaMemsetAsync(out, 0, (size_t)W * 8, s) != cudaSuccess) { cudaGetLastError(); return KR_ERR_CUDA; }
+    return KR_OK;
+  }
+  // Otherwise no clearing is needed: the planner clears every block that
+  // several tasks (or none) add into, and a block with one task is written
+  // whole by its flush.
 
   const int64_t S = std::min<int64_t>(STATIC_BLOCK, (W + 31) / 32 * 32);
   const int64_t nblocks = (W + S - 1) / S;
@@ -75,7 +120,7 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
   const int64_t gidx_n = (W >> gsh) + 1;
   // layout: [Prod][ids, block_begin][counters][g index][tasks]
   const size_t off_ids = align256(sizeof(Prod));
-  const size_t off_cnt = off_ids + 256;
+  const size_t off_cnt = off_ids + align256(sizeof(StaticSmall));
   const size_t off_gidx = off_cnt + 256;
   const size_t off_tasks = off_gidx + align256((size_t)(gidx_n + 1) * sizeof(int32_t));
   const size_t need = off_tasks + (size_t)task_cap * sizeof(DenseTask);
@@ -108,29 +153,23 @@ extern "C" kr_status kron_dense_product_static(const int64_t* fcode, const void*
   P.gidx = (int32_t*)(base + off_gidx);
   P.gidx_n = gidx_n;
   P.gshift = gsh;
-  struct Small {
-    int32_t ids[2];
-    int64_t block_begin[2];
-  } small{};
+  StaticSmall small{};
   small.ids[0] = 0;
   small.block_begin[0] = 0;
   small.block_begin[1] = nblocks;
 
   Prod* dprod = (Prod*)base;
-  int32_t* dids = (int32_t*)(base + off_ids);
-  int64_t* dbb = (int64_t*)(base + off_ids + offsetof(Small, block_begin));
+  StaticSmall* dsmall = (StaticSmall*)(base + off_ids);
   int64_t* dcnt = (int64_t*)(base + off_cnt);
   DenseTask* dtasks = (DenseTask*)(base + off_tasks);
-  // host sources are pageable stack objects: the copies finish staging them
-  // before returning, and the stream orders them before the kernels
-  if (cudaMemcpyAsync(dprod, &P, sizeof(Prod), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(dids, &small, sizeof(Small), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemsetAsync(dcnt, 0, 2 * sizeof(int64_t), s) != cudaSuccess) {
-    cudaGetLastError();
-    return KR_ERR_CUDA;
-  }
-  if (launch_build_gindex(dprod, dids, 1, ng, s) != cudaSuccess ||
-      launch_dense_plan(dprod, dids, dbb, 1, nblocks, dtasks, task_cap, dcnt, s) != cudaSuccess) {
+  k_static_setup<<<1, 32, 0, s>>>(P, small, dprod, dsmall, dcnt);
+  if (cudaGetLastError() != cudaSuccess) return KR_ERR_CUDA;
+  const int64_t check_blocks = std::min<int64_t>((nf + ng + 255) / 256, 4 * (int64_t)sms);
+  k_static_check<<<(unsigned)check_blocks, 256, 0, s>>>(dprod, W);
+  if (cudaGetLastError() != cudaSuccess) return KR_ERR_CUDA;
+  if (launch_build_gindex(dprod, dsmall->ids, 1, ng, s) != cudaSuccess ||
+      launch_dense_plan(dprod, dsmall->ids, dsmall->block_begin, 1, nblocks, dtasks, task_cap, dcnt, s) !=
+          cudaSuccess) {
     cudaGetLastError();
     return KR_ERR_CUDA;
   }
