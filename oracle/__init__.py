@@ -53,6 +53,10 @@ def _lib(plant: int = 0) -> ctypes.CDLL:
             L.orc_poly_mul_trunc.argtypes = L.orc_poly_mul.argtypes + [u32, i64]
             L.orc_poisson_mul_trunc.restype = vp
             L.orc_poisson_mul_trunc.argtypes = L.orc_poisson_mul.argtypes + [u32, i64]
+            L.orc_poly_mul_tr.restype = vp
+            L.orc_poly_mul_tr.argtypes = L.orc_poly_mul.argtypes + [ctypes.POINTER(OrcTrunc)]
+            L.orc_poisson_mul_tr.restype = vp
+            L.orc_poisson_mul_tr.argtypes = L.orc_poisson_mul.argtypes + [ctypes.POINTER(OrcTrunc)]
             L.orc_result_nterms.restype = i64
             L.orc_result_nterms.argtypes = [vp]
             L.orc_result_overflow.restype = i32
@@ -65,6 +69,24 @@ def _lib(plant: int = 0) -> ctypes.CDLL:
             L.orc_key_hash.argtypes = [vp, i32]
             _libs[plant] = L
         return _libs[plant]
+
+
+class OrcTrunc(ctypes.Structure):
+    """Every truncation criterion at once (oracle.cpp's OrcTrunc)."""
+    _fields_ = [("deg_on", ctypes.c_int32), ("deg_mask", ctypes.c_uint32), ("deg_max", ctypes.c_int64),
+                ("harm_on", ctypes.c_int32), ("harm_mask", ctypes.c_uint32), ("harm_max", ctypes.c_int64),
+                ("coef_on", ctypes.c_int32), ("coef_min", ctypes.c_double)]
+
+
+def _orc_trunc(trunc, harmonic, coef_min):
+    t = OrcTrunc()
+    if trunc is not None:
+        t.deg_on, t.deg_max, t.deg_mask = 1, int(trunc[0]), int(trunc[1] or 0)
+    if harmonic is not None:
+        t.harm_on, t.harm_max, t.harm_mask = 1, int(harmonic[0]), int(harmonic[1] or 0)
+    if coef_min is not None:
+        t.coef_on, t.coef_min = 1, float(coef_min)
+    return t
 
 
 def _p(a: np.ndarray):
@@ -94,11 +116,12 @@ def _trunc_mask(trunc, nv):
 
 
 def poly_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
-             keep_zero: bool = False, plant: int = 0, trunc=None) -> PolyResult:
+             keep_zero: bool = False, plant: int = 0, trunc=None, coef_min=None) -> PolyResult:
     """h = f * g by the definition.  f, g: objects with .exps [v, n] int32, .coef.
 
     trunc = (N, mask): keep the pairs whose product term has degree <= N in the
-    variables of the bit mask (0 = all variables)."""
+    variables of the bit mask (0 = all variables).  coef_min = eps (float64
+    coefficients only): keep the pairs with |C_f * C_g| >= eps."""
     L = _lib(plant)
     is_f64 = f.coef.dtype == np.float64
     ef = np.ascontiguousarray(f.exps, dtype=np.int32)
@@ -109,7 +132,10 @@ def poly_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
     nv = ef.shape[0]
     args = (nv, cf.shape[0], _p(ef), _p(cf), cg.shape[0], _p(eg), _p(cg),
             int(is_f64), nthreads, shard[0], shard[1], int(keep_zero))
-    if trunc is None:
+    if coef_min is not None:
+        t = _orc_trunc(None if trunc is None else _trunc_mask(trunc, nv)[::-1], None, coef_min)
+        r = L.orc_poly_mul_tr(*args, ctypes.byref(t))
+    elif trunc is None:
         r = L.orc_poly_mul(*args)
     else:
         r = L.orc_poly_mul_trunc(*args, *_trunc_mask(trunc, nv))
@@ -127,10 +153,14 @@ def poly_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
 
 
 def poisson_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
-                keep_zero: bool = False, plant: int = 0, trunc=None) -> PSeriesResult:
+                keep_zero: bool = False, plant: int = 0, trunc=None, harmonic=None,
+                coef_min=None) -> PSeriesResult:
     """h = f * g for Poisson series, by the product-to-sum identities.
 
-    trunc = (N, mask) truncates by the degree of the polynomial part."""
+    trunc = (N, mask) truncates by the degree of the polynomial part;
+    harmonic = (N, mask) keeps the terms whose harmonic order (sum of
+    |multiplier| over the trig variables of mask, 0 = all) is <= N;
+    coef_min = eps keeps the pairs with |C_f * C_g| >= eps."""
     L = _lib(plant)
     np_, nt = f.exps.shape[0], f.trig.shape[0]
     a = [np.ascontiguousarray(x) for x in (f.exps.astype(np.int32), f.trig.astype(np.int32),
@@ -139,7 +169,10 @@ def poisson_mul(f, g, nthreads: int = 1, shard: tuple[int, int] = (1, 0),
                                            g.kind.astype(np.uint8), g.coef.astype(np.float64))]
     args = (np_, nt, a[3].shape[0], *[_p(x) for x in a], b[3].shape[0],
             *[_p(x) for x in b], nthreads, shard[0], shard[1], int(keep_zero))
-    if trunc is None:
+    if harmonic is not None or coef_min is not None:
+        t = _orc_trunc(None if trunc is None else _trunc_mask(trunc, np_)[::-1], harmonic, coef_min)
+        r = L.orc_poisson_mul_tr(*args, ctypes.byref(t))
+    elif trunc is None:
         r = L.orc_poisson_mul(*args)
     else:
         r = L.orc_poisson_mul_trunc(*args, *_trunc_mask(trunc, np_))

@@ -166,12 +166,58 @@ void run_threads(int nthreads, int64_t nf, F body) {
   for (auto& x : th) x.join();
 }
 
-// Degree truncation: on = 0 keeps every term.
+// Truncation (Sec. 3 lists three criteria: the exponents of polynomial
+// variables, the order of the Fourier harmonics and the absolute value of the
+// coefficients).  A zero flag leaves that criterion off.
+//  * degree: a pair contributes only when the degree of its product term in
+//    the polynomial variables of mask (the sum of their exponents) is <= N;
+//  * harmonic order: a Poisson term is kept only when its harmonic order, the
+//    sum of |multiplier| over the trig variables of hmask, is <= hN; it is
+//    judged term by term, on each of the two terms a pair emits (the order of
+//    a sum or difference of multiplier vectors is not the sum of the orders);
+//  * coefficient magnitude: a pair contributes only when |C_f * C_g|, the
+//    float64 product of the two coefficients (for Poisson series before the
+//    1/2 of the product-to-sum identities), is >= cmin.
 struct Trunc {
   int on = 0;
   uint32_t mask = 0;   // bit k: polynomial variable k counts
   int64_t N = 0;
+  int hon = 0;
+  uint32_t hmask = 0;  // bit k: trig variable k counts
+  int64_t hN = 0;
+  int con = 0;
+  double cmin = 0.0;
 };
+
+// The pair (C, D) passes the coefficient bound.
+bool coef_kept(const Trunc& T, double C, double D) {
+  if (!T.con) return true;
+  const double p = C * D;
+#if ORC_PLANT == 11
+  return (p >= 0 ? p : -p) > T.cmin;   // planted: the bound itself excluded
+#endif
+  return (p >= 0 ? p : -p) >= T.cmin;
+}
+
+// Harmonic order of the trig part key.c[1 .. nt] in the variables of hmask.
+bool above_harmonic(const Trunc& T, const Key& key, int nt) {
+  if (!T.hon) return false;
+  int64_t o = 0;
+  for (int k = 0; k < nt; ++k) {
+#if ORC_PLANT == 14
+    {   // planted: the mask ignored, every trig variable counts
+#else
+    if ((T.hmask >> k) & 1u) {
+#endif
+      const int64_t t = key.c[1 + k];
+      o += t >= 0 ? t : -t;
+    }
+  }
+#if ORC_PLANT == 13
+  return o >= T.hN;   // planted: the bound itself excluded
+#endif
+  return o > T.hN;
+}
 
 // Degree of the polynomial part poly[0..np) in the truncation variables.
 bool above_bound(const Trunc& T, const int32_t* poly, int np) {
@@ -205,6 +251,9 @@ void poly_slice(int nv, const int32_t* ef, const Coef* cf, int64_t nf, int64_t i
       key.c[0] = ef[i] + ef[i];   // planted: uses f's first exponent twice
 #endif
       if (above_bound(T, key.c, nv)) continue;
+      if constexpr (std::is_same<Coef, double>::value) {
+        if (!coef_kept(T, cf[i], cg[j])) continue;
+      }
       if (!in_shard(key, nv, smod, sid)) continue;
       auto it = map.find(key);
       if (it == map.end()) it = map.emplace(key, Acc()).first;
@@ -287,9 +336,11 @@ struct PSIn {
   const double* c;    // [n]
 };
 
-void emit(TermMap<AccF>& map, Key& key, int np, int nt, double coef, int64_t smod, int64_t sid) {
+void emit(TermMap<AccF>& map, Key& key, int np, int nt, double coef, int64_t smod, int64_t sid,
+          const Trunc& T) {
   int s = canonicalise(key, nt);
   if (s == 0) return;
+  if (above_harmonic(T, key, nt)) return;
   if (!in_shard(key, 1 + nt + np, smod, sid)) return;
   auto it = map.find(key);
   if (it == map.end()) it = map.emplace(key, AccF()).first;
@@ -307,6 +358,11 @@ void poisson_slice(int np, int nt, const PSIn& F, const PSIn& G, int64_t i0, int
         for (int k = 0; k < np; ++k) poly[k] = F.e[(int64_t)k * F.n + i] + G.e[(int64_t)k * G.n + j];
         if (above_bound(T, poly, np)) continue;
       }
+#if ORC_PLANT == 12
+      if (!coef_kept(T, F.c[i] * 0.5, G.c[j])) continue;   // planted: the bound applied after the 1/2
+#else
+      if (!coef_kept(T, F.c[i], G.c[j])) continue;
+#endif
       double h = (F.c[i] * G.c[j]) * 0.5;
 #if ORC_PLANT == 1
       h = F.c[i] * G.c[j];   // planted: the product-to-sum halves dropped
@@ -331,14 +387,14 @@ void poisson_slice(int np, int nt, const PSIn& F, const PSIn& G, int64_t i0, int
 #if ORC_PLANT == 3
       for (int k = 0; k < nt; ++k) key.c[1 + k] = -key.c[1 + k];   // planted: g - f
 #endif
-      emit(map, key, np, nt, sd * h, smod, sid);
+      emit(map, key, np, nt, sd * h, smod, sid, T);
       // sum term: trig(f) + trig(g)
       for (int k = 0; k < np; ++k)
         key.c[1 + nt + k] = F.e[(int64_t)k * F.n + i] + G.e[(int64_t)k * G.n + j];
       key.c[0] = ks;
       for (int k = 0; k < nt; ++k)
         key.c[1 + k] = F.t[(int64_t)k * F.n + i] + G.t[(int64_t)k * G.n + j];
-      emit(map, key, np, nt, ss * h, smod, sid);
+      emit(map, key, np, nt, ss * h, smod, sid, T);
     }
   }
 }
@@ -413,6 +469,52 @@ void* orc_poisson_mul_trunc(int np, int nt, int64_t nf, const int32_t* ef, const
   Trunc T;
   T.on = 1; T.mask = mask; T.N = max_degree;
   return poisson_mul(np, nt, F, G, nthreads, shard_mod, shard_id, keep_zero, T);
+}
+
+// Every truncation criterion at once.  deg_on / harm_on / coef_on switch the
+// criteria on (see Trunc); a coefficient bound needs float64 coefficients.
+struct OrcTrunc {
+  int32_t deg_on;
+  uint32_t deg_mask;    // 0 = every polynomial variable
+  int64_t deg_max;
+  int32_t harm_on;
+  uint32_t harm_mask;   // 0 = every trig variable
+  int64_t harm_max;
+  int32_t coef_on;
+  double coef_min;
+};
+
+static Trunc to_trunc(const OrcTrunc* t, int np, int nt) {
+  Trunc T;
+  if (!t) return T;
+  T.on = t->deg_on;
+  T.mask = t->deg_mask ? t->deg_mask : (np >= 32 ? 0xffffffffu : (1u << np) - 1u);
+  T.N = t->deg_max;
+  T.hon = t->harm_on;
+  T.hmask = t->harm_mask ? t->harm_mask : (nt >= 32 ? 0xffffffffu : (1u << nt) - 1u);
+  T.hN = t->harm_max;
+  T.con = t->coef_on;
+  T.cmin = t->coef_min;
+  return T;
+}
+
+void* orc_poly_mul_tr(int nv, int64_t nf, const int32_t* ef, const void* cf, int64_t ng,
+                      const int32_t* eg, const void* cg, int is_f64, int nthreads, int64_t shard_mod,
+                      int64_t shard_id, int keep_zero, const OrcTrunc* tr) {
+  if (nv < 1 || nv > MAXK || nf < 0 || ng < 0) return nullptr;
+  if (tr && (tr->harm_on || (tr->coef_on && !is_f64))) return nullptr;
+  return poly_mul(nv, nf, ef, cf, ng, eg, cg, is_f64, nthreads, shard_mod, shard_id, keep_zero,
+                  to_trunc(tr, nv, 0));
+}
+
+void* orc_poisson_mul_tr(int np, int nt, int64_t nf, const int32_t* ef, const int32_t* tf,
+                         const uint8_t* kf, const double* cf, int64_t ng, const int32_t* eg,
+                         const int32_t* tg, const uint8_t* kg, const double* cg, int nthreads,
+                         int64_t shard_mod, int64_t shard_id, int keep_zero, const OrcTrunc* tr) {
+  if (np < 0 || nt < 1 || 1 + np + nt > MAXK || nf < 0 || ng < 0) return nullptr;
+  if (tr && tr->deg_on && np < 1) return nullptr;
+  PSIn F{nf, ef, tf, kf, cf}, G{ng, eg, tg, kg, cg};
+  return poisson_mul(np, nt, F, G, nthreads, shard_mod, shard_id, keep_zero, to_trunc(tr, np, nt));
 }
 
 int64_t orc_result_nterms(const void* r) { return (int64_t)((const Result*)r)->keys.size(); }

@@ -117,3 +117,56 @@ def eval_truncated_pseries(f, g, x: np.ndarray, y: np.ndarray, mask: int, N: int
             val += a * b
             mag += am * bm
     return val, mag
+
+
+def eval_poly_real(exps: np.ndarray, coef: np.ndarray, x: np.ndarray):
+    """(value, magnitude) of a float64 polynomial at the real point x (x > 0)."""
+    mono = np.prod(x[:, None] ** exps.astype(np.float64), axis=0)
+    return float((coef * mono).sum()), float(np.abs(coef * mono).sum())
+
+
+def powers_of_ten(p, levels: np.ndarray, rng):
+    """A copy of p whose coefficients are +-10^-level * (1 + u / 10), u in [0, 1):
+    the magnitude of a product of two such coefficients lies in
+    [10^-(a+b), 1.21 * 10^-(a+b)), so |C_f C_g| >= 0.5 * 10^-N exactly when
+    a + b <= N, whatever the rounding."""
+    mag = 10.0 ** (-levels.astype(np.float64)) * (1.0 + 0.1 * rng.uniform(levels.shape[0]))
+    c = np.where(p.coef < 0, -mag, mag)
+    if hasattr(p, "trig"):
+        return type(p)(p.exps, p.trig, p.kind, c)
+    return type(p)(p.exps, c)
+
+
+def eval_level_truncated(f, g, lf, lg, N, evaluate):
+    """(value, magnitude) of sum over level pairs with a + b <= N of F_a * G_b:
+    the product keeping the pairs with a + b <= N, reached from f and g alone."""
+    val, mag = 0.0, 0.0
+    for a in np.unique(lf):
+        va, ma = evaluate(f, lf == a)
+        for b in np.unique(lg):
+            if a + b > N:
+                continue
+            vb, mb = evaluate(g, lg == b)
+            val += va * vb
+            mag += ma * mb
+    return val, mag
+
+
+def sample_grid(s, x: np.ndarray, M: int) -> np.ndarray:
+    """Values of a Poisson series with two trig variables at the real point x
+    on the M x M grid of angles y = 2 pi (m1, m2) / M."""
+    grid = 2.0 * np.pi * np.arange(M) / M
+    y1, y2 = np.meshgrid(grid, grid, indexing="ij")
+    mono = np.prod(x[:, None] ** s.exps.astype(np.float64), axis=0)
+    vals = np.zeros((M, M))
+    for i in range(s.coef.shape[0]):
+        ph = s.trig[0, i] * y1 + s.trig[1, i] * y2
+        vals += s.coef[i] * mono[i] * (np.cos(ph) if s.kind[i] == 0 else np.sin(ph))
+    return vals
+
+
+def fourier_coefficients(vals: np.ndarray) -> np.ndarray:
+    """Complex Fourier coefficients c_k of grid samples of a trig polynomial,
+    S(y) = sum_k c_k exp(i k.y), by the 2-D FFT: c_k = FFT[k mod M] / M^2
+    (exact for |k_m| < M / 2)."""
+    return np.fft.fft2(vals) / vals.size

@@ -12,8 +12,9 @@ import numpy as np
 import pytest
 
 import oracle
-from pins import (M61, as_dict, box_convolution, degrees, eval_mod_m31, eval_mod_p,
-                  eval_pseries, eval_truncated_mod_m31, eval_truncated_pseries)
+from pins import (M61, as_dict, box_convolution, degrees, eval_level_truncated, eval_mod_m31,
+                  eval_mod_p, eval_poly_real, eval_pseries, eval_truncated_mod_m31,
+                  eval_truncated_pseries, fourier_coefficients, powers_of_ten, sample_grid)
 from workloads import (PSeries, Poly, Rng, dense_total_degree, fateman, random_poly,
                        random_pseries, total_degree_tuples, workload_cfg1,
                        workload_cfg2, workload_cfg3)
@@ -405,6 +406,119 @@ def test_oracle_truncation():
     assert pin_truncation() == []
 
 
+def pin_coef_truncation(plant=0):
+    """Truncation by coefficient magnitude (Sec. 3): a pair contributes when
+    |C_f C_g| >= eps.  With coefficients +-10^-level (1 + u/10) and
+    eps = 0.5 * 10^-N the kept pairs are exactly those whose levels add up to
+    at most N, so the truncated product evaluates to the sum of F_a G_b over
+    a + b <= N (reached from f and g alone, at random points and angles).  At
+    the boundary: 2 * 3 against eps = 6 is kept and against the next double
+    above 6 is not; for Poisson series the bound applies to C_f C_g before the
+    1/2 of the product-to-sum identities."""
+    errs = []
+    rng = Rng(2300)
+    for s, (v, n, lo, hi) in enumerate([(2, 70, -3, 4), (3, 90, [-2, 0, -4], [3, 4, 1])]):
+        f0 = random_poly(v, n, lo, hi, 2310 + s, "f64")
+        g0 = random_poly(v, n + 13, lo, hi, 2320 + s, "f64")
+        lf, lg = rng.ints(0, 4, f0.n), rng.ints(0, 4, g0.n)
+        f, g = powers_of_ten(f0, lf, rng), powers_of_ten(g0, lg, rng)
+        for N in (0, 3, 5, 8):
+            for nth in (1, 3):
+                h = oracle.poly_mul(f, g, nthreads=nth, plant=plant, coef_min=0.5 * 10.0 ** -N)
+                for _ in range(2):
+                    x = 0.5 + rng.uniform(v)
+                    want, mag = eval_level_truncated(
+                        f, g, lf, lg, N, lambda p, sel: eval_poly_real(p.exps[:, sel], p.coef[sel], x))
+                    got, _ = eval_poly_real(h.exps, h.coef, x)
+                    if abs(got - want) > 1e-12 * mag:
+                        errs.append(f"coefficient-truncated polynomial v={v} N={N} threads={nth}")
+                        break
+    for s, (np_, nt, n) in enumerate([(1, 2, 60), (2, 3, 80)]):
+        f0 = random_pseries(np_, nt, n, 2, 3, 2330 + s)
+        g0 = random_pseries(np_, nt, n + 9, 2, 3, 2340 + s)
+        lf, lg = rng.ints(0, 4, f0.n), rng.ints(0, 4, g0.n)
+        f, g = powers_of_ten(f0, lf, rng), powers_of_ten(g0, lg, rng)
+        for N in (1, 4, 7):
+            h = oracle.poisson_mul(f, g, nthreads=2, plant=plant, coef_min=0.5 * 10.0 ** -N)
+            H = PSeries(h.exps, h.trig, h.kind, h.coef)
+            for _ in range(2):
+                x = 0.5 + rng.uniform(np_)
+                y = 2 * math.pi * rng.uniform(nt)
+                sub = lambda p, sel: eval_pseries(PSeries(p.exps[:, sel], p.trig[:, sel], p.kind[sel],
+                                                          p.coef[sel]), x, y)
+                want, mag = eval_level_truncated(f, g, lf, lg, N, sub)
+                got, _ = eval_pseries(H, x, y)
+                if abs(got - want) > 1e-12 * mag:
+                    errs.append(f"coefficient-truncated Poisson np={np_} nt={nt} N={N}")
+                    break
+    # the boundary, on a polynomial and a Poisson product
+    f = Poly(np.array([[1], [0]], np.int32), np.array([2.0]))
+    g = Poly(np.array([[0], [1]], np.int32), np.array([3.0]))
+    for eps, want in ((6.0, {(1, 1): 6.0}), (np.nextafter(6.0, 7.0), {})):
+        r = oracle.poly_mul(f, g, plant=plant, coef_min=eps)
+        if as_dict(r.exps, r.coef) != want:
+            errs.append(f"coefficient bound at eps={eps!r}: {as_dict(r.exps, r.coef)}")
+    f = PSeries(np.zeros((1, 1), np.int32), np.array([[1]], np.int32), np.zeros(1, np.uint8), np.array([2.0]))
+    g = PSeries(np.zeros((1, 1), np.int32), np.array([[1]], np.int32), np.zeros(1, np.uint8), np.array([3.0]))
+    for eps, want in ((6.0, {0: 3.0, 2: 3.0}), (np.nextafter(6.0, 7.0), {})):
+        r = oracle.poisson_mul(f, g, plant=plant, coef_min=eps)
+        got = {int(r.trig[0, i]): float(r.coef[i]) for i in range(r.coef.shape[0])}
+        if got != want:
+            errs.append(f"Poisson coefficient bound at eps={eps!r}: {got}")
+    return errs
+
+
+def pin_harmonic_truncation(plant=0):
+    """Truncation by the order of the Fourier harmonics (Sec. 3): a term is kept
+    when the sum of |multiplier| over the chosen trig variables is at most N.
+    Pinned by the 2-D FFT of F G sampled on a grid of angles (a different
+    algorithm): the truncated product's Fourier coefficients must be those of
+    F G for every harmonic of order <= N and zero above; plus hand-worked
+    cases (cos y cos y = 1/2 + 1/2 cos 2y; a mask that counts one variable)."""
+    errs = []
+    rng = Rng(2400)
+    M = 16   # product multipliers lie in [-6, 6]: no aliasing on 16 points
+    for s in range(2):
+        f = random_pseries(1, 2, 40, 2, 3, 2410 + s)
+        g = random_pseries(1, 2, 45, 2, 3, 2420 + s)
+        scale = float(np.abs(f.coef).sum() * np.abs(g.coef).sum())
+        x = 0.5 + rng.uniform(1)
+        # coefficients of F G: from the product of the sampled values
+        full = fourier_coefficients(sample_grid(f, x, M) * sample_grid(g, x, M))
+        k = np.fft.fftfreq(M, 1.0 / M).astype(int)
+        K1, K2 = np.meshgrid(k, k, indexing="ij")
+        for mask in (0, 0b10):
+            order = (np.abs(K1) if mask in (0, 0b01) else 0) + (np.abs(K2) if mask in (0, 0b10) else 0)
+            for N in (0, 2, 3, 5):
+                h = oracle.poisson_mul(f, g, nthreads=2, plant=plant, harmonic=(N, mask), keep_zero=True)
+                H = PSeries(h.exps, h.trig, h.kind, h.coef)
+                got = fourier_coefficients(sample_grid(H, x, M))
+                want = np.where(order <= N, full, 0.0)
+                if np.abs(got - want).max() > 1e-12 * scale:
+                    errs.append(f"harmonic truncation mask={mask:b} N={N}: Fourier coefficients differ")
+    one = lambda t, c: PSeries(np.zeros((1, 1), np.int32), np.array(t, np.int32)[:, None],
+                               np.zeros(1, np.uint8), np.array([c]))
+    for N, want in ((0, {(0,): 0.5}), (1, {(0,): 0.5}), (2, {(0,): 0.5, (2,): 0.5})):
+        r = oracle.poisson_mul(one([1], 1.0), one([1], 1.0), plant=plant, harmonic=(N, 0))
+        got = {tuple(int(v) for v in r.trig[:, i]): float(r.coef[i]) for i in range(r.coef.shape[0])}
+        if got != want:
+            errs.append(f"cos y * cos y at harmonic order <= {N}: {got}")
+    # (1, 1) and (-1, 1): difference (2, 0), sum (0, 2); only variable 0 counts
+    r = oracle.poisson_mul(one([1, 1], 1.0), one([-1, 1], 1.0), plant=plant, harmonic=(1, 0b01))
+    got = {tuple(int(v) for v in r.trig[:, i]): float(r.coef[i]) for i in range(r.coef.shape[0])}
+    if got != {(0, 2): 0.5}:
+        errs.append(f"masked harmonic order: {got}")
+    return errs
+
+
+def test_oracle_coefficient_truncation():
+    assert pin_coef_truncation() == []
+
+
+def test_oracle_harmonic_truncation():
+    assert pin_harmonic_truncation() == []
+
+
 # ---------------------------------------------------------------------------
 # planted mistakes: each must be caught by some pin
 # ---------------------------------------------------------------------------
@@ -420,6 +534,10 @@ PLANTS = {
     8: "thread merge drops the other thread's running sum",
     9: "mass counts every contribution twice",
     10: "thread merge drops the other thread's mass",
+    11: "coefficient bound applied as > eps instead of >= eps",
+    12: "coefficient bound applied after the product-to-sum 1/2",
+    13: "harmonic order bound applied as < N instead of <= N",
+    14: "harmonic order counts every trig variable, ignoring the mask",
 }
 
 
@@ -427,5 +545,5 @@ PLANTS = {
 def test_planted_mistake_is_caught(plant):
     caught = (pin_werner(plant) + pin_canonical(plant) + pin_random_angles(plant)
               + pin_bruteforce(plant) + pin_mod_p(plant) + pin_truncation(plant)
-              + pin_mass(plant))
+              + pin_mass(plant) + pin_coef_truncation(plant) + pin_harmonic_truncation(plant))
     assert caught, f"planted mistake {plant} ({PLANTS[plant]}) escaped every pin"
