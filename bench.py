@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--block-slots", type=int, default=0, help="dense output block size (0 = library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched / served measurements")
     ap.add_argument("--batch-products", type=int, default=4096, help="products in the uneven batch")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="time the oracle on the whole dense and hash workloads, one thread and every core, and exit")
     ap.add_argument("--case", default="", choices=["", "cfg3", "cfg4s", "cfg4"],
                     help="profiling runs: time only this secondary case (cfg4s = cfg4 at 5000 terms)")
     return ap.parse_args()
@@ -121,17 +123,26 @@ class Clocks:
 # DRAM bytes (read + write) per launch of k_dense_accum on this workload, from
 # one ncu capture of the kernel on it; valid only for the kernel source it was
 # taken on, identified by the leading hex digits of its SHA-256.
-DENSE_TRAFFIC = {"source_sha256": "3972bf7597ef3daf", "bytes": 2760960}
+DENSE_TRAFFIC = {"source": "kr_dense.cu", "source_sha256": "3972bf7597ef3daf", "bytes": 2760960}
+# DRAM traffic of the polynomial hash insert kernel on the MP-sparse product,
+# per launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture)
+HASH_TRAFFIC = {"source": "kr_hash.cu", "source_sha256": "", "bytes": None}
 
 
-def dense_traffic():
+def kernel_traffic(rec):
+    """A recorded DRAM traffic figure, or None once the kernel's source differs
+    from the one the counters were taken on."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "paper_1004_4548_gb300", "csrc", "kr_dense.cu"), "rb") as fh:
+        with open(os.path.join(ROOT, "paper_1004_4548_gb300", "csrc", rec["source"]), "rb") as fh:
             sha = hashlib.sha256(fh.read()).hexdigest()
     except OSError:
         return None
-    return DENSE_TRAFFIC["bytes"] if sha.startswith(DENSE_TRAFFIC["source_sha256"]) else None
+    return rec["bytes"] if rec["source_sha256"] and sha.startswith(rec["source_sha256"]) else None
+
+
+def dense_traffic():
+    return kernel_traffic(DENSE_TRAFFIC)
 
 
 def measured_peaks():
@@ -145,24 +156,76 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
-def cpu_baseline(f, g, budget_s: float = 12.0):
+# The oracle's sample of the workload: a fixed slice, so that every run (and
+# both arms) times the same work.  The multi-threaded rate still depends on
+# the slice (thread start-up and the final merge of the per-thread maps are
+# amortised over it), which is why it is fixed rather than sized by a budget.
+CPU_SAMPLE_MT = 4096   # f terms x all g terms, every core
+CPU_SAMPLE_ST = 512    # f terms x all g terms, one thread
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(f, g, single: bool = True):
+    """The oracle on the host's cores over the fixed sample (and on one thread)."""
     import oracle
     from workloads import Poly
     cores = os.cpu_count() or 1
-    m = 64
-    fs = Poly(np.ascontiguousarray(f.exps[:, :m]), f.coef[:m].copy())
-    t = time.perf_counter()
-    oracle.poly_mul(fs, g, nthreads=cores)
-    dt = max(time.perf_counter() - t, 1e-3)
-    m = int(min(f.n, max(cores, m * budget_s / dt)))
-    fs = Poly(np.ascontiguousarray(f.exps[:, :m]), f.coef[:m].copy())
-    t = time.perf_counter()
-    oracle.poly_mul(fs, g, nthreads=cores)
-    dt = time.perf_counter() - t
-    tp = m * g.n
-    return {"value": tp / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {m} of {f.n} f terms x all {g.n} g terms of the workload "
-                      f"({tp} term-products, {dt:.1f} s, std::map oracle, {cores} threads)"}
+
+    def rate(m, threads):
+        fs = Poly(np.ascontiguousarray(f.exps[:, :m]), f.coef[:m].copy())
+        t = time.perf_counter()
+        oracle.poly_mul(fs, g, nthreads=threads)
+        dt = time.perf_counter() - t
+        return m * g.n / dt / 1e6, dt
+
+    m = min(f.n, CPU_SAMPLE_MT)
+    v, dt = rate(m, cores)
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": f"first {m} of {f.n} f terms x all {g.n} g terms of the workload "
+                     f"({m * g.n} term-products, {dt:.2f} s, std::map oracle, {cores} threads)"}
+    if single:
+        m1 = min(f.n, CPU_SAMPLE_ST)
+        v1, dt1 = rate(m1, 1)
+        out["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                "sample": f"first {m1} f terms x all {g.n} g terms "
+                                          f"({m1 * g.n} term-products, {dt1:.2f} s)"}
+    return out
+
+
+def cpu_full():
+    """The oracle on the whole dense (degree 20) and hash (MP-sparse) workloads,
+    one thread and every core: one JSON line per run."""
+    import oracle
+    from workloads import workload_cfg2, workload_cfg3
+    cores = os.cpu_count() or 1
+    model = cpu_model()
+    for name, (f, g) in (("dense path, degree-20 workload", workload_cfg2()),
+                         ("hash path, MP-sparse workload", workload_cfg3())):
+        for threads in (cores, 1):
+            t = time.perf_counter()
+            r = oracle.poly_mul(f, g, nthreads=threads)
+            dt = time.perf_counter() - t
+            print(json.dumps({"cpu_full": name, "threads": threads, "cpu_model": model, "seconds": dt,
+                              "term_products": f.n * g.n, "output_terms": int(r.coef.shape[0]),
+                              "value": f.n * g.n / dt / 1e6, "unit": UNIT}), flush=True)
 
 
 def reference_arm(args):
@@ -174,8 +237,7 @@ def reference_arm(args):
     vals = []
     cb = None
     for i in range(args.warmup + args.steps):
-        per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-        cb = cpu_baseline(f, g, budget_s=per_step)
+        cb = cpu_baseline(f, g, single=(i == args.warmup + args.steps - 1))
         if i >= args.warmup:
             vals.append(cb["value"])
     v = statistics.median(vals)
@@ -194,6 +256,9 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.cpu_full:
+        cpu_full()
+        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -212,6 +277,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     ctx = kron.Context(local)
@@ -335,16 +401,40 @@ def main():
         want = set(args.paths.split(",")) if args.paths else None
         sel = lambda name: want is None or name in want
         ctx.set_profiling(True)
+        hbm = measured_peaks().get("hbm_gbs")
         if sel("hash_cfg3"):
-            paths["hash_cfg3"] = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert",
-                                           max(3, args.steps // 2))
-        if sel("poisson_cfg4") or sel("poisson_cfg4_hash"):
+            h3 = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert",
+                           max(3, args.steps // 2))
+            # 24 B per term-product: an 8 B key probe read, an 8 B coefficient read and write
+            roof3 = hbm_roofline("k_hash_insert_poly", h3["term_products"], h3["kernel_ms"], 24, hbm,
+                                 kernel_traffic(HASH_TRAFFIC))
+            # the ceiling of the same insert routine on random keys, at this product's
+            # table size (2^24 slots) and key count, and of plain random adds
+            ins = kron.kr_probe_table_update_rate(24, h3["output_terms"], h3["term_products"], 0, local, 3)
+            add = kron.kr_probe_table_update_rate(24, h3["output_terms"], h3["term_products"], 1, local, 3)
+            roof3["ceiling_insert_per_s"] = ins
+            roof3["ceiling_random_add_per_s"] = add
+            roof3["frac_of_insert_ceiling"] = (h3["term_products"] / (h3["kernel_ms"] * 1e-3)) / ins \
+                if ins > 0 else None
+            h3["roofline"] = roof3
+            paths["hash_cfg3"] = h3
+        if sel("poisson_cfg4") or sel("poisson_cfg4_hash") or sel("poisson_cfg4_truncated"):
             f4, g4 = workload_cfg4()
             if sel("poisson_cfg4"):
-                paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3)
+                paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3, hbm_gbs=hbm)
             if sel("poisson_cfg4_hash"):
                 paths["poisson_cfg4_hash"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3,
-                                                          path=kron.KR_PATH_HASH)
+                                                          path=kron.KR_PATH_HASH, hbm_gbs=hbm)
+            if sel("poisson_cfg4_truncated"):
+                # Sec. 3's truncation of a Poisson product: pairs with |C_f C_g| >= 1e-38 (about 14%
+                # of them; the magnitudes fall with the exponents and multipliers) and terms of
+                # harmonic order <= 20; the rate counts every pair of the product
+                paths["poisson_cfg4_truncated"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3,
+                                                               hbm_gbs=hbm, kernel_name="k_hash_insert_trunc",
+                                                               harmonic_order=20, coef_min=1e-38)
+                paths["poisson_cfg4_truncated"]["context"] = (
+                    "the Poisson workload truncated by coefficient magnitude (|C_f C_g| >= 1e-38) and "
+                    "harmonic order (<= 20); units are all 4e8 pairs of the untruncated product")
         fa, ga = fateman()
         if sel("fateman_full"):
             paths["fateman_full"] = time_poly(kron, ctx, fa, ga, dev, stream, flush, "dense_accum", 5)
@@ -382,7 +472,7 @@ def main():
                 "clocks": clk,
                 "stages_ms_last_step": {k: round(v, 4) for k, v in stages},
                 "wall_s_timed": wall,
-                "sm_cycles_per_term_product": (clk["sm_mhz"] * 1e6 * ms * 1e-3 / tp * 152)
+                "sm_cycles_per_term_product": (clk["sm_mhz"] * 1e6 * ms * 1e-3 / tp * num_sms)
                 if clk.get("sm_mhz") else None,
                 "paths": paths,
                 "batched": batched}
@@ -615,19 +705,34 @@ def time_poly(kron, ctx, f, g, dev, stream, flush, kernel, steps, units=None, **
             "kernel_rate": tp / (kms * 1e-3) / 1e6, "stages_ms_last_step": dict(ctx.stages())}
 
 
-def time_pseries(kron, ctx, f, g, dev, stream, flush, steps, path=0):
+# Algorithmic bytes per term-product of the Poisson accumulation: each pair
+# updates two keys.  Hash table: per update an 8 B key probe read and an 8 B
+# coefficient read and write (48 B a pair).  Dense array indexed by key: per
+# update one 8 B coefficient read and write (32 B a pair).
+POISSON_BYTES = {"hash": 48, "dense": 32}
+
+
+def hbm_roofline(kernel, units, kms, bytes_per_unit, hbm_gbs, traffic=None):
+    achieved = units * bytes_per_unit / (kms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": achieved / hbm_gbs if hbm_gbs else None, "traffic": traffic,
+            "algorithmic_bytes_per_term_product": bytes_per_unit, "units_per_launch": units,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, read + write)"}
+
+
+def time_pseries(kron, ctx, f, g, dev, stream, flush, steps, path=0, hbm_gbs=None, kernel_name=None,
+                 **opts):
     import torch
     from workloads import PSeries
     F = PSeries(*(torch.from_numpy(x).to(dev) for x in (f.exps, f.trig, f.kind, f.coef)))
     G = PSeries(*(torch.from_numpy(x).to(dev) for x in (g.exps, g.trig, g.kind, g.coef)))
-    out = kron.poisson_mul(F, G, ctx=ctx, path=path)
-    kernel = "hash_insert"
+    out = kron.poisson_mul(F, G, ctx=ctx, path=path, **opts)
     times, kt = [], []
     for _ in range(steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        out = kron.poisson_mul(F, G, ctx=ctx, capacity=int(out[3].shape[0]), path=path)
+        out = kron.poisson_mul(F, G, ctx=ctx, capacity=int(out[3].shape[0]), path=path, **opts)
         b.record(stream)
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
@@ -635,11 +740,15 @@ def time_pseries(kron, ctx, f, g, dev, stream, flush, steps, path=0):
     tp = f.n * g.n
     ms = statistics.mean(times)
     kms = statistics.mean(kt)
-    return {"value": tp / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "term_products": tp,
-            "output_terms": int(out[3].shape[0]), "kernel": "hash_insert", "kernel_ms": kms,
-            "kernel_rate": tp / (kms * 1e-3) / 1e6,
-            "hbm_algorithmic_GBps": tp * 48 / (kms * 1e-3) / 1e9,
-            "stages_ms_last_step": dict(ctx.stages())}
+    form = "hash" if path == 2 else "dense"   # the automatic choice is the dense array here
+    r = {"value": tp / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": ms, "term_products": tp,
+         "output_terms": int(out[3].shape[0]), "kernel": "hash_insert", "kernel_ms": kms,
+         "kernel_rate": tp / (kms * 1e-3) / 1e6, "accumulator": form,
+         "stages_ms_last_step": dict(ctx.stages())}
+    if hbm_gbs:
+        r["roofline"] = hbm_roofline(kernel_name or "k_hash_insert_pseries", tp, kms, POISSON_BYTES[form],
+                                     hbm_gbs)
+    return r
 
 
 if __name__ == "__main__":

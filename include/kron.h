@@ -162,6 +162,28 @@ typedef struct {
    * kron_split_hist helps choose windows of equal work. */
   int64_t code_lo;
   int64_t code_hi;
+  /* Truncation by the order of the Fourier harmonics (Sec. 3), Poisson series
+   * only: with trunc_harmonic = 1 the product keeps only the terms whose
+   * harmonic order, the sum of |t_k| over the trig variables of harmonic_mask
+   * (bit k = trig variable k, 0 = all of them), is at most harmonic_order.
+   * The order of a sum or a difference of multiplier vectors is not the sum
+   * of the orders, so each of the two terms a pair emits is judged on its own,
+   * before it reaches the accumulator; the output order is unchanged.  The
+   * counted multipliers of both operands must lie in [-32767, 32767]
+   * (KR_ERR_INVALID otherwise); a negative order gives the zero series. */
+  int32_t trunc_harmonic;
+  uint32_t harmonic_mask;
+  int64_t harmonic_order;
+  /* Truncation by the absolute value of the coefficients (Sec. 3), float64
+   * coefficients only (KR_ERR_INVALID for int64 ones): coef_min > 0 keeps only
+   * the pairs of terms with |C_f * C_g| >= coef_min, that product being the
+   * float64 product of the two coefficients (for Poisson series, before the
+   * 1/2 of Eq. 6).  Both operands are then walked in order of decreasing |C|,
+   * so that for each term of f the kept partners are a prefix of g, and the
+   * rest of the pairs is skipped without being formed (the ordering by the
+   * truncation criterion that Sec. 3 proposes).  Polynomial products with a
+   * bound take the hash path; 0 = no bound. */
+  double coef_min;
 } kr_opts;
 
 /* ------------------------------------------------------------------------ */
@@ -373,6 +395,20 @@ double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t reps);
  * coefficients.  Allocates and frees a small device buffer; synchronises the
  * device's default stream. */
 double kr_probe_smem_accumulate_rate(int32_t device, int32_t reps);
+
+/* The hash path's ceiling (Sec. 3.2, the hash table; Sec. 5 measures clock
+ * cycles per monomial-by-monomial multiplication, and on this path each one
+ * is an insert-or-add into the table): the rate of `updates` insert-or-adds
+ * (mode 0: a CAS claim of the key's slot, linear probing, then an atomic add
+ * of the value, issued as the polynomial hash kernel issues them) or of plain
+ * atomic adds into each key's home slot (mode 1), with keys drawn at random
+ * from `distinct` values, into a zeroed table of 2^log2_slots 16-byte slots in
+ * device memory, on CUDA device `device`: best of `reps` launches, in updates
+ * per second; < 0 on failure or bad arguments (log2_slots in [10, 30],
+ * distinct at most 0.7 of the slots).  Allocates and frees the table;
+ * synchronises the device's default stream. */
+double kr_probe_table_update_rate(int32_t device, int32_t log2_slots, int64_t distinct, int64_t updates,
+                                  int32_t mode, int32_t reps);
 
 /* Self-test of the library's bounded device waits (the compaction's look-back
  * over preceding chunks): runs the wait against a predecessor that never

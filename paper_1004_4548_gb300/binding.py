@@ -48,7 +48,9 @@ class kr_opts(ctypes.Structure):
     _fields_ = [("path", _i32), ("block_slots", _i32), ("load_factor", ctypes.c_double),
                 ("probe_limit", _i32), ("unsorted", _i32), ("max_regrow", _i32),
                 ("table_slots", _i64), ("truncate", _i32), ("trunc_mask", ctypes.c_uint32),
-                ("trunc_degree", _i64), ("code_lo", _i64), ("code_hi", _i64)]
+                ("trunc_degree", _i64), ("code_lo", _i64), ("code_hi", _i64),
+                ("trunc_harmonic", _i32), ("harmonic_mask", ctypes.c_uint32), ("harmonic_order", _i64),
+                ("coef_min", ctypes.c_double)]
 
 
 class kr_job(ctypes.Structure):
@@ -77,6 +79,7 @@ SIGNATURES = {
     "kr_probe_smem_atomic_rate": (ctypes.c_double, [_i32, _i32, _i32]),
     "kr_probe_smem_accumulate_rate": (ctypes.c_double, [_i32, _i32]),
     "kr_selftest_bounded_wait": (ctypes.c_int, [_i32]),
+    "kr_probe_table_update_rate": (ctypes.c_double, [_i32, _i32, _i64, _i64, _i32, _i32]),
     "kron_dense_product_static": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_int, _i64,
                                                  _vp, _vp]),
     "kron_plan": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
@@ -180,14 +183,20 @@ def _stream_ptr(stream):
 
 
 def _opts(path=0, block_slots=0, load_factor=0.0, probe_limit=0, unsorted=0, max_regrow=0,
-          table_slots=0, trunc_degree=None, trunc_mask=0, code_lo=0, code_hi=0):
+          table_slots=0, trunc_degree=None, trunc_mask=0, code_lo=0, code_hi=0,
+          harmonic_order=None, harmonic_mask=0, coef_min=0.0):
     """kr_opts from keywords; trunc_degree (an int) asks for the truncated product
     of degree <= trunc_degree in the variables of trunc_mask (0 = all);
-    [code_lo, code_hi) restricts the product to a window of output keys."""
+    [code_lo, code_hi) restricts the product to a window of output keys;
+    harmonic_order (an int) keeps the Poisson terms whose harmonic order in the
+    trig variables of harmonic_mask (0 = all) is at most that; coef_min > 0
+    keeps the pairs of float64 terms with |C_f * C_g| >= coef_min."""
     t = trunc_degree is not None
+    h = harmonic_order is not None
     return kr_opts(path, block_slots, load_factor, probe_limit, unsorted, max_regrow, table_slots,
                    1 if t else 0, int(trunc_mask) if t else 0, int(trunc_degree) if t else 0,
-                   int(code_lo), int(code_hi))
+                   int(code_lo), int(code_hi), 1 if h else 0, int(harmonic_mask) if h else 0,
+                   int(harmonic_order) if h else 0, float(coef_min))
 
 
 class Context:
@@ -260,6 +269,13 @@ def _alloc(shape, dtype, device, host):
 def kr_probe_smem_atomic_rate(device: int = 0, f64: bool = False, reps: int = 5) -> float:
     """Shared-memory 64-bit atomic adds per second, whole chip (measured)."""
     return float(load().kr_probe_smem_atomic_rate(device, int(f64), reps))
+
+
+def kr_probe_table_update_rate(log2_slots: int, distinct: int, updates: int, mode: int = 0,
+                               device: int = 0, reps: int = 5) -> float:
+    """Random insert-or-adds (mode 0) or plain adds (mode 1) per second into a
+    table of 2^log2_slots 16-byte slots (the hash path's ceiling)."""
+    return float(load().kr_probe_table_update_rate(device, log2_slots, distinct, updates, mode, reps))
 
 
 def kr_selftest_bounded_wait(device: int = 0) -> int:

@@ -370,7 +370,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     Bump b(pass ? ctx->work : nullptr);
     // the arrays uploaded from the host first and contiguous: one copy
     A.lprods = b.take<Prod>(nlive);
-    A.oplists = b.take<OpRef>(3 * (int64_t)nops);
+    A.oplists = b.take<OpRef>(5 * (int64_t)nops);
     A.dense_ids = b.take<int32_t>((int64_t)dense_ids.size() + 1);
     A.block_begin = b.take<int64_t>((int64_t)dense_ids.size() + 1);
     A.hash_ids = b.take<int32_t>((int64_t)hash_ids.size() + 1);
@@ -406,6 +406,14 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
         if (pl.p.nt > 0) {
           op.tcode = b.take<int64_t>(n);
           op.kind = b.take<uint8_t>(n);
+        }
+        if (pl.p.htrunc) op.hpack = b.take<uint32_t>(2 * (int64_t)pl.p.hwords * n);
+        if (pl.p.ctrunc) {
+          op.mkey = b.take<uint64_t>(n);
+          op.midx = b.take<uint64_t>(n);
+          op.mkey2 = b.take<uint64_t>(n);
+          op.midx2 = b.take<uint64_t>(n);
+          op.mtmp = b.take<unsigned char>(n * mag_tmp_bytes_per_term(pl.p));
         }
       }
       if (pl.p.path == PATH_DENSE && pl.p.nt == 0) {
@@ -519,10 +527,24 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   }
   bool gindex_needed = false;
   for (int p : dense_ids) gindex_needed |= plans[p].p.g.sort_method != SORT_CLUSTER;
+  // operands of products truncated by harmonic order (packed multipliers) and
+  // by coefficient magnitude (reorder by decreasing |C|)
+  std::vector<OpRef> hops, mops;
+  int64_t max_n_h = 0, max_n_m = 0;
+  for (int q = 0; q < nlive; ++q) {
+    const Prod& P = plans[live_ids[q]].p;
+    for (int which = 0; which < 2; ++which) {
+      const int64_t n = which ? P.g.n : P.f.n;
+      if (P.htrunc) { hops.push_back(OpRef{q, which}); max_n_h = std::max(max_n_h, n); }
+      if (P.ctrunc) { mops.push_back(OpRef{q, which}); max_n_m = std::max(max_n_m, n); }
+    }
+  }
   std::vector<OpRef> lists = all;
   lists.insert(lists.end(), bm.begin(), bm.end());
   lists.insert(lists.end(), bt.begin(), bt.end());
   lists.insert(lists.end(), cl.begin(), cl.end());
+  lists.insert(lists.end(), hops.begin(), hops.end());
+  lists.insert(lists.end(), mops.begin(), mops.end());
   ensure_pinned(ctx, sizeof(Prod) * (size_t)(nlive + 1) * 3 + sizeof(OpRef) * lists.size() +
                          16 * (h_block_begin.size() + h_task_begin.size() + 4 * (size_t)nlive) +
                          (size_t)(A.up_end - (char*)A.lprods) + 65536, s);
@@ -553,6 +575,8 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
   const OpRef* d_bm = d_all + all.size();
   const OpRef* d_bt = d_bm + bm.size();
   const OpRef* d_cl = d_bt + bt.size();
+  const OpRef* d_h = d_cl + cl.size();
+  const OpRef* d_m = d_h + hops.size();
   // ---------------- phase B1 device work
   plan_span.done();
   mark(ctx, s, "plan_upload");
@@ -607,6 +631,27 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     ck(ctx, launch_gather(A.lprods, d_all, (int)all.size(), s), "gather");
     ctx->launches += 1;
     mark(ctx, s, "gather");
+  }
+  if (!hops.empty()) {
+    ck(ctx, launch_harmonic_pack(A.lprods, d_h, (int)hops.size(), max_n_h, s), "harmonic pack");
+    ctx->launches += 1;
+  }
+  if (!mops.empty()) {
+    ck(ctx, launch_mag_keys(A.lprods, d_m, (int)mops.size(), max_n_m, s), "magnitude keys");
+    ctx->launches += 1;
+    for (const OpRef& r : mops) {
+      const Operand& op = r.which ? plans[live_ids[r.prod]].p.g : plans[live_ids[r.prod]].p.f;
+      bool in_tmp = false;
+      ck(ctx, radix_sort_pairs(op.mkey, op.midx, op.mkey2, op.midx2, op.n, 64, A.scan, s, &in_tmp),
+         "magnitude sort");
+      ctx->launches += 3 * 8;
+      if (in_tmp)
+        ck(ctx, cudaMemcpyAsync(op.midx, op.midx2, sizeof(uint64_t) * (size_t)op.n, cudaMemcpyDeviceToDevice, s),
+           "magnitude order");
+    }
+    ck(ctx, launch_mag_reorder(A.lprods, d_m, (int)mops.size(), max_n_m, s), "magnitude reorder");
+    ctx->launches += 2;
+    mark(ctx, s, "magnitude_order");
   }
   if (gindex_needed) {
     ck(ctx, launch_build_gindex(A.lprods, A.dense_ids, (int)dense_ids.size(), max_ng_dense, s), "g index");
@@ -686,12 +731,16 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       mark(ctx, s, "dense_accum");
     }
     if (!hash_ids.empty()) {
-      bool any_poly = false, any_pseries = false;
-      for (int p : hash_ids) (plans[p].p.nt > 0 ? any_pseries : any_poly) = true;
+      bool any_poly = false, any_pseries = false, any_trunc = false;
+      for (int p : hash_ids) {
+        const Prod& P = plans[p].p;
+        if (P.ctrunc || P.htrunc) any_trunc = true;
+        else (P.nt > 0 ? any_pseries : any_poly) = true;
+      }
       ck(ctx, launch_hash_insert(A.lprods, A.hash_ids, A.task_begin, (int)hash_ids.size(), any_poly,
-                                 any_pseries, ctx->num_sms * 8, s),
+                                 any_pseries, any_trunc, ctx->num_sms * 8, s),
          "hash insert");
-      ctx->launches += (any_poly ? 1 : 0) + (any_pseries ? 1 : 0);
+      ctx->launches += (any_poly ? 1 : 0) + (any_pseries ? 1 : 0) + (any_trunc ? 1 : 0);
       mark(ctx, s, "hash_insert");
     }
     ck(ctx, launch_compact(A.lprods, nlive, Z.chunk_begin, nchunks_total, Z.counts, Z.cstat, Z.counters + 2,

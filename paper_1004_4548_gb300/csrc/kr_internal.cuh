@@ -80,6 +80,19 @@ struct Operand {
   // records how many terms are kept (the sorted prefix [0, nkeep))
   int64_t sent;
   int64_t nkeep;
+  // truncation by harmonic order: the counted trig multipliers as 16-bit
+  // lanes biased by 32768, two per word, rows [0, hwords) holding t and rows
+  // [hwords, 2 hwords) holding -t ([2 hwords][n]), so that one sum of
+  // absolute lane differences (vsadu2) per word gives |t_f - t_g| and
+  // |t_f + t_g| in the counted variables
+  uint32_t* hpack;
+  // truncation by coefficient magnitude: sort scratch (keys, indices and
+  // their ping-pong copies) and the staging of the reordered term arrays
+  uint64_t* mkey;
+  uint64_t* midx;
+  uint64_t* mkey2;
+  uint64_t* midx2;
+  unsigned char* mtmp;
 };
 
 // One product, planned on the host, read by every kernel.
@@ -101,6 +114,19 @@ struct Prod {
   int32_t gvar;
   uint32_t gmask;
   int32_t gvar_min, gvar_max;
+  // truncation by harmonic order (Poisson series): a term is kept when the
+  // sum of |t_k| over the trig variables of hmask is <= hN; hwords packed
+  // words per term (Operand::hpack)
+  int32_t htrunc;
+  int32_t hwords;
+  uint32_t hmask;
+  int64_t hN;
+  // truncation by coefficient magnitude (float64): a pair is kept when
+  // |C_f * C_g| >= cmin as the kernels form the product (for Poisson series
+  // f's coefficients are halved, and so is cmin); both operands are then in
+  // order of decreasing |C| (kept terms first)
+  int32_t ctrunc;
+  double cmin;
   int64_t Wp;           // polynomial code range (product of poly widths)
   int64_t T2;           // canonical |trig code| values: (Wt - 1) / 2 + 1
   int64_t krange;       // output key range: Wp, or 2 * T2 * Wp for Poisson
@@ -282,6 +308,31 @@ __device__ __forceinline__ void smem_acc_split64(uint32_t a, uint32_t hi_dist, u
   if (h) asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a + hi_dist), "r"(h) : "memory");
 }
 
+// Harmonic orders |t_f - t_g| and |t_f + t_g| (counted variables) of term i
+// of f and term j of g, from their packed multipliers (Operand::hpack).
+__device__ __forceinline__ void harmonic_orders(const Prod& P, int64_t i, int64_t j, uint32_t* od,
+                                                uint32_t* os) {
+  const int hw = P.hwords;
+  const int64_t nf = P.f.n, ng = P.g.n;
+  uint32_t d = 0, sm = 0;
+  for (int w = 0; w < hw; ++w) {
+    const uint32_t a = __ldg(&P.f.hpack[(int64_t)w * nf + i]);
+    d += __vsadu2(a, __ldg(&P.g.hpack[(int64_t)w * ng + j]));
+    sm += __vsadu2(a, __ldg(&P.g.hpack[(int64_t)(hw + w) * ng + j]));
+  }
+  *od = d;
+  *os = sm;
+}
+
+// Bytes per term of Operand::mtmp: code, coefficient, trig code, packed
+// multipliers and kind, each array 8-byte aligned.
+__host__ __device__ inline int64_t mag_tmp_bytes_per_term(const Prod& P) {
+  return 8 + 8 + (P.nt > 0 ? 8 + 1 : 0) + (P.htrunc ? 8 * (int64_t)P.hwords : 0);
+}
+
+// The coefficient bound on a pair's product (false for NaN).
+__device__ __forceinline__ bool coef_kept(const Prod& P, double prod) { return fabs(prod) >= P.cmin; }
+
 // 64-bit mixing function (the finaliser of MurmurHash3, Appleby) for table slots
 __device__ __forceinline__ uint64_t mix64(uint64_t k) {
   k ^= k >> 33;
@@ -315,6 +366,14 @@ cudaError_t launch_gather(Prod* dprods, const OpRef* dops, int nops, cudaStream_
 cudaError_t launch_front_cluster(Prod* dprods, const OpRef* dops, int nops, int64_t max_key_range,
                                  cudaStream_t s);
 
+// Truncation by harmonic order: the packed multipliers of the listed operands
+// (from their sorted trig codes).  Truncation by coefficient magnitude: keys
+// and indices for the reorder by decreasing |C|, then (after the caller's
+// sort, indices back in midx) the reorder itself, through mtmp.
+cudaError_t launch_harmonic_pack(Prod* dprods, const OpRef* dops, int nops, int64_t max_n, cudaStream_t s);
+cudaError_t launch_mag_keys(Prod* dprods, const OpRef* dops, int nops, int64_t max_n, cudaStream_t s);
+cudaError_t launch_mag_reorder(Prod* dprods, const OpRef* dops, int nops, int64_t max_n, cudaStream_t s);
+
 cudaError_t launch_dense_plan(const Prod* dprods, const int32_t* ddense_prods,
                               const int64_t* dblock_begin, int ndense, int64_t nblocks_total,
                               DenseTask* dtasks, int64_t task_cap, int64_t* dtask_count,
@@ -339,8 +398,15 @@ cudaError_t launch_split_sample(const Prod* dprods, int prod, int nbins, int64_t
                                 unsigned long long* dhist, cudaStream_t s);
 // accumulation of every hash-path product's tiles (and Poisson tiles on the
 // dense path): poly / pseries say which kinds the list holds
+// Ceiling probe: updates insert-or-adds (mode 0) or plain adds (mode 1) of
+// keys from `distinct` values into a zeroed table of `slots` (a power of two)
+// 16-byte slots; fails counts lanes that found no slot.
+cudaError_t launch_probe_table_update(uint64_t* table, uint64_t slots, int64_t distinct, int64_t updates,
+                                      int mode, unsigned long long* fails, cudaStream_t s);
+// (trunc: products truncated by coefficient magnitude or harmonic order, in a
+// kernel of their own)
 cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
-                               int nhash, bool poly, bool pseries, int grid, cudaStream_t s);
+                               int nhash, bool poly, bool pseries, bool trunc, int grid, cudaStream_t s);
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
 // cstat: nchunks zeroed words of scan state; sync: two zeroed int64 (a
 // ticket counter, then an error flag set when a bounded wait gave up); scan:

@@ -1,4 +1,4 @@
-// Peak-rate probes for the roofline of the dense path.  The paper measures a
+// Peak-rate probes for the rooflines of the dense and the hash path.  The paper measures a
 // multiplication by its clock cycles per monomial-by-monomial multiplication
 // (Sec. 5) and calls a kernel optimal when that count approaches the cost of
 // one coefficient multiply-add.  On the GPU the dense path's multiply-add is a
@@ -142,6 +142,54 @@ extern "C" double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaFree(sink);
+  if (cudaGetLastError() != cudaSuccess) best = -1.0;
+  cudaSetDevice(prev);
+  return best;
+}
+
+// The hash path's ceiling (Sec. 3.2: the highly sparse product accumulates
+// into a hash table; here an open-addressing table in device memory): random
+// insert-or-adds at a given table size and key count, in the insert routine
+// of the polynomial kernel, with nothing else in the loop.
+extern "C" double kr_probe_table_update_rate(int32_t device, int32_t log2_slots, int64_t distinct,
+                                             int64_t updates, int32_t mode, int32_t reps) {
+  if (log2_slots < 10 || log2_slots > 30 || distinct < 1 || updates < 1 || (mode != 0 && mode != 1) ||
+      distinct > (int64_t(1) << log2_slots) * 7 / 10)
+    return -1.0;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return -1.0; }
+  const uint64_t slots = uint64_t(1) << log2_slots;
+  uint64_t* table = nullptr;
+  unsigned long long* fails = nullptr;
+  if (cudaMalloc(&table, slots * 16) != cudaSuccess || cudaMalloc(&fails, 8) != cudaSuccess) {
+    cudaGetLastError();
+    if (table) cudaFree(table);
+    cudaSetDevice(prev);
+    return -1.0;
+  }
+  double best = -1.0;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  unsigned long long hf = 0;
+  for (int r = 0; r < (reps > 0 ? reps : 5) + 1; ++r) {
+    cudaMemset(table, 0, slots * 16);
+    cudaMemset(fails, 0, 8);
+    cudaEventRecord(a, 0);
+    launch_probe_table_update(table, slots, distinct, updates, mode, fails, 0);
+    cudaEventRecord(b, 0);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaMemcpy(&hf, fails, 8, cudaMemcpyDeviceToHost);
+    if (hf) { best = -1.0; break; }
+    if (r > 0 && ms > 0.f) best = std::max(best, (double)updates / (ms * 1e-3));
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(table);
+  cudaFree(fails);
   if (cudaGetLastError() != cudaSuccess) best = -1.0;
   cudaSetDevice(prev);
   return best;

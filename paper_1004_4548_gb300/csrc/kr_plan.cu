@@ -155,6 +155,31 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     if (kr > lim) { pl.st = KR_ERR_OVERFLOW; return; }
     P.krange = (int64_t)kr;
   }
+  // ---- truncation by harmonic order (Sec. 3), Poisson series: each emitted
+  // term is tested in the kernels against the packed multipliers
+  if (o.trunc_harmonic) {
+    uint32_t m = o.harmonic_mask ? o.harmonic_mask : 0xffffffffu;
+    if (P.nt < 32) m &= (1u << P.nt) - 1u;
+    if (P.nt == 0 || m == 0) { pl.st = KR_ERR_INVALID; return; }
+    int counted = 0;
+    for (int k = 0; k < P.nt; ++k) {
+      if (!((m >> k) & 1u)) continue;
+      if (rf[2 * MAXV + k] > 32767 || rg[2 * MAXV + k] > 32767) { pl.st = KR_ERR_INVALID; return; }
+      ++counted;
+    }
+    if (o.harmonic_order < 0) { pl.empty = true; return; }   // no term has a negative order
+    P.htrunc = 1;
+    P.hmask = m;
+    P.hN = o.harmonic_order;
+    P.hwords = (counted + 1) / 2;
+  }
+  // ---- truncation by coefficient magnitude (Sec. 3), float64 coefficients
+  if (o.coef_min != 0.0) {
+    if (!job.f64 || !(o.coef_min > 0.0) || std::isinf(o.coef_min)) { pl.st = KR_ERR_INVALID; return; }
+    P.ctrunc = 1;
+    // Poisson tiles form (C_f / 2) * C_g: halving both sides is exact
+    P.cmin = P.nt > 0 ? o.coef_min * 0.5 : o.coef_min;
+  }
   // ---- window of output keys (the whole range unless one was asked for)
   P.klo = 0;
   P.kspan = P.krange;
@@ -177,12 +202,19 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     if (o.path == KR_PATH_DENSE) {
       if (!fits) { pl.st = KR_ERR_INVALID; return; }
       P.path = PATH_DENSE;
-    } else if (o.path == KR_PATH_HASH) {
+    } else if (o.path == KR_PATH_HASH || P.ctrunc) {
+      // a coefficient bound usually keeps a small part of the product: a
+      // table sized by the estimate of the kept keys beats clearing and
+      // compacting an array over the whole key range
       P.path = PATH_HASH;
     } else {
       const bool dense_enough = (double)P.krange <= DENSE_POISSON_KAPPA * 2.0 * pairs + 65536.0;
       P.path = (fits && dense_enough) ? PATH_DENSE : PATH_HASH;
     }
+  } else if (P.ctrunc) {
+    // a coefficient bound walks the operands by decreasing |C|, which the
+    // block-by-block dense kernel (it needs code order) cannot do
+    P.path = PATH_HASH;
   } else if (o.path == KR_PATH_DENSE) {
     if ((double)P.kspan * 8.0 > (double)DENSE_MAX_BYTES || P.krange > INT32_MAX) {
       pl.st = KR_ERR_INVALID;
@@ -214,6 +246,11 @@ void plan_product(const Job& job, const int32_t* rf, const int32_t* rg, int num_
     op.nkeep = op.n;
     plan_sort(op, kr, which ? &pl.passes_g : &pl.passes_f, &pl.radix_sort_n);
     pl.op_bytes[which] = op.n * (8 * 7 + 1) + 8 * 256;
+    if (P.htrunc) pl.op_bytes[which] += op.n * 8 * P.hwords;
+    if (P.ctrunc) {
+      pl.op_bytes[which] += op.n * (8 * 4 + mag_tmp_bytes_per_term(P));
+      pl.radix_sort_n = std::max(pl.radix_sort_n, op.n);   // the reorder by magnitude
+    }
   }
   // ---- accumulators
   if (P.path == PATH_DENSE && P.nt > 0) {

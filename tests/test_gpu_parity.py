@@ -305,6 +305,11 @@ def test_peak_probes_report_rates(kron):
     rsplit = kron.kr_probe_smem_accumulate_rate(0, 2)
     assert r64 > 1e10 and rsplit > 1e10
     assert rsplit > 0.8 * r64
+    # the hash path's ceiling: random insert-or-adds and plain adds in a 2^22-slot table
+    ins = kron.kr_probe_table_update_rate(22, 1 << 20, 1 << 23, 0, 0, 2)
+    add = kron.kr_probe_table_update_rate(22, 1 << 20, 1 << 23, 1, 0, 2)
+    assert ins > 1e9 and add > 1e9
+    assert kron.kr_probe_table_update_rate(22, 1 << 22, 1 << 23, 0, 0, 1) < 0   # load above 0.7 refused
 
 
 def test_bounded_wait_gives_up_and_reports(kron):
