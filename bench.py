@@ -14,7 +14,10 @@ Poisson path as secondary measurements under "paths".
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Under torchrun each rank runs its own replica of the workload (independent
-products, no collective on the data path): "scaling": "weak".
+products, no collective on the data path): "scaling": "weak".  With several
+ranks the line also carries "sharded": one large product (full-size
+Fateman) split over the ranks by output key window and gathered with one
+all_gather, strong scaling.
 """
 from __future__ import annotations
 
@@ -53,8 +56,9 @@ def parse():
     ap.add_argument("--batch-products", type=int, default=4096, help="products in the uneven batch")
     ap.add_argument("--cpu-full", action="store_true",
                     help="time the oracle on the whole dense and hash workloads, one thread and every core, and exit")
-    ap.add_argument("--case", default="", choices=["", "cfg3", "cfg4s", "cfg4"],
-                    help="profiling runs: time only this secondary case (cfg4s = cfg4 at 5000 terms)")
+    ap.add_argument("--case", default="", choices=["", "cfg3", "cfg4s", "cfg4", "cfg4h", "cfg2"],
+                    help="profiling runs: time only this case (cfg4s = cfg4 at 5000 terms, cfg4h = cfg4 on "
+                         "the hash path, cfg2 = the headline product)")
     return ap.parse_args()
 
 
@@ -459,6 +463,10 @@ def main():
         ctx.trim()
         batched = time_batched(kron, ctx, dev, args.batch_products)
 
+    # ---- one product split over the ranks (only with several ranks)
+    sharded = None
+    if world > 1 and not args.no_paths:
+        sharded = time_sharded(kron, ctx, dev, stream, world, rank, max(3, args.steps // 2), 2)
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -476,6 +484,8 @@ def main():
                 if clk.get("sm_mhz") else None,
                 "paths": paths,
                 "batched": batched}
+        if sharded is not None:
+            line["sharded"] = sharded
         line["cpu_baseline"] = None if args.no_cpu else cpu_baseline(f, g)
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -497,6 +507,11 @@ def profile_case(args):
         r = time_poly(kron, ctx, *workload_cfg3(), dev, stream, flush, "hash_insert", args.steps)
     elif args.case == "cfg4":
         r = time_pseries(kron, ctx, *workload_cfg4(), dev, stream, flush, args.steps)
+    elif args.case == "cfg4h":
+        r = time_pseries(kron, ctx, *workload_cfg4(), dev, stream, flush, args.steps, path=kron.KR_PATH_HASH)
+    elif args.case == "cfg2":
+        from workloads import workload_cfg2
+        r = time_poly(kron, ctx, *workload_cfg2(), dev, stream, flush, "dense_accum", args.steps)
     else:
         f, g = workload_cfg4(5000)
         r = time_pseries(kron, ctx, f, g, dev, stream, flush, args.steps)
@@ -572,28 +587,34 @@ def time_batched(kron, ctx, dev, nprod):
                                     "wall_s": pt, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                                     "p99_ms": float(np.percentile(lat, 99) * 1e3),
                                     "gpu_launches": p_launches}}
-    # CUDA graph replay of prepared batches against kron_mul_batch, same chunks
-    graph = {"chunks": 0, "replay_s": 0.0, "batch_call_s": 0.0, "products": 0}
-    for a in range(0, min(nprod, 512), chunk):
+    # CUDA graph replay of prepared batches against kron_mul_batch: the whole
+    # uneven batch, in the same chunks, each chunk's graph replayed twice
+    graph = {"chunks": 0, "replay_s": 0.0, "batch_call_s": 0.0, "products": 0, "graph_kernels": 0,
+             "batch_call_launches": 0}
+    for a in range(0, nprod, chunk):
         part = D[a:a + chunk]
         pb = kron.PreparedBatch(part, device=dev.index or 0)
         pb.launch()
         torch.cuda.synchronize()
-        reps = 3
+        reps = 2
         t = time.perf_counter()
         for _ in range(reps):
             pb.launch()
         torch.cuda.synchronize()
         graph["replay_s"] += (time.perf_counter() - t) / reps
         assert all(r["status"] == 0 for r in pb.results())
+        graph["graph_kernels"] += pb.graph_kernels()
         pb.close()
+        l0 = ctx.launch_count()
         t = time.perf_counter()
         for _ in range(reps):
             kron.kron_mul_batch(part, ctx=ctx)
         torch.cuda.synchronize()
         graph["batch_call_s"] += (time.perf_counter() - t) / reps
+        graph["batch_call_launches"] += (ctx.launch_count() - l0) // reps
         graph["chunks"] += 1
         graph["products"] += len(part)
+        ctx.trim()
     graph["replay_products_per_s"] = graph["products"] / graph["replay_s"]
     graph["batch_call_products_per_s"] = graph["products"] / graph["batch_call_s"]
     res["cuda_graph"] = graph
@@ -625,7 +646,7 @@ def time_batched(kron, ctx, dev, nprod):
         rate = frac * cap
         t_arr = arrival_times(nreq, rate, seed=99)
         reqs = [Request(f, g, float(a)) for (f, g), a in zip(D[:nreq], t_arr)]
-        server = Server(device=dev.index or 0, workers=2, max_batch=chunk, mem_budget=60e9)
+        server = Server(device=dev.index or 0, workers=2, max_batch=chunk, mem_budget=60e9)   # library defaults
         st = server.run(reqs, time_limit=60.0)
         server.close()
         reqs1 = [Request(f, g, float(a)) for (f, g), a in zip(D[:nreq], t_arr)]
@@ -635,12 +656,54 @@ def time_batched(kron, ctx, dev, nprod):
             "continuous_batching": {"completed": st.completed, "products_per_s": st.products_per_s,
                                     "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_batch": st.mean_batch,
                                     "batches": st.batches, "failed": st.extra.get("failed", 0),
-                                    "errors": st.extra.get("errors", [])},
+                                    "errors": st.extra.get("errors", []),
+                                    "policy": {"giant_policy": server.giant_policy, "giant": server.giant,
+                                               "work_cap": server.work_cap, "workers": len(server.workers)}},
             "one_by_one": {"completed": st1.completed, "products_per_s": st1.products_per_s,
                            "p50_ms": st1.p50_ms, "p99_ms": st1.p99_ms,
                            "note": "requests still queued at the time limit are not counted"}}
     res["serving"] = serve
     return res
+
+
+def time_sharded(kron, ctx, dev, stream, world, rank, steps, warmup):
+    """One large product split over the ranks by output key window (Sec. 4's
+    disjoint output ranges): full-size Fateman, rank r computing window r of
+    equal sampled work, then the packed all_gather of the windows' terms, so
+    that every rank holds the whole product.  Strong scaling; the time is the
+    maximum over ranks."""
+    import torch
+    import torch.distributed as dist
+    from paper_1004_4548_gb300 import shard
+    from workloads import Poly, fateman
+    f, g = fateman()
+    F = Poly(torch.from_numpy(f.exps).to(dev), torch.from_numpy(f.coef).to(dev))
+    G = Poly(torch.from_numpy(g.exps).to(dev), torch.from_numpy(g.coef).to(dev))
+    cuts = shard.split_points(F, G, world, ctx=ctx)
+    times, wtimes, nterms = [], [], 0
+    for it in range(warmup + steps):
+        dist.barrier()
+        torch.cuda.synchronize()
+        a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        part = shard.mul_window(F, G, cuts[rank], cuts[rank + 1], ctx=ctx)
+        m.record(stream)
+        whole = shard.gather_parts(part)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if it >= warmup:
+            t = torch.tensor([a.elapsed_time(b), a.elapsed_time(m)], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            times.append(float(t[0]))
+            wtimes.append(float(t[1]))
+        nterms = int(whole[-1].shape[0])
+    ms = statistics.mean(times)
+    tp = f.n * g.n
+    return {"workload": "Fateman's benchmark at full size, 46376 x 46376 terms, split by output key window",
+            "ranks": world, "scaling": "strong", "ms_per_step": ms, "value": tp / (ms * 1e-3) / 1e6,
+            "unit": UNIT, "window_ms_max": statistics.mean(wtimes), "output_terms": nterms,
+            "cuts": [int(c) for c in cuts],
+            "exchange": "one all_gather of the term counts and one of the packed windows (NCCL)"}
 
 
 def kept_pairs(f, g, N):

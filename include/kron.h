@@ -324,6 +324,9 @@ kr_status kron_batch_launch(kr_batch* b, kr_stream stream);
  * batch again for it. */
 kr_status kron_batch_results(kr_batch* b, kr_result* res, int32_t njobs);
 void kron_batch_destroy(kr_batch* b);
+/* Kernel launches in one replay of a prepared batch (the kernel nodes of its
+ * graph), or -1 on failure. */
+int64_t kron_batch_graph_kernels(const kr_batch* b);
 
 /* Work histogram of one product for splitting it into output key windows:
  * nsamples term pairs drawn uniformly (from a counter-based hash of seed) are

@@ -5,12 +5,15 @@ The paper picks the algorithm from the densities of the factors (Sec. 3.2)
 without a threshold; here the choice is measured.  Products are grouped into
 shape classes by kind (polynomial / Poisson series), the magnitude of the
 term-product count and, for polynomials, the ratio of the code range W to the
-term-product count.  For every class seen in a sample of the uneven batch,
-each candidate configuration multiplies representative products (timed with
-CUDA events around the call, median of three), and the fastest is stored in a
-JSON table.  opts_for() looks a product's class up in the table.
+term-product count.  For every class of the uneven batch, the class's
+products (up to `per_class` of them) are multiplied as one batch
+(kron_mul_batch, the way the options are used), once with the library's own
+choices and once per candidate configuration (wall time around the call,
+median of three after a warm-up).  A class gets a table entry only when a
+candidate beats the library's choices by more than `margin`; every other
+class keeps them.  opts_for() looks a product's class up in the table.
 
-  python -m paper_1004_4548_gb300.autotune --out tuned.json [--products 512]
+  python -m paper_1004_4548_gb300.autotune --out tuned.json [--products 4096]
 """
 from __future__ import annotations
 
@@ -95,22 +98,20 @@ def opts_for(f, g, table: dict | None = None) -> dict:
     return o
 
 
-def _time_one(kron, ctx, f, g, o, reps=3):
+def _time_batch(kron, ctx, pairs, o, reps=3):
     import torch
+    opts = [dict(o) for _ in pairs]
     ts = []
     for _ in range(reps + 1):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        if hasattr(f, "trig"):
-            kron.poisson_mul(f, g, ctx=ctx, **o)
-        else:
-            kron.poly_mul(f.exps, f.coef, g.exps, g.coef, ctx=ctx, **o)
+        kron.kron_mul_batch(pairs, ctx=ctx, opts=opts)
         torch.cuda.synchronize()
         ts.append(time.perf_counter() - t)
     return float(np.median(ts[1:]))
 
 
-def tune(products: int = 512, per_class: int = 2, seed_base: int = 5000) -> dict:
+def tune(products: int = 4096, per_class: int = 16, seed_base: int = 5000, margin: float = 0.03) -> dict:
     import torch
     import paper_1004_4548_gb300 as kron
     from workloads import PSeries, Poly, batch_mix
@@ -128,35 +129,37 @@ def tune(products: int = 512, per_class: int = 2, seed_base: int = 5000) -> dict
         classes.setdefault(class_key(feat), []).append((f, g, feat))
     table, report = {}, {}
     for key, items in sorted(classes.items()):
-        sample = items[:per_class]
-        cands = candidates(sample[0][2])
-        best, best_t = None, float("inf")
-        times = []
-        for o in cands:
-            t = 0.0
-            for f, g, _ in sample:
-                t += _time_one(kron, ctx, dev(f), dev(g), o)
-            times.append((o, t))
-            if t < best_t:
+        sample = [(dev(f), dev(g)) for f, g, _ in items[:per_class]]
+        t_def = _time_batch(kron, ctx, sample, {})
+        best, best_t = None, t_def
+        for o in candidates(items[0][2]):
+            t = _time_batch(kron, ctx, sample, o)
+            if t < best_t and t < t_def * (1.0 - margin):
                 best, best_t = o, t
-        table[key] = best
-        report[key] = {"n": len(items), "best": best, "ms": best_t * 1e3 / len(sample),
-                       "default_ms": _time_one(kron, ctx, dev(sample[0][0]), dev(sample[0][1]), {}) * 1e3}
+        if best is not None:
+            table[key] = best
+        report[key] = {"n": len(items), "sampled": len(sample), "best": best, "ms": best_t * 1e3,
+                       "default_ms": t_def * 1e3}
+        del sample
+        ctx.trim()
     return {"classes": table, "report": report,
             "candidates": {"dense_block_slots": DENSE_S, "hash_load_factor": HASH_ALPHA},
-            "sample": f"{products} products of the uneven batch, seeds {seed_base}+k, {per_class} per class"}
+            "sample": f"{products} products of the uneven batch, seeds {seed_base}+k; per class up to "
+                      f"{per_class} products as one batch; entries only where a candidate beats the "
+                      f"library's choices by more than {margin:.0%}"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=TABLE)
-    ap.add_argument("--products", type=int, default=512)
-    ap.add_argument("--per-class", type=int, default=2)
+    ap.add_argument("--products", type=int, default=4096)
+    ap.add_argument("--per-class", type=int, default=16)
+    ap.add_argument("--margin", type=float, default=0.03)
     a = ap.parse_args()
-    res = tune(a.products, a.per_class)
+    res = tune(a.products, a.per_class, margin=a.margin)
     with open(a.out, "w") as fh:
         json.dump(res, fh, indent=1, sort_keys=True)
-    print(f"{len(res['classes'])} classes tuned -> {a.out}")
+    print(f"{len(res['classes'])} of {len(res['report'])} classes take tuned options -> {a.out}")
 
 
 if __name__ == "__main__":

@@ -98,6 +98,7 @@ SIGNATURES = {
     "kron_batch_launch": (ctypes.c_int, [_vp, _vp]),
     "kron_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(kr_result), _i32]),
     "kron_batch_destroy": (None, [_vp]),
+    "kron_batch_graph_kernels": (_i64, [_vp]),
     "kron_fetch_pseries": (ctypes.c_int, [_vp, ctypes.POINTER(kr_pseries_out), _vp]),
 }
 
@@ -577,6 +578,10 @@ class PreparedBatch:
 
     def launch(self, stream=None):
         _check(self.L, None, self.L.kron_batch_launch(self.h, _stream_ptr(stream)), "kron_batch_launch")
+
+    def graph_kernels(self) -> int:
+        """Kernel launches in one replay (the kernel nodes of the captured graph)."""
+        return int(self.L.kron_batch_graph_kernels(self.h))
 
     def results(self):
         """Statuses and device views after the launch's stream has been synchronised."""

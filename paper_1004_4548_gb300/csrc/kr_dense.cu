@@ -498,8 +498,7 @@ cudaError_t launch_dense_accum(const Prod* dprods, const DenseTask* dtasks,
                                const int64_t* dtask_count, int64_t task_cap, int64_t* dtask_next,
                                int grid, int64_t max_S, cudaStream_t s) {
   const size_t smem = (size_t)max_S * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_dense_accum, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_dense_accum, (size_t)smem);
   if (e != cudaSuccess) return e;
   // persistent grid: every CTA that fits on the GPU at once (grid = SMs on entry)
   int per_sm = 0;

@@ -517,7 +517,7 @@ cudaError_t launch_front_cluster(Prod* dprods, const OpRef* dops, int nops, int6
   if (nops <= 0) return cudaSuccess;
   const int64_t lw = cluster_slice_words(max_key_range);
   const size_t smem = (size_t)(2 * lw) * 4;
-  cudaError_t e = cudaFuncSetAttribute(k_front_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit((const void*)k_front_cluster, (size_t)smem);
   if (e != cudaSuccess) return e;
   k_front_cluster<<<(unsigned)(nops * CL_CTAS), CL_THREADS, smem, s>>>(dprods, dops);
   return cudaGetLastError();

@@ -346,6 +346,11 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
 // ---------------------------------------------------------------------------
 // launchers (host side); each returns cudaGetLastError()
 // ---------------------------------------------------------------------------
+// Raises (never lowers) a kernel's dynamic shared memory limit to `bytes` on
+// the current device, thread-safely; launchers call it before launching with
+// more than 48 KB.
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
+
 struct OpRef {      // (product, operand) pair addressed by a per-operand kernel
   int32_t prod;
   int32_t which;    // 0 = f, 1 = g
@@ -443,6 +448,17 @@ cudaError_t order_by_bitmap(const uint64_t* key, const uint64_t* val, uint64_t* 
                             int64_t n, int64_t krange, void* scratch, cudaStream_t s);
 cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
                           int64_t krange, int64_t* bins, cudaStream_t s);
+// Large outputs over code ranges whose one-bit-per-code bitmap would not stay
+// in L2 (above 2^30 codes, 128 MB): terms bucketed by 2^20 codes, then ranked
+// in each bucket by a shared-memory bitmap; sorted in place (key2/val2: n
+// terms of scratch; bins: order_buckets_scratch(krange) int64).
+constexpr int64_t ORDER_BUCKET_MIN_N = int64_t(1) << 20;
+constexpr int64_t ORDER_BUCKET_MIN_RANGE = int64_t(1) << 30;
+constexpr int64_t ORDER_MAX_BUCKETS = int64_t(1) << 22;
+int64_t order_buckets(int64_t krange);
+int64_t order_buckets_scratch(int64_t krange);
+cudaError_t order_by_buckets(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
+                             int64_t krange, int64_t* bins, cudaStream_t s);
 
 // Decode of one product's sorted terms.  With dev_count, n is a capacity and
 // the count is the product's device-side nout (0 when its status is set);

@@ -113,6 +113,199 @@ __global__ void __launch_bounds__(ORD_THREADS) k_seg_sort(const uint64_t* __rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// bucketed bitmap ordering (large outputs): a counting pass and a scatter put
+// the terms in buckets of BK_CODES consecutive codes (bucket order, not yet
+// sorted inside); then one CTA per bucket sets the bits of its keys in a
+// bitmap of the bucket's codes in shared memory, turns it into per-word
+// prefix counts, and writes every term at its rank.  Every random access
+// (bit set, rank lookup) stays in shared memory and every write stays inside
+// the bucket's own output range, where L2 combines them.
+// ---------------------------------------------------------------------------
+constexpr int BK_LOG2 = 20;                       // codes per bucket: 2^20
+constexpr int64_t BK_CODES = int64_t(1) << BK_LOG2;
+constexpr int BK_WORDS = (int)(BK_CODES / 64);    // 16384 bitmap words: 128 KB, prefixes 64 KB
+constexpr int BK_THREADS = 1024;
+
+int64_t order_buckets(int64_t krange) { return (krange + BK_CODES - 1) / BK_CODES; }
+int64_t order_buckets_scratch(int64_t krange) {
+  const int64_t nb = order_buckets(krange);
+  return 3 * (nb + 1) + scan_scratch_entries(nb);
+}
+
+// Counting and scatter by bucket, each CTA over one contiguous slice of the
+// terms: a shared-memory histogram of the slice, one global atomic per
+// (CTA, bucket) (the per-term global atomics of a direct count would pile
+// onto a few thousand counters), then in the scatter each term's place in its
+// bucket is the CTA's reserved base plus a shared-memory rank.
+constexpr int BK_CTA_THREADS = 512;
+constexpr int BK_MAX_SMEM_BUCKETS = 8192;   // histogram in shared memory up to this many buckets
+
+__device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  *a = min(n, (int64_t)blockIdx.x * per);
+  *b = min(n, *a + per);
+}
+
+__global__ void __launch_bounds__(BK_CTA_THREADS) k_bk_count(const uint64_t* __restrict__ key, int64_t n,
+                                                             int64_t nb, unsigned long long* __restrict__ cnt) {
+  extern __shared__ uint32_t bh[];
+  const bool local = nb <= BK_MAX_SMEM_BUCKETS;
+  if (local)
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) bh[b] = 0;
+  __syncthreads();
+  int64_t a, e;
+  bk_slice(n, &a, &e);
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
+    const uint64_t b = key[i] >> BK_LOG2;
+    if (b >= (uint64_t)nb) continue;
+    if (local) atomicAdd(&bh[b], 1u);
+    else atomicAdd(&cnt[b], 1ull);
+  }
+  __syncthreads();
+  if (local)
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x)
+      if (bh[b]) atomicAdd(&cnt[b], (unsigned long long)bh[b]);
+}
+
+__global__ void __launch_bounds__(BK_CTA_THREADS) k_bk_scatter(const uint64_t* __restrict__ key,
+                                                               const uint64_t* __restrict__ val, int64_t n,
+                                                               int64_t nb, const int64_t* __restrict__ off,
+                                                               unsigned long long* __restrict__ cur,
+                                                               uint64_t* __restrict__ okey,
+                                                               uint64_t* __restrict__ oval) {
+  extern __shared__ uint32_t bh[];   // [nb] slice counts, then ranks; [nb] bases (uint64 pairs)
+  const bool local = nb <= BK_MAX_SMEM_BUCKETS;
+  unsigned long long* base = (unsigned long long*)(bh + ((nb + 1) & ~int64_t(1)));
+  int64_t a, e;
+  bk_slice(n, &a, &e);
+  if (local) {
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) bh[b] = 0;
+    __syncthreads();
+    for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
+      const uint64_t b = key[i] >> BK_LOG2;
+      if (b < (uint64_t)nb) atomicAdd(&bh[b], 1u);
+    }
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+      base[b] = bh[b] ? atomicAdd(&cur[b], (unsigned long long)bh[b]) : 0ull;
+      bh[b] = 0;
+    }
+    __syncthreads();
+  }
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) {
+    const uint64_t k = key[i];
+    const int64_t b = (int64_t)(k >> BK_LOG2);
+    if (b >= nb) continue;
+    const uint64_t r = local ? base[b] + atomicAdd(&bh[b], 1u) : atomicAdd(&cur[b], 1ull);
+    const int64_t pos = off[b] + (int64_t)r;
+    if (pos < off[b + 1]) {
+      okey[pos] = k;
+      oval[pos] = val[i];
+    }
+  }
+}
+
+// One CTA per bucket b: terms [off[b], off[b+1]) of (key, val), written sorted
+// to the same range of (okey, oval).
+__global__ void __launch_bounds__(BK_THREADS) k_bk_rank(const uint64_t* __restrict__ key,
+                                                        const uint64_t* __restrict__ val,
+                                                        const int64_t* __restrict__ off,
+                                                        uint64_t* __restrict__ okey, uint64_t* __restrict__ oval) {
+  extern __shared__ __align__(16) unsigned char bk_smem[];
+  unsigned long long* bits = (unsigned long long*)bk_smem;      // [BK_WORDS]
+  uint32_t* pre = (uint32_t*)(bk_smem + 8 * BK_WORDS);          // [BK_WORDS] ones before the word
+  __shared__ uint32_t wsum[BK_THREADS / 32];
+  const int64_t b = blockIdx.x;
+  const int64_t s0 = off[b], s1 = off[b + 1];
+  if (s1 <= s0) return;
+  for (int w = threadIdx.x; w < BK_WORDS; w += blockDim.x) bits[w] = 0ull;
+  __syncthreads();
+  const uint64_t base = (uint64_t)b << BK_LOG2;
+  for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+    const uint32_t c = (uint32_t)(key[i] - base);   // < BK_CODES
+    atomicOr(&bits[c >> 6], 1ull << (c & 63));
+  }
+  __syncthreads();
+  // exclusive prefix of the words' popcounts: each thread owns BK_WORDS / BK_THREADS consecutive words
+  constexpr int PER = BK_WORDS / BK_THREADS;
+  const int w0 = threadIdx.x * PER;
+  uint32_t local[PER];
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    local[q] = tsum;
+    tsum += (uint32_t)__popcll(bits[w0 + q]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < BK_THREADS / 32 ? wsum[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < BK_THREADS / 32) wsum[lane] = v;
+  }
+  __syncthreads();
+  const uint32_t tbase = (warp > 0 ? wsum[warp - 1] : 0u) + x - tsum;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) pre[w0 + q] = tbase + local[q];
+  __syncthreads();
+  for (int64_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+    const uint64_t k = key[i];
+    const uint32_t c = (uint32_t)(k - base);
+    const uint32_t w = c >> 6;
+    const int64_t rank = (int64_t)pre[w] + __popcll(bits[w] & ((1ull << (c & 63)) - 1ull));
+    if (s0 + rank < s1) {
+      okey[s0 + rank] = k;
+      oval[s0 + rank] = val[i];
+    }
+  }
+}
+
+// Sorts (key, val)[0, n) by key (distinct keys < krange) in place, through
+// key2/val2 (n terms of scratch); bins: order_buckets_scratch(krange) int64.
+cudaError_t order_by_buckets(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
+                             int64_t krange, int64_t* bins, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  const int64_t nb = order_buckets(krange);
+  int64_t* off = bins;                                               // [nb + 1]
+  unsigned long long* cur = (unsigned long long*)(bins + nb + 1);    // [nb + 1]
+  cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int64_t) * 2 * (nb + 1), s);
+  if (e != cudaSuccess) return e;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // slices of at least 4096 terms, at most a few CTAs per SM
+  int64_t grid = (n + 4095) / 4096;
+  if (grid > (int64_t)sms * 4) grid = (int64_t)sms * 4;
+  if (grid < 1) grid = 1;
+  const bool local = nb <= BK_MAX_SMEM_BUCKETS;
+  const size_t csm = local ? (size_t)nb * 4 : 0;
+  const size_t ssm = local ? (size_t)((nb + 1) & ~int64_t(1)) * 4 + (size_t)nb * 8 : 0;
+  if ((e = raise_smem_limit((const void*)k_bk_count, csm)) != cudaSuccess ||
+      (e = raise_smem_limit((const void*)k_bk_scatter, ssm)) != cudaSuccess)
+    return e;
+  k_bk_count<<<(unsigned)grid, BK_CTA_THREADS, csm, s>>>(key, n, nb, (unsigned long long*)off);
+  e = launch_scan_exclusive(off, nb, off + nb, bins + 2 * (nb + 1), s);
+  if (e != cudaSuccess) return e;
+  k_bk_scatter<<<(unsigned)grid, BK_CTA_THREADS, ssm, s>>>(key, val, n, nb, off, cur, key2, val2);
+  const size_t smem = (size_t)BK_WORDS * 12;
+  e = raise_smem_limit((const void*)k_bk_rank, smem);
+  if (e != cudaSuccess) return e;
+  k_bk_rank<<<(unsigned)nb, BK_THREADS, smem, s>>>(key2, val2, off, key, val);
+  return cudaGetLastError();
+}
+
 int64_t order_bins(int64_t krange) { return (krange + ORD_C - 1) / ORD_C; }
 int64_t order_bins_scratch(int64_t krange) {
   const int64_t nb = order_bins(krange);
@@ -237,7 +430,7 @@ cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t
   k_bin_scatter<<<(unsigned)grid, 256, 0, s>>>(key, val, n, nb, off, cur, key2, val2);
   const int64_t nseg = (n + ORD_C - 1) / ORD_C;
   const int smem = (int)((sizeof(uint64_t) + sizeof(uint16_t)) * ORD_SEG);
-  e = cudaFuncSetAttribute(k_seg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = raise_smem_limit((const void*)k_seg_sort, (size_t)smem);
   if (e != cudaSuccess) return e;
   k_seg_sort<<<(unsigned)nseg, ORD_THREADS, smem, s>>>(key2, val2, off, nb, key, val);
   return cudaGetLastError();

@@ -223,13 +223,11 @@ cudaError_t launch_sort_small(Prod* dprods, const OpRef* dops, int nops, int met
                               cudaStream_t s) {
   if (nops <= 0) return cudaSuccess;
   if (method == SORT_BITMAP) {
-    cudaError_t e = cudaFuncSetAttribute(k_bitmap_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k_bitmap_sort, (size_t)smem);
     if (e != cudaSuccess) return e;
     k_bitmap_sort<<<nops, 1024, smem, s>>>(dprods, dops);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(k_bitonic_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = raise_smem_limit((const void*)k_bitonic_sort, (size_t)smem);
     if (e != cudaSuccess) return e;
     k_bitonic_sort<<<nops, 1024, smem, s>>>(dprods, dops);
   }

@@ -19,10 +19,14 @@ A batch is also capped in work (term-products): the oldest waiting request
 always starts the batch, and later requests join it only while the cap holds,
 so a small request never waits behind a very large one in the same batch
 and can overtake it on the other worker.  A request above `giant` term
-products runs in a batch of its own: it waits at the head of the queue until
-no batch is running (with giant_alone) and no other batch starts while it
-runs, so that the largest products, which set the tail latency, have the GPU
-to themselves.  A worker releases its
+products runs in a batch of its own.  With giant_policy "alone" it waits at
+the head of the queue until no batch is running and no other batch starts
+while it runs, so that it has the GPU to itself.  With "shared" it starts on
+the first free worker (at most one such request at a time) and the other
+workers go on serving the smaller requests meanwhile, which then never wait
+behind it.  A batch of one request goes through the single-product call
+(poly_mul / poisson_mul), which waits on the device once instead of three
+times.  A worker releases its
 context's cached scratch after a batch when it holds more than `trim_bytes`.
 A worker whose batch runs out of device memory releases its context's cached
 scratch, holds off new batches, waits until the other workers are idle and
@@ -90,12 +94,17 @@ class Server:
     """Continuous batching over `workers` contexts on one GPU."""
 
     def __init__(self, device: int = 0, workers: int = 2, mem_budget: float = 64e9,
-                 max_batch: int = 256, wave_pairs: int = 0, work_cap: float = 2e8,
-                 giant: float = 5e7, trim_bytes: float = 24e9, giant_alone: bool = True):
+                 max_batch: int = 256, wave_pairs: int = 0, work_cap: float = 5e7,
+                 giant: float = 2e7, trim_bytes: float = 24e9, giant_alone: bool = True,
+                 giant_policy: str = "shared"):
+        if giant_policy not in ("alone", "shared"):
+            raise ValueError("giant_policy must be 'alone' or 'shared'")
         self.device = device
         self.work_cap = work_cap
         self.giant = giant
         self.giant_alone = giant_alone
+        self.giant_policy = giant_policy
+        self.giants_running = 0
         self.trim_bytes = trim_bytes
         self.exclusive = False
         self.hold = 0             # workers retrying alone after running out of memory
@@ -122,6 +131,15 @@ class Server:
         return 64.0 * out_terms + 1e6
 
     def _mul(self, w: _Worker, batch: list[Request]):
+        if len(batch) == 1 and hasattr(batch[0].f.coef, "is_cuda"):
+            # one request: the single-product call (its outputs are the caller's tensors)
+            r = batch[0]
+            if r.poisson:
+                e, t, k, c, _ = B.poisson_mul(r.f, r.g, ctx=w.ctx, stream=w.stream)
+                return [{"status": 0, "nterms": int(c.shape[0]), "exps": e, "trig": t, "kind": k,
+                         "coef": c, "owned": True}]
+            e, c, _, _ = B.poly_mul(r.f.exps, r.f.coef, r.g.exps, r.g.coef, ctx=w.ctx, stream=w.stream)
+            return [{"status": 0, "nterms": int(c.shape[0]), "exps": e, "coef": c, "owned": True}]
         return B.kron_mul_batch([(r.f, r.g) for r in batch], ctx=w.ctx, stream=w.stream,
                                 wave_pairs=self.wave_pairs)
 
@@ -144,6 +162,30 @@ class Server:
                 self.hold -= 1
                 w.retrying = False
 
+    def _shared_batch(self, pending: list[Request], room: float):
+        """The next batch under giant_policy "shared": the oldest request that
+        is very large, alone, when it is the oldest of all and no other very
+        large one runs; otherwise the oldest smaller requests within the caps
+        (very large ones keep their place)."""
+        head = pending[0]
+        if head.pairs > self.giant:
+            if self.giants_running == 0:
+                return [head], self.predict_bytes(head)
+        batch, used, work = [], 0.0, 0.0
+        for r in pending:
+            if r.pairs > self.giant:
+                continue
+            b = self.predict_bytes(r)
+            if not batch:
+                if b > room and self.in_flight_bytes > 0:
+                    break   # wait for memory to come back
+            elif used + b > room or work + r.pairs > self.work_cap or len(batch) >= self.max_batch:
+                continue    # later, smaller requests may still fit
+            batch.append(r)
+            used += b
+            work += r.pairs
+        return batch, used
+
     def _run_batch(self, w: _Worker, batch: list[Request], t0: float, bytes_: float):
         import torch
         out = None
@@ -161,7 +203,10 @@ class Server:
                 # results are library-owned until the context's next batch: copy them out
                 for r, o in zip(batch, out):
                     r.status = o["status"]
-                    r.result = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in o.items()}
+                    if o.get("owned"):
+                        r.result = {k: v for k, v in o.items() if k != "owned"}
+                    else:
+                        r.result = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in o.items()}
                 w.stream.synchronize()
             done = time.perf_counter() - t0
             obs = {False: [0, 0], True: [0, 0]}
@@ -189,7 +234,10 @@ class Server:
                 pass
             with self.lock:
                 self.in_flight_bytes -= bytes_
-                self.exclusive = False if any(r.pairs > self.giant for r in batch) else self.exclusive
+                if any(r.pairs > self.giant for r in batch):
+                    self.exclusive = False
+                    if self.giant_policy == "shared":
+                        self.giants_running -= 1
                 w.busy = False
 
     def run(self, requests: list[Request], time_limit: float = 120.0) -> ServeStats:
@@ -217,7 +265,25 @@ class Server:
                     room = self.mem_budget - self.in_flight_bytes
                 batch, used, work = [], 0.0, 0.0
                 idle = all(not w.busy for w in self.workers)
-                if pending[0].pairs > self.giant and not idle and self.giant_alone:
+                if self.giant_policy == "shared":
+                    batch, used = self._shared_batch(pending, room)
+                    if batch:
+                        taken = set(id(r) for r in batch)
+                        pending = [r for r in pending if id(r) not in taken]
+                        w = free[0]
+                        with self.lock:
+                            w.busy = True
+                            self.in_flight_bytes += used
+                            if batch[0].pairs > self.giant:
+                                self.giants_running += 1
+                        w.thread = threading.Thread(target=self._run_batch, args=(w, batch, t0, used))
+                        w.thread.start()
+                        batches += 1
+                        sizes.append(len(batch))
+                        continue
+                    time.sleep(0.0002)   # nothing may start now
+                    continue
+                elif pending[0].pairs > self.giant and not idle and self.giant_alone:
                     # the oldest request is very large: no new batch starts
                     # until the GPU is free, then it runs alone
                     time.sleep(0.0002)

@@ -74,8 +74,11 @@ def mul_window(f, g, lo: int, hi: int, ctx=None, **opts):
 
 def gather_parts(part, group=None):
     """Concatenate every rank's part (tensors whose last axis is the term axis)
-    in rank order; every rank receives the whole.  Works with any backend that
-    supports all_gather for the part's device and dtypes."""
+    in rank order; every rank receives the whole.  The fields of a part are
+    packed into one byte buffer (each field padded to 8 bytes), so the gather
+    is one all_gather of the term counts and one of the packed buffers.  Works
+    with any backend that supports all_gather of int64 and uint8 tensors on
+    the part's device."""
     import torch
     import torch.distributed as dist
     world = dist.get_world_size(group)
@@ -85,15 +88,35 @@ def gather_parts(part, group=None):
     sizes_t = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
     dist.all_gather(sizes_t, mine, group=group)
     sizes = [int(x.item()) for x in sizes_t]
-    m = max(1, max(sizes))
-    out = []
+
+    def field_bytes(a, k):
+        rows = 1
+        for d in a.shape[:-1]:
+            rows *= int(d)
+        b = rows * k * a.element_size()
+        return b, (b + 7) // 8 * 8
+
+    def packed(k):
+        return sum(field_bytes(a, k)[1] for a in part)
+
+    m = max(8, max(packed(k) for k in sizes))
+    buf = torch.zeros(m, dtype=torch.uint8, device=dev)
+    o = 0
     for a in part:
-        pad = torch.zeros(tuple(a.shape[:-1]) + (m,), dtype=a.dtype, device=dev)
-        pad[..., :n] = a
-        bufs = [torch.empty_like(pad) for _ in range(world)]
-        dist.all_gather(bufs, pad, group=group)
-        out.append(torch.cat([b[..., :k] for b, k in zip(bufs, sizes)], dim=-1))
-    return tuple(out)
+        b, pb = field_bytes(a, n)
+        if b:
+            buf[o:o + b] = a.contiguous().view(-1).view(torch.uint8)
+        o += pb
+    bufs = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(bufs, buf, group=group)
+    pieces = [[] for _ in part]
+    for rb, k in zip(bufs, sizes):
+        o = 0
+        for q, a in enumerate(part):
+            b, pb = field_bytes(a, k)
+            pieces[q].append(rb[o:o + b].view(a.dtype).reshape(tuple(a.shape[:-1]) + (k,)))
+            o += pb
+    return tuple(torch.cat(p, dim=-1) for p in pieces)
 
 
 def sharded_mul(f, g, group=None, ctx=None, gather: bool = True, **opts):

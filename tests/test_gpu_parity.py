@@ -249,6 +249,23 @@ def test_table_full_regrows(kron):
     assert e.value.status == kron.KR_ERR_TABLE_FULL
 
 
+def test_large_table_regrows_and_float64(kron):
+    """Forced down to 2^20 slots, the MP-sparse product's 5.8 M keys overfill
+    the table: it grows until they fit, and the result is still exact.  A
+    float64 product with millions of output terms (a table far larger than
+    L2) matches within the tolerance."""
+    f, g = workload_cfg3()
+    r = oracle.poly_mul(f, g, nthreads=NT)
+    ex, cf = run_poly(kron, f, g, path=kron.KR_PATH_HASH, table_slots=1 << 20)
+    assert_poly_equal(ex, cf, r, "MP-sparse after regrowth")
+    f = random_poly(5, 3000, -20, 20, 5500, "f64")
+    g = random_poly(5, 2800, -20, 20, 5501, "f64")
+    r = oracle.poly_mul(f, g, nthreads=NT, keep_zero=True)
+    assert r.coef.shape[0] > 4_000_000
+    ex, cf = run_poly(kron, f, g, path=kron.KR_PATH_HASH)
+    assert_poly_close(ex, cf, r, REL, "large float64 hash product")
+
+
 def test_error_statuses(kron):
     f = random_poly(2, 50, -3, 3, 81)
     dup = Poly(np.concatenate([f.exps, f.exps[:, :1]], axis=1), np.concatenate([f.coef, f.coef[:1]]))

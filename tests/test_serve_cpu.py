@@ -116,7 +116,7 @@ def test_giants_run_alone_and_results_match_requests(monkeypatch):
     monkeypatch.setattr(serve, "_Worker", _FakeWorker)
     log, lock, active = [], threading.Lock(), [0]
     monkeypatch.setattr(B, "kron_mul_batch", _recording_batch(log, lock, active))
-    srv = serve.Server(workers=2, giant=500_000)   # 900 x 900 = 810,000 pairs: a giant
+    srv = serve.Server(workers=2, giant=500_000, giant_policy="alone")   # 900 x 900 = 810,000 pairs: a giant
     reqs = _mixed_requests(120)
     st = srv.run(reqs, time_limit=60)
     assert st.completed == 120 and st.extra["failed"] == 0
@@ -147,3 +147,42 @@ def test_batches_respect_the_work_and_memory_caps(monkeypatch):
     assert max(len(s) for s, _ in log) <= 4
     # arrival order is kept among requests that fit: the first batch starts with the oldest
     assert log[0][0][0] == 25
+
+
+def test_shared_policy_runs_one_giant_at_a_time_beside_small_batches(monkeypatch):
+    """giant_policy "shared": a very large request starts on a free worker
+    without waiting for the others, never beside another very large one, and
+    smaller requests keep being served on the other worker meanwhile."""
+    import time
+    monkeypatch.setattr(serve, "_Worker", _FakeWorker)
+    lock = threading.Lock()
+    state = {"giants": 0, "max_giants": 0, "small_beside_giant": 0, "batches": []}
+
+    def run(pairs, ctx=None, stream=None, wave_pairs=0):
+        sizes = [f.coef.shape[0] * g.coef.shape[0] for f, g in pairs]
+        giant = any(p > 500_000 for p in sizes)
+        with lock:
+            state["batches"].append(sizes)
+            if giant:
+                state["giants"] += 1
+                state["max_giants"] = max(state["max_giants"], state["giants"])
+            elif state["giants"]:
+                state["small_beside_giant"] += 1
+        time.sleep(0.004 if giant else 0.0005)
+        with lock:
+            if giant:
+                state["giants"] -= 1
+        return [{"status": 0, "nterms": int(p), "coef": torch.ones(1)} for p in sizes]
+
+    monkeypatch.setattr(B, "kron_mul_batch", run)
+    srv = serve.Server(workers=2, giant=500_000, giant_policy="shared")
+    reqs = _mixed_requests(160, seed=3)
+    st = srv.run(reqs, time_limit=60)
+    assert st.completed == 160 and st.extra["failed"] == 0
+    assert state["max_giants"] == 1
+    assert state["small_beside_giant"] > 0
+    for sizes in state["batches"]:
+        if any(p > 500_000 for p in sizes):
+            assert len(sizes) == 1
+    for r in reqs:
+        assert r.status == 0 and r.result["nterms"] == r.pairs

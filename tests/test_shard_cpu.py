@@ -98,3 +98,42 @@ def test_gather_of_windows_over_gloo(world, forced):
     assert sum(n for _, _, n, _ in out) == r.coef.shape[0]
     if forced:
         assert out[1][2] == 0   # the empty window contributes nothing and breaks nothing
+
+
+def _mixed_rank(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["GLOO_SOCKET_IFNAME"] = os.environ.get("GLOO_SOCKET_IFNAME", "lo")
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        sizes = [5, 0, 3][:world]
+
+        def part_of(r):
+            k = sizes[r]
+            base = 100 * r
+            return (torch.arange(2 * k, dtype=torch.int32).reshape(2, k) + base,       # exponents
+                    torch.arange(3 * k, dtype=torch.int32).reshape(3, k) - base,       # trig multipliers
+                    (torch.arange(k, dtype=torch.int64) % 2).to(torch.uint8),          # kinds: odd byte counts
+                    torch.arange(k, dtype=torch.float64) * 0.5 + r)                   # coefficients
+        got = shard.gather_parts(part_of(rank))
+        want = [torch.cat(x, dim=-1) for x in zip(*(part_of(r) for r in range(world)))]
+        q.put((rank, all(torch.equal(a, b) and a.dtype == b.dtype for a, b in zip(got, want))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gather_of_mixed_fields_over_gloo():
+    """Poisson-like parts (int32 rows, uint8 kinds, float64 coefficients; one
+    rank empty): the packed gather restores every field in rank order."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_mixed_rank, args=(k, 3, port, q)) for k in range(3)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(3)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, ok in out), out
