@@ -10,6 +10,7 @@ ones must not see leftovers of the earlier ones) and watches the device's
 free memory across them.  This file is collected last so that a failure here
 comes after every other test has run.
 """
+import gc
 import os
 
 import numpy as np
@@ -85,11 +86,19 @@ def test_static_scratch_entry_matches_oracle_in_a_row(kron):
              (random_poly(2, 3000, -300, 300, 503), random_poly(2, 2500, -300, 300, 504))]
     prepared = [_case(f, g) for f, g in cases]
     outs = [torch.empty(W, dtype=ops[1].dtype, device="cuda") for ops, W, _, _ in prepared]
-    # first call: the library looks up the array's address and the kernels load
-    kron.kron_dense_product_static(*prepared[0][0], prepared[0][1], out=outs[0])
+    # first calls: the library looks up the array's address, and every kernel
+    # the loop below runs (the library's and torch's fill and copy) is loaded
+    # (CUDA loads a module's code into device memory on first use)
+    for (ops, W, _, _), out in zip(prepared, outs):
+        out.fill_(7)
+        kron.kron_dense_product_static(*ops, W, out=out)
+        out.cpu()
     torch.cuda.synchronize()
+    gc.collect()
     free0 = torch.cuda.mem_get_info()[0]
-    used0 = torch.cuda.memory_allocated()
+    # torch's count of device allocation requests (cumulative; frees of other
+    # tests' tensors do not move it)
+    allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
     for rnd in range(2):
         for k, ((ops, W, want, mass), out) in enumerate(zip(prepared, outs)):
             out.fill_(7)   # garbage the call must overwrite in full
@@ -97,7 +106,7 @@ def test_static_scratch_entry_matches_oracle_in_a_row(kron):
             torch.cuda.synchronize()
             _check(out.cpu().numpy(), want, mass, f"round {rnd} case {k}")
     assert torch.cuda.mem_get_info()[0] == free0, "device memory was allocated during the calls"
-    assert torch.cuda.memory_allocated() == used0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs0
 
 
 def test_static_scratch_entry_rejects_too_large(kron):
