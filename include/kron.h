@@ -413,6 +413,16 @@ double kr_probe_smem_accumulate_rate(int32_t device, int32_t reps);
 double kr_probe_table_update_rate(int32_t device, int32_t log2_slots, int64_t distinct, int64_t updates,
                                   int32_t mode, int32_t reps);
 
+/* Chip-wide arithmetic rates of the coefficient multiply-add forms the kernels
+ * use (Sec. 5 calls a multiplication optimal when its cost per
+ * monomial-by-monomial multiplication nears that of one coefficient
+ * multiply-add): kind 0 = 64 x 64 -> 64-bit integer multiply-add (int64
+ * coefficients), 1 = 32 x 32 -> 64-bit multiply-add (int64 coefficients that
+ * fit 32 bits), 2 = float64 FMA; best of `reps` launches on CUDA device
+ * `device`, in operations per second; < 0 on failure.  Allocates and frees
+ * 8 KB; synchronises the device's default stream. */
+double kr_probe_alu_rate(int32_t device, int32_t kind, int32_t reps);
+
 /* Self-test of the library's bounded device waits (the compaction's look-back
  * over preceding chunks): runs the wait against a predecessor that never
  * publishes, on CUDA device `device`, and returns KR_ERR_TIMEOUT when the wait

@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     KR_PATH_AUTO, KR_PATH_DENSE, KR_PATH_HASH, KR_MAXV,
     Context, KronError, context, load, lib_path,
     kron_plan, kron_encode, kron_decode, poly_mul, poisson_mul, kr_probe_smem_atomic_rate,
-    kr_probe_smem_accumulate_rate, kr_probe_table_update_rate, kr_selftest_bounded_wait,
+    kr_probe_smem_accumulate_rate, kr_probe_table_update_rate, kr_probe_alu_rate,
+    kr_selftest_bounded_wait,
     kron_dense_product_static, kron_mul_batch, PreparedBatch,
 )

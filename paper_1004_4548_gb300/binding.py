@@ -80,6 +80,7 @@ SIGNATURES = {
     "kr_probe_smem_accumulate_rate": (ctypes.c_double, [_i32, _i32]),
     "kr_selftest_bounded_wait": (ctypes.c_int, [_i32]),
     "kr_probe_table_update_rate": (ctypes.c_double, [_i32, _i32, _i64, _i64, _i32, _i32]),
+    "kr_probe_alu_rate": (ctypes.c_double, [_i32, _i32, _i32]),
     "kron_dense_product_static": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _i64, ctypes.c_int, _i64,
                                                  _vp, _vp]),
     "kron_plan": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp]),
@@ -277,6 +278,11 @@ def kr_probe_table_update_rate(log2_slots: int, distinct: int, updates: int, mod
     """Random insert-or-adds (mode 0) or plain adds (mode 1) per second into a
     table of 2^log2_slots 16-byte slots (the hash path's ceiling)."""
     return float(load().kr_probe_table_update_rate(device, log2_slots, distinct, updates, mode, reps))
+
+
+def kr_probe_alu_rate(kind: int, device: int = 0, reps: int = 5) -> float:
+    """Multiply-adds per second: 0 = int64, 1 = 32 x 32 -> 64 bit, 2 = float64 FMA."""
+    return float(load().kr_probe_alu_rate(device, kind, reps))
 
 
 def kr_selftest_bounded_wait(device: int = 0) -> int:

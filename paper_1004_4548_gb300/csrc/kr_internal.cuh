@@ -157,6 +157,9 @@ struct Prod {
   int64_t task_begin;   // first task index of this product (hash tiles)
   int64_t ntasks;
   // compaction
+  uint32_t* live;       // dense array, two-pass compaction: per 64-slot row, the live bits of
+                        // its even and of its odd slots (two words), written by the counting
+                        // pass so that the writing pass loads only the pairs holding a live slot
   int64_t chunk;        // accumulator slots per compaction chunk
   int64_t nchunks;
   int64_t chunk_begin;  // first chunk index of this product
@@ -412,6 +415,10 @@ cudaError_t launch_probe_table_update(uint64_t* table, uint64_t slots, int64_t d
 // kernel of their own)
 cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const int64_t* dtask_begin,
                                int nhash, bool poly, bool pseries, bool trunc, int grid, cudaStream_t s);
+// Compaction: up to this many chunks one pass (each chunk read once, one
+// launch); above it two passes, whose counting pass keeps more loads in
+// flight (and stores the live bits of dense arrays, Prod::live).
+constexpr int64_t COMPACT_ONE_PASS_MAX = 1024;
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
 // cstat: nchunks zeroed words of scan state; sync: two zeroed int64 (a
 // ticket counter, then an error flag set when a bounded wait gave up); scan:

@@ -73,9 +73,95 @@ __global__ void __launch_bounds__(PK_THREADS) k_probe_smem_split64(int64_t* __re
   if (acc == ~0ull) sink[blockIdx.x] = (int64_t)acc;
 }
 
+// Chip-wide arithmetic rates of the coefficient multiply-add forms the
+// kernels use: 64 x 64 -> 64-bit integer multiply-add (int64 coefficients),
+// 32 x 32 -> 64-bit multiply-add (int64 coefficients that fit 32 bits), and
+// float64 FMA.  Eight independent chains per thread, so that issue, not
+// latency, sets the rate.
+constexpr int ALU_THREADS = 256;
+constexpr int ALU_ITERS = 4096;
+constexpr int ALU_CHAINS = 8;
+
+__global__ void __launch_bounds__(ALU_THREADS) k_probe_alu(int kind, int64_t* __restrict__ sink, int64_t seed) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t acc = 0;
+  if (kind == 0) {
+    uint64_t x[ALU_CHAINS];
+#pragma unroll
+    for (int c = 0; c < ALU_CHAINS; ++c) x[c] = (uint64_t)(seed + t * ALU_CHAINS + c) | 1ull;
+    // x * x (both factors unknown to the compiler): a multiply by a constant
+    // would let it fold consecutive steps into one
+    for (int it = 0; it < ALU_ITERS; ++it) {
+#pragma unroll
+      for (int c = 0; c < ALU_CHAINS; ++c) x[c] = x[c] * x[c] + (uint64_t)(2 * c + 1);
+    }
+#pragma unroll
+    for (int c = 0; c < ALU_CHAINS; ++c) acc ^= (int64_t)x[c];
+  } else if (kind == 1) {
+    int64_t x[ALU_CHAINS];
+    int32_t y[ALU_CHAINS];
+#pragma unroll
+    for (int c = 0; c < ALU_CHAINS; ++c) { x[c] = seed + t + c; y[c] = (int32_t)(seed ^ (t + 7 * c)) | 1; }
+    for (int it = 0; it < ALU_ITERS; ++it) {
+#pragma unroll
+      for (int c = 0; c < ALU_CHAINS; ++c) x[c] += (int64_t)y[c] * (int64_t)(int32_t)x[c];
+    }
+#pragma unroll
+    for (int c = 0; c < ALU_CHAINS; ++c) acc ^= x[c];
+  } else {
+    double x[ALU_CHAINS];
+#pragma unroll
+    for (int c = 0; c < ALU_CHAINS; ++c) x[c] = 1.0 + 1e-9 * (double)((t + c) & 1023);
+    const double m = 0.999999999, a = 1e-12;
+    for (int it = 0; it < ALU_ITERS; ++it) {
+#pragma unroll
+      for (int c = 0; c < ALU_CHAINS; ++c) x[c] = fma(x[c], m, a);
+    }
+    double d = 0.0;
+#pragma unroll
+    for (int c = 0; c < ALU_CHAINS; ++c) d += x[c];
+    acc = __double_as_longlong(d);
+  }
+  if (acc == seed) sink[t & 1023] = acc;   // keeps the work observable
+}
+
 }  // namespace kr
 
 using namespace kr;
+
+extern "C" double kr_probe_alu_rate(int32_t device, int32_t kind, int32_t reps) {
+  if (kind < 0 || kind > 2) return -1.0;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return -1.0; }
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_alu, ALU_THREADS, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int grid = sms * per_sm;
+  int64_t* sink = nullptr;
+  if (cudaMalloc(&sink, 1024 * 8) != cudaSuccess) { cudaGetLastError(); cudaSetDevice(prev); return -1.0; }
+  double best = -1.0;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int r = 0; r < (reps > 0 ? reps : 5) + 1; ++r) {
+    cudaEventRecord(a, 0);
+    k_probe_alu<<<grid, ALU_THREADS>>>(kind, sink, 12345);
+    cudaEventRecord(b, 0);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double ops = (double)grid * ALU_THREADS * ALU_ITERS * ALU_CHAINS;
+    if (r > 0 && ms > 0.f) best = std::max(best, ops / (ms * 1e-3));
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (cudaGetLastError() != cudaSuccess) best = -1.0;
+  cudaSetDevice(prev);
+  return best;
+}
 
 extern "C" double kr_probe_smem_accumulate_rate(int32_t device, int32_t reps) {
   int prev = 0;

@@ -95,8 +95,8 @@ class Server:
 
     def __init__(self, device: int = 0, workers: int = 2, mem_budget: float = 64e9,
                  max_batch: int = 256, wave_pairs: int = 0, work_cap: float = 5e7,
-                 giant: float = 2e7, trim_bytes: float = 24e9, giant_alone: bool = True,
-                 giant_policy: str = "shared"):
+                 giant: float = 2e7, trim_bytes: float = 96e9, giant_alone: bool = True,
+                 giant_policy: str = "shared", queue_scale: int = 0, work_cap_max: float = 4e8):
         if giant_policy not in ("alone", "shared"):
             raise ValueError("giant_policy must be 'alone' or 'shared'")
         self.device = device
@@ -105,6 +105,12 @@ class Server:
         self.giant_alone = giant_alone
         self.giant_policy = giant_policy
         self.giants_running = 0
+        # queue_scale > 0: the work cap grows with the queue, work_cap * (1 + waiting /
+        # queue_scale) up to work_cap_max, so that a long queue is drained in larger
+        # batches (fewer launches and waits per product) while a short one keeps small
+        # batches and their short latency
+        self.queue_scale = queue_scale
+        self.work_cap_max = work_cap_max
         self.trim_bytes = trim_bytes
         self.exclusive = False
         self.hold = 0             # workers retrying alone after running out of memory
@@ -118,6 +124,15 @@ class Server:
         self.lock = threading.Lock()
         self.in_flight_bytes = 0.0
 
+    def warm_up(self, requests: list[Request], n: int = 2):
+        """Runs the largest requests (by term-products: the n largest polynomial
+        products and the n largest Poisson products) once on every worker, so
+        that each context's scratch has grown before serving starts (a growth
+        frees and allocates device memory, which waits for the whole device)."""
+        for w in self.workers:
+            with_torch_stream(w.stream, lambda: [self._mul(w, [r]) for r in largest(requests, n)])
+            w.stream.synchronize()
+
     def close(self):
         """Release the workers' contexts (their scratch and results)."""
         for w in self.workers:
@@ -130,17 +145,18 @@ class Server:
         # output (16 B) + ordering scratch (16 B) + table at load 0.5 (32 B) per term
         return 64.0 * out_terms + 1e6
 
-    def _mul(self, w: _Worker, batch: list[Request]):
+    def _mul(self, w: _Worker, batch: list[Request], stream=None):
+        stream = w.stream if stream is None else stream
         if len(batch) == 1 and hasattr(batch[0].f.coef, "is_cuda"):
             # one request: the single-product call (its outputs are the caller's tensors)
             r = batch[0]
             if r.poisson:
-                e, t, k, c, _ = B.poisson_mul(r.f, r.g, ctx=w.ctx, stream=w.stream)
+                e, t, k, c, _ = B.poisson_mul(r.f, r.g, ctx=w.ctx, stream=stream)
                 return [{"status": 0, "nterms": int(c.shape[0]), "exps": e, "trig": t, "kind": k,
                          "coef": c, "owned": True}]
-            e, c, _, _ = B.poly_mul(r.f.exps, r.f.coef, r.g.exps, r.g.coef, ctx=w.ctx, stream=w.stream)
+            e, c, _, _ = B.poly_mul(r.f.exps, r.f.coef, r.g.exps, r.g.coef, ctx=w.ctx, stream=stream)
             return [{"status": 0, "nterms": int(c.shape[0]), "exps": e, "coef": c, "owned": True}]
-        return B.kron_mul_batch([(r.f, r.g) for r in batch], ctx=w.ctx, stream=w.stream,
+        return B.kron_mul_batch([(r.f, r.g) for r in batch], ctx=w.ctx, stream=stream,
                                 wave_pairs=self.wave_pairs)
 
     def _retry_alone(self, w: _Worker, batch: list[Request]):
@@ -171,6 +187,9 @@ class Server:
         if head.pairs > self.giant:
             if self.giants_running == 0:
                 return [head], self.predict_bytes(head)
+        cap = self.work_cap
+        if self.queue_scale > 0:
+            cap = min(self.work_cap_max, self.work_cap * (1 + len(pending) / self.queue_scale))
         batch, used, work = [], 0.0, 0.0
         for r in pending:
             if r.pairs > self.giant:
@@ -179,7 +198,7 @@ class Server:
             if not batch:
                 if b > room and self.in_flight_bytes > 0:
                     break   # wait for memory to come back
-            elif used + b > room or work + r.pairs > self.work_cap or len(batch) >= self.max_batch:
+            elif used + b > room or work + r.pairs > cap or len(batch) >= self.max_batch:
                 continue    # later, smaller requests may still fit
             batch.append(r)
             used += b
@@ -189,25 +208,27 @@ class Server:
     def _run_batch(self, w: _Worker, batch: list[Request], t0: float, bytes_: float):
         import torch
         out = None
+        stream = w.stream
         try:
-            with torch.cuda.stream(w.stream):
+            with torch.cuda.stream(stream):
                 now = time.perf_counter() - t0
                 for r in batch:
                     r.start = now
                 try:
-                    out = self._mul(w, batch)
+                    out = self._mul(w, batch, stream)
                 except B.KronError as e:
                     if e.status != B.KR_ERR_OOM:
                         raise
                     out = self._retry_alone(w, batch)
                 # results are library-owned until the context's next batch: copy them out
+                stream.synchronize()
                 for r, o in zip(batch, out):
                     r.status = o["status"]
                     if o.get("owned"):
                         r.result = {k: v for k, v in o.items() if k != "owned"}
                     else:
                         r.result = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in o.items()}
-                w.stream.synchronize()
+                stream.synchronize()
             done = time.perf_counter() - t0
             obs = {False: [0, 0], True: [0, 0]}
             for r, o in zip(batch, out):
@@ -339,9 +360,38 @@ class Server:
                           rejected=len(reqs) - len(done))
 
 
-def serve_one_by_one(requests: list[Request], device: int = 0, time_limit: float = 120.0) -> ServeStats:
-    """The baseline: one poly_mul / poisson_mul call per request, in arrival order."""
+def largest(requests: list[Request], n: int) -> list[Request]:
+    """The n largest polynomial and the n largest Poisson requests by term-products."""
+    out = []
+    for poisson in (False, True):
+        rs = sorted((r for r in requests if r.poisson == poisson), key=lambda r: -r.pairs)
+        out += rs[:n]
+    return out
+
+
+def with_torch_stream(stream, fn):
+    import torch
+    with torch.cuda.stream(stream):
+        return fn()
+
+
+def _single(ctx, r: Request):
+    if r.poisson:
+        return B.poisson_mul(r.f, r.g, ctx=ctx)
+    return B.poly_mul(r.f.exps, r.f.coef, r.g.exps, r.g.coef, ctx=ctx)
+
+
+def serve_one_by_one(requests: list[Request], device: int = 0, time_limit: float = 120.0,
+                     warm: bool = False) -> ServeStats:
+    """The baseline: one poly_mul / poisson_mul call per request, in arrival
+    order (warm: the largest requests run once first, untimed, as the server's
+    warm_up does)."""
+    import torch
     ctx = B.Context(device)
+    if warm:
+        for r in largest(requests, 2):
+            _single(ctx, r)
+        torch.cuda.synchronize()
     reqs = sorted(requests, key=lambda r: r.arrival)
     t0 = time.perf_counter()
     for r in reqs:
@@ -351,11 +401,7 @@ def serve_one_by_one(requests: list[Request], device: int = 0, time_limit: float
         if r.arrival > now:
             time.sleep(r.arrival - now)
         r.start = time.perf_counter() - t0
-        if r.poisson:
-            out = B.poisson_mul(r.f, r.g, ctx=ctx)
-        else:
-            out = B.poly_mul(r.f.exps, r.f.coef, r.g.exps, r.g.coef, ctx=ctx)
-        r.result = out
+        r.result = _single(ctx, r)
         r.status = 0
         r.done = time.perf_counter() - t0
     wall = time.perf_counter() - t0
