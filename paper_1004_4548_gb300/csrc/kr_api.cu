@@ -517,13 +517,6 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       // the block-accumulated arrays are cleared by the dense planning kernel
       // (the blocks that its flushes do not write whole)
       for (int p : dense_ids) plans[p].p.dense = (void*)b.take<uint64_t>(plans[p].p.kspan);
-      // live bits of every dense array compacted in two passes (written whole by the counting pass)
-      for (int p : live_ids) {
-        Plan& pl = plans[p];
-        pl.p.live = nullptr;
-        if (pl.p.path == PATH_DENSE && nchunks_total > COMPACT_ONE_PASS_MAX)
-          pl.p.live = b.take<uint32_t>((pl.p.kspan + 63) / 64 * 2);
-      }
       if (!pass) ensure(ctx, &ctx->acc, &ctx->acc_cap, b.off + 1, s);
     }
   };

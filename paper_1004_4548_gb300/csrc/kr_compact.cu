@@ -52,10 +52,7 @@ __device__ __forceinline__ ulonglong2 ld_pair(const uint64_t* p) {
 }
 
 // Loads the warp's part and returns its number of live slots (in every lane).
-// MASKED (dense array with the counting pass's live bits): a lane loads its
-// pair of slots only when one of them is live, so that sectors without a
-// live slot are not read again.
-template <bool STREAM, bool MASKED = false>
+template <bool STREAM>
 __device__ __forceinline__ int load_part(const Prod& P, int64_t s0, int64_t s1, int warp, Part& pt) {
   const int lane = threadIdx.x & 31;
   const bool dense = P.path == PATH_DENSE;
@@ -66,21 +63,12 @@ __device__ __forceinline__ int load_part(const Prod& P, int64_t s0, int64_t s1, 
   int n = 0;
   if (dense) {
     const uint64_t* a = (const uint64_t*)P.dense;
-    uint32_t mw = 0;   // lane l: word l of the part's row masks (row t: words 2t, 2t + 1)
-    if (MASKED && pt.a + 32 * (int64_t)lane < pt.b) mw = P.live[pt.a / 32 + lane];
 #pragma unroll
     for (int t = 0; t < CP_ROWS; ++t) {
       const int64_t s = pt.a + 64 * t + 2 * lane;
       ulonglong2 v = make_ulonglong2(0, 0);
-      bool want = true;
-      if (MASKED) {
-        const uint32_t e = __shfl_sync(CP_FULL, mw, 2 * t), o = __shfl_sync(CP_FULL, mw, 2 * t + 1);
-        want = ((e | o) >> lane) & 1u;
-      }
-      if (want) {
-        if (s + 1 < pt.b) v = ld_pair<STREAM>(a + s);
-        else if (s < pt.b) v.x = a[s];
-      }
+      if (s + 1 < pt.b) v = ld_pair<STREAM>(a + s);
+      else if (s < pt.b) v.x = a[s];
       pt.v[t] = v;
     }
 #pragma unroll
@@ -136,26 +124,7 @@ __device__ __forceinline__ int count_part(const Prod& P, int64_t s0, int64_t s1,
   const int64_t a0 = min(s1, s0 + per * warp), b0 = min(s1, a0 + per);
   const bool f64 = P.f64;
   int n = 0;
-  if (P.path == PATH_DENSE && P.live) {
-    // rows of 64 slots, walked by the whole warp together: the live bits of
-    // each row's even and odd slots are stored for the writing pass
-    const uint64_t* a = (const uint64_t*)P.dense;
-#pragma unroll 4
-    for (int64_t r = a0; r < b0; r += 64) {
-      const int64_t s = r + 2 * lane;
-      int f0 = 0, f1 = 0;
-      if (s + 1 < b0) {
-        const ulonglong2 v = ld_pair<true>(a + s);
-        f0 = live_word(v.x, f64);
-        f1 = live_word(v.y, f64);
-      } else if (s < b0) {
-        f0 = live_word(__ldcs(a + s), f64);
-      }
-      n += f0 + f1;
-      const unsigned e = __ballot_sync(CP_FULL, f0), o = __ballot_sync(CP_FULL, f1);
-      if (lane == 0) *(uint2*)(P.live + r / 32) = make_uint2(e, o);
-    }
-  } else if (P.path == PATH_DENSE) {
+  if (P.path == PATH_DENSE) {
     const uint64_t* a = (const uint64_t*)P.dense;
 #pragma unroll 4
     for (int64_t s = a0 + 2 * lane; s < b0; s += 64) {
@@ -221,7 +190,7 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(const Prod* __re
     const int64_t s0 = (c - chunk_begin[p]) * P.chunk;
     const int64_t s1 = min(accum_slots(P), s0 + P.chunk);
     Part pt;
-    const int n = P.live ? load_part<true, true>(P, s0, s1, warp, pt) : load_part<true>(P, s0, s1, warp, pt);
+    const int n = load_part<true>(P, s0, s1, warp, pt);
     if ((threadIdx.x & 31) == 0) wsum[warp] = n;
     __syncthreads();
     int64_t run = offs[c];

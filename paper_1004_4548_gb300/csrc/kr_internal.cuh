@@ -157,9 +157,6 @@ struct Prod {
   int64_t task_begin;   // first task index of this product (hash tiles)
   int64_t ntasks;
   // compaction
-  uint32_t* live;       // dense array, two-pass compaction: per 64-slot row, the live bits of
-                        // its even and of its odd slots (two words), written by the counting
-                        // pass so that the writing pass loads only the pairs holding a live slot
   int64_t chunk;        // accumulator slots per compaction chunk
   int64_t nchunks;
   int64_t chunk_begin;  // first chunk index of this product
@@ -417,7 +414,7 @@ cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const i
                                int nhash, bool poly, bool pseries, bool trunc, int grid, cudaStream_t s);
 // Compaction: up to this many chunks one pass (each chunk read once, one
 // launch); above it two passes, whose counting pass keeps more loads in
-// flight (and stores the live bits of dense arrays, Prod::live).
+// flight.
 constexpr int64_t COMPACT_ONE_PASS_MAX = 1024;
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
 // cstat: nchunks zeroed words of scan state; sync: two zeroed int64 (a
