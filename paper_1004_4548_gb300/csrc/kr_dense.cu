@@ -197,6 +197,27 @@ struct Slice<int64_t> {
   __device__ __forceinline__ int64_t get(int64_t s) const {
     return (int64_t)(((uint64_t)hi[s] << 32) | (uint64_t)lo[s]);
   }
+  // Adds the product of one chunk-table entry (slice offset x, int32
+  // coefficient y, read from shared address ent) and a g term (code offset
+  // gc, int32 coefficient cg) at offset x + gc, known to lie in the slice: the
+  // load, the product and the add as one sequence with no range test and no
+  // branch (the high-word reduction is guarded by a predicate).
+  __device__ __forceinline__ void add_entry(uint32_t ent, int32_t gc, int32_t cg) const {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t.reg .b32 x, y, a, o, t, h, l, u;\n\t.reg .s64 v;\n\t"
+        "ld.shared.v2.b32 {x, y}, [%0];\n\t"
+        "add.s32 x, x, %1;\n\t"
+        "mad.lo.u32 a, x, 4, %3;\n\t"
+        "mul.wide.s32 v, y, %2;\n\t"
+        "mov.b64 {l, u}, v;\n\t"
+        "atom.shared.add.u32 o, [a], l;\n\t"
+        "add.cc.u32 t, o, l;\n\t"
+        "addc.u32 h, u, 0;\n\t"
+        "setp.ne.u32 q, h, 0;\n\t"
+        "add.u32 a, a, %4;\n\t"
+        "@q red.shared.add.u32 [a], h;\n\t}"
+        ::"r"(ent), "r"(gc), "r"(cg), "r"(lo_sh), "r"(hi_dist) : "memory");
+  }
 };
 
 template <>
@@ -252,7 +273,9 @@ constexpr int DENSE_Q = KR_DENSE_Q;   // f terms examined per thread and table f
 // window its slot falls in, loads one g term and adds its products with the
 // tile's f terms to the slice with shared-memory atomics (consecutive lanes of
 // a window hold consecutive g terms, so one atomic instruction touches nearby
-// words).  The slice offset a = (F_i - B) + G_j lies in [0, S) for the pairs
+// words).  A step in which every lane holds a g term that pairs in range with
+// all TILE_R terms of a full tile (most steps of a dense product) adds without
+// range tests.  The slice offset a = (F_i - B) + G_j lies in [0, S) for the pairs
 // this block owns; others are skipped (32-bit arithmetic is exact there, since
 // the dense path keeps codes below 2^31).
 template <typename T, bool C32>
@@ -402,16 +425,42 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
           }
         }
         int32_t e0 = ct.excl[k], e1 = ct.excl[k + 1];
-        for (; p < pe; p += 32) {
-          while (p >= e1) {   // empty windows (non-owners) are skipped here too
-            ++k;
-            e0 = e1;
-            e1 = ct.excl[k + 1];
+        const int32_t lim32 = (int32_t)lim;
+        const uint32_t fc_sh = (uint32_t)__cvta_generic_to_shared(&ct.fc[0]);
+        // the lanes step together (uniform trip count) so that they can vote
+        for (int32_t base = pb; base < pe; base += 32, p += 32) {
+          const bool act = p < pe;
+          int32_t gc = 0;
+          T cg = (T)0;
+          int rk = 0;
+          if (act) {
+            while (p >= e1) {   // empty windows (non-owners) are skipped here too
+              ++k;
+              e0 = e1;
+              e1 = ct.excl[k + 1];
+            }
+            const int64_t j = (int64_t)ct.lo[k] + (p - e0);
+            gc = G32 ? G32[j] : (int32_t)G[j];
+            cg = CG[j];
+            rk = ct.run[k];
           }
-          const int64_t j = (int64_t)ct.lo[k] + (p - e0);
-          const int32_t gc = G32 ? G32[j] : (int32_t)G[j];
-          const T cg = CG[j];
-          const int rk = ct.run[k];
+          if constexpr (C32) {
+            // core step: in every lane a full tile and a g term in range for
+            // all of the tile's f terms (offsets x_0 + gc .. x_7 + gc inside
+            // [0, lim), the x_a ascending): no range tests
+            bool core = false;
+            if (act && rk == TILE_R) {
+              const int32_t o0 = ct.fc[k].x + gc;
+              core = o0 >= 0 && o0 < lim32 - (ct.fc[k + TILE_R - 1].x - ct.fc[k].x);
+            }
+            if (__all_sync(FULL, core)) {
+              const uint32_t ent = fc_sh + (uint32_t)k * 8u;
+#pragma unroll
+              for (int a = 0; a < TILE_R; ++a) acc.add_entry(ent + 8u * a, gc, (int32_t)cg);
+              continue;
+            }
+          }
+          if (!act) continue;
 #if KR_FULL_TILE_FAST
           if (rk == TILE_R) {   // the common case: a full tile, the loop fully unrolled
 #pragma unroll

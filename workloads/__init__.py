@@ -10,7 +10,7 @@ gives the same inputs on x86 and Arm hosts.
 """
 from .synth import (  # noqa: F401
     Rng, Poly, PSeries, total_degree_tuples,
-    dense_total_degree, mp_sparse, poisson_random, random_poly, random_pseries,
+    dense_total_degree, dense_box, mp_sparse, poisson_random, random_poly, random_pseries,
     workload_cfg1, workload_cfg2, workload_cfg3, workload_cfg4, batch_mix, fateman,
     arrival_times,
 )

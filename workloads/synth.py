@@ -179,6 +179,23 @@ def poisson_random(n: int, npoly: int, ntrig: int, prange: int, trange: int,
     return PSeries(_soa(P), _soa(T), np.ascontiguousarray(K), coef.astype(np.float64))
 
 
+def dense_box(lo, hi, keep: float, coef_lo: int, coef_hi: int, seed: int) -> Poly:
+    """The monomials of the box lo <= e <= hi (variable 0 fastest), each kept
+    with probability keep; nonzero int64 coefficients uniform in [coef_lo, coef_hi].
+    Long runs of consecutive exponents of variable 0, broken where a monomial
+    was dropped."""
+    rng = Rng(seed)
+    lo = [int(x) for x in lo]
+    hi = [int(x) for x in hi]
+    axes = [np.arange(a, b + 1, dtype=np.int64) for a, b in zip(lo, hi)]
+    grid = np.stack(np.meshgrid(*axes[::-1], indexing="ij")[::-1], axis=-1).reshape(-1, len(lo))
+    if keep < 1.0:
+        grid = grid[rng.uniform(grid.shape[0]) < keep]
+    coef = rng.nonzero_ints(coef_lo, coef_hi, grid.shape[0])
+    perm = rng.perm(grid.shape[0])
+    return Poly(_soa(grid[perm].astype(np.int32)), coef[perm])
+
+
 def random_poly(nvars: int, n: int, lo, hi, seed: int, dtype="i64",
                 coef_range=(-1000, 1000)) -> Poly:
     """n distinct random monomials, exponent k uniform in [lo[k], hi[k]]."""
