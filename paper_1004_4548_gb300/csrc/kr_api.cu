@@ -42,6 +42,11 @@ struct kr_ctx {
   // host depends on them (no hash table to size or regrow); its term count
   // then stays on the device until the decode (ProdResult::n = -1)
   bool allow_deferred = false;
+  // a deferred dense polynomial product whose caller's outputs are all in
+  // device memory: the compaction decodes its terms there (direct_done), and
+  // the output step only reads the count
+  DirectOut direct{};
+  bool direct_done = false;
   // split histogram (kron_split_hist): the pipeline stops after phase B1 and
   // samples the keys of product 0 into split_hist (host) instead
   int32_t split_nbins = 0;
@@ -770,10 +775,19 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       ctx->launches += (any_poly ? 1 : 0) + (any_pseries ? 1 : 0) + (any_trunc ? 1 : 0);
       mark(ctx, s, "hash_insert");
     }
+    DirectOut direct{};
+    if (deferred && ctx->direct.coef) {
+      const Prod& P0 = plans[live_ids[0]].p;
+      if (P0.path == PATH_DENSE && P0.nt == 0) {
+        direct = ctx->direct;
+        ctx->direct_done = true;
+      }
+    }
+    int compact_launches = 0;
     ck(ctx, launch_compact(A.lprods, nlive, Z.chunk_begin, nchunks_total, Z.counts, Z.cstat, Z.counters + 2,
-                           Z.scan, Z.okey, Z.oval, out_total, s),
+                           Z.scan, Z.okey, Z.oval, out_total, s, direct, &compact_launches),
        "compaction");
-    ctx->launches += nchunks_total == 0 ? 1 : (nchunks_total <= 1024 ? 2 : 4);
+    ctx->launches += compact_launches;
     mark(ctx, s, "compact");
     if (deferred) {
       // the count, the status and the position (0: the only product) stay on
@@ -934,13 +948,15 @@ kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
     const bool exps_dev = !h->exps || is_device_ptr(h->exps);
     const bool codes_dev = !h->codes || is_device_ptr(h->codes);
     if (exps_dev && codes_dev && is_device_ptr(h->coef)) {
-      // deferred count, device outputs: decode up to the capacity, read the
-      // count, then report it
-      ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->capacity, h->codes, s,
-                                 true, ctx->res_val, (uint64_t*)h->coef),
-         "decode");
-      ctx->launches += 1;
-      mark(ctx, s, "decode");
+      // deferred count, device outputs: decode up to the capacity (unless the
+      // compaction has decoded into these arrays), read the count, then report it
+      if (!ctx->direct_done) {
+        ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->capacity, h->codes, s,
+                                   true, ctx->res_val, (uint64_t*)h->coef),
+           "decode");
+        ctx->launches += 1;
+        mark(ctx, s, "decode");
+      }
       const kr_status st = settle_deferred(ctx, s);
       h->nterms = st == KR_OK ? ctx->res_n : 0;
       if (st != KR_OK) return st;
@@ -1322,18 +1338,37 @@ kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out*
     if (opts) in.opts = *opts;
     std::vector<ProdResult> res;
     // the term count may stay on the device until the decode (host outputs:
-    // until the decode into scratch, whose terms are then copied)
+    // until the decode into scratch, whose terms are then copied); with every
+    // output in device memory the compaction may decode into it directly
     ctx->allow_deferred = true;
+    ctx->direct = DirectOut{};
+    ctx->direct_done = false;
+    if (h->capacity > 0 && is_device_ptr(h->coef) && (!h->exps || is_device_ptr(h->exps)) &&
+        (!h->codes || is_device_ptr(h->codes))) {
+      ctx->direct.exps = h->exps;
+      ctx->direct.codes = h->codes;
+      ctx->direct.coef = (uint64_t*)h->coef;
+      ctx->direct.ld = h->capacity;
+      ctx->direct.cap = h->capacity;
+    }
     try {
       run_pipeline(ctx, {in}, s, res);
     } catch (...) {
       ctx->allow_deferred = false;
+      ctx->direct = DirectOut{};
+      ctx->direct_done = false;
       throw;
     }
     ctx->allow_deferred = false;
-    if (res[0].st != KR_OK) return res[0].st;
+    ctx->direct = DirectOut{};
+    if (res[0].st != KR_OK) {
+      ctx->direct_done = false;
+      return res[0].st;
+    }
     keep_result(ctx, res[0], false);
-    return emit_poly(ctx, h, s);
+    const kr_status st = emit_poly(ctx, h, s);
+    ctx->direct_done = false;
+    return st;
   });
 }
 

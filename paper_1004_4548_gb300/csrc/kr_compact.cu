@@ -85,6 +85,20 @@ __device__ __forceinline__ int load_part(const Prod& P, int64_t s0, int64_t s1, 
   return __reduce_add_sync(CP_FULL, (unsigned)n);
 }
 
+// Output terms [a, b) of a dense product (just written to okey / oval by
+// this CTA) decoded into the caller's arrays, one term per thread.  A pass
+// of its own after the chunk's writes, so that the chunk's registers are free.
+__device__ __noinline__ void write_direct(const Prod& P, const DirectOut& D, int64_t a, int64_t b,
+                                          const uint64_t* __restrict__ okey,
+                                          const uint64_t* __restrict__ oval) {
+  for (int64_t q = a + threadIdx.x; q < b; q += blockDim.x) {
+    const int64_t code = (int64_t)okey[q] + P.klo;
+    if (D.codes) D.codes[q] = code;
+    if (D.exps) decode_poly_part(P, code, D.exps, D.ld, q);
+    D.coef[q] = oval[q];
+  }
+}
+
 // Writes the live slots of the warp's part in slot order from output position
 // `run` (slots outside the part were loaded as zeros, which are not live).
 // Keys are written relative to the product's key window (dense: the slot).
@@ -179,7 +193,8 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(const Prod* __re
                                                                 const int64_t* __restrict__ offs,
                                                                 int64_t cap,
                                                                 uint64_t* __restrict__ okey,
-                                                                uint64_t* __restrict__ oval) {
+                                                                uint64_t* __restrict__ oval,
+                                                                const DirectOut D) {
   const int64_t nchunks = chunk_begin[nprod];
   __shared__ int wsum[CP_WARPS];
   const int warp = threadIdx.x >> 5;
@@ -196,6 +211,12 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact_scatter(const Prod* __re
     int64_t run = offs[c];
     for (int w = 0; w < warp; ++w) run += wsum[w];
     write_part(P, pt, run, cap, okey, oval);
+    if (D.coef && P.path == PATH_DENSE) {   // uniform across the CTA
+      int64_t cnt = 0;
+      for (int w = 0; w < CP_WARPS; ++w) cnt += wsum[w];
+      __syncthreads();   // the chunk's terms are in okey / oval
+      write_direct(P, D, offs[c], min(offs[c] + cnt, min(cap, D.cap)), okey, oval);
+    }
     __syncthreads();   // wsum is rewritten for the next chunk
   }
 }
@@ -274,14 +295,15 @@ __global__ void k_lookback_selftest(uint64_t* cstat, int64_t* err, int64_t* out)
   }
 }
 
-__global__ void __launch_bounds__(CP_THREADS) k_compact(const Prod* __restrict__ prods, int nprod,
+__global__ void __launch_bounds__(CP_THREADS) k_compact(Prod* __restrict__ prods, int nprod,
                                                         const int64_t* __restrict__ chunk_begin,
                                                         uint64_t* __restrict__ cstat,
                                                         int64_t* __restrict__ offs,
                                                         unsigned long long* __restrict__ ticket,
                                                         int64_t* __restrict__ err, int64_t cap,
                                                         uint64_t* __restrict__ okey,
-                                                        uint64_t* __restrict__ oval) {
+                                                        uint64_t* __restrict__ oval,
+                                                        const DirectOut D) {
   const int64_t nchunks = chunk_begin[nprod];
   __shared__ int wsum[CP_WARPS];
   __shared__ int64_t s_c, s_excl;
@@ -306,7 +328,15 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact(const Prod* __restrict__
       const int64_t excl = lookback(cstat, c, cnt, err);
       if (threadIdx.x == 0) {
         offs[c] = excl;
-        if (c == nchunks - 1) offs[nchunks] = excl + cnt;
+        if (c == nchunks - 1) {
+          offs[nchunks] = excl + cnt;
+          if (nprod == 1) {   // the product's count and status (as k_finish_counts)
+            Prod& Q = prods[0];
+            Q.out_start = 0;
+            Q.nout = Q.status ? 0 : excl + cnt;
+            if (excl + cnt > cap) Q.status |= ST_OUTCAP;
+          }
+        }
         s_excl = excl;
       }
     }
@@ -315,6 +345,12 @@ __global__ void __launch_bounds__(CP_THREADS) k_compact(const Prod* __restrict__
       int64_t run = s_excl;
       for (int w = 0; w < warp; ++w) run += wsum[w];
       write_part(P, pt, run, cap, okey, oval);
+    }
+    if (live && D.coef && P.path == PATH_DENSE) {   // uniform across the CTA
+      int64_t cnt = 0;
+      for (int w = 0; w < CP_WARPS; ++w) cnt += wsum[w];
+      __syncthreads();   // the chunk's terms are in okey / oval
+      write_direct(P, D, s_excl, min(s_excl + cnt, min(cap, D.cap)), okey, oval);
     }
     __syncthreads();   // wsum, s_c and s_excl are rewritten for the next chunk
   }
@@ -339,7 +375,9 @@ __global__ void k_finish_counts(Prod* __restrict__ prods, int nprod,
 
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
                            int64_t* dcounts, uint64_t* dcstat, int64_t* dsync, int64_t* dscan,
-                           uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s) {
+                           uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s,
+                           const DirectOut& direct, int* launches) {
+  *launches = 0;
   if (nchunks > 0) {
     // persistent grid: every CTA that fits on the GPU at once
     int dev = 0, sms = 152, per = 0;
@@ -352,7 +390,10 @@ cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin,
     if (nchunks <= COMPACT_ONE_PASS_MAX) {
       const int64_t grid = std::min<int64_t>(nchunks, (int64_t)sms * std::max(per, 1));
       k_compact<<<(unsigned)grid, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcstat, dcounts,
-                                                     (unsigned long long*)dsync, dsync + 1, cap, okey, oval);
+                                                     (unsigned long long*)dsync, dsync + 1, cap, okey, oval,
+                                                     direct);
+      *launches += 1;
+      if (nprod == 1) return cudaGetLastError();   // counted by the last chunk's CTA
     } else {
       int pc = 0, ps = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pc, k_compact_count, CP_THREADS, 0) != cudaSuccess ||
@@ -366,13 +407,15 @@ cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin,
       cudaError_t e = launch_scan_exclusive(dcounts, nchunks, dcounts + nchunks, dscan, s);
       if (e != cudaSuccess) return e;
       k_compact_scatter<<<(unsigned)gs, CP_THREADS, 0, s>>>(dprods, nprod, dchunk_begin, dcounts, cap, okey,
-                                                           oval);
+                                                           oval, direct);
+      *launches += 3;
     }
   } else {
     cudaMemsetAsync(dcounts, 0, sizeof(int64_t), s);
   }
   k_finish_counts<<<(nprod + 127) / 128, 128, 0, s>>>(dprods, nprod, dchunk_begin, dcounts,
                                                       dcounts + nchunks, cap);
+  *launches += 1;
   return cudaGetLastError();
 }
 

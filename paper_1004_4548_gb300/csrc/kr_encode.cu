@@ -30,6 +30,7 @@ namespace kr {
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 256;
 constexpr int RS_SPLIT_MAX = 256;
+static_assert(RS_SPLIT_MAX <= RS_THREADS, "the combine takes one partial per thread");
 constexpr int RS_CTA_BUDGET = 2048;   // CTAs of one launch, about 13 per SM
 
 struct RangePart {
@@ -141,23 +142,51 @@ __global__ void __launch_bounds__(RS_THREADS) k_range_scan(const Prod* __restric
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // the combine: thread q loads partial q (all at once, one round of loads),
+  // then warp reductions and one pass over the warps' results
   const int nsplit = gridDim.x;
+  const int q = threadIdx.x;   // nsplit <= RS_SPLIT_MAX == RS_THREADS
+  const bool has = q < nsplit;
+  int32_t plo[MAXV], phi[MAXV];
+#pragma unroll
+  for (int k = 0; k < MAXV; ++k) {
+    plo[k] = INT32_MAX;
+    phi[k] = INT32_MIN;
+    if (has && k < nvar) {
+      plo[k] = __ldcg(&pp[q].lo[k]);
+      phi[k] = __ldcg(&pp[q].hi[k]);
+    }
+  }
+  int pf = has ? __ldcg(&pp[q].fits) : 1;
+  long long pa = has ? __ldcg(&pp[q].dlo) : LLONG_MAX, pb = has ? __ldcg(&pp[q].dhi) : LLONG_MIN;
+#pragma unroll
+  for (int k = 0; k < MAXV; ++k) {
+    if (k < nvar) {
+      const int32_t a = __reduce_min_sync(0xffffffffu, plo[k]);
+      const int32_t b = __reduce_max_sync(0xffffffffu, phi[k]);
+      if (lane == 0) { smin[k][warp] = a; smax[k][warp] = b; }
+    }
+  }
+  pf = __all_sync(0xffffffffu, pf);
+  for (int o = 16; o > 0; o >>= 1) {
+    pa = min(pa, __shfl_xor_sync(0xffffffffu, pa, o));
+    pb = max(pb, __shfl_xor_sync(0xffffffffu, pb, o));
+  }
+  __syncthreads();   // every warp has read its own partial record above
+  if (lane == 0) { sfits[warp] = pf; sdlo[warp] = pa; sdhi[warp] = pb; }
+  __syncthreads();
   int32_t* res = ranges + (int64_t)blockIdx.y * RANGE_STRIDE;
   const int k = threadIdx.x;
   if (k < nvar) {
     int32_t lo = INT32_MAX, hi = INT32_MIN;
-    for (int q = 0; q < nsplit; ++q) { lo = min(lo, __ldcg(&pp[q].lo[k])); hi = max(hi, __ldcg(&pp[q].hi[k])); }
+    for (int w = 0; w < RS_THREADS / 32; ++w) { lo = min(lo, smin[k][w]); hi = max(hi, smax[k][w]); }
     if (k < P.np) { res[k] = lo; res[MAXV + k] = hi; }
     else { res[2 * MAXV + (k - P.np)] = hi; }
   }
   if (k == 0) {
     int f = 1;
     long long a = LLONG_MAX, b = LLONG_MIN;
-    for (int q = 0; q < nsplit; ++q) {
-      f &= __ldcg(&pp[q].fits);
-      a = min(a, __ldcg(&pp[q].dlo));
-      b = max(b, __ldcg(&pp[q].dhi));
-    }
+    for (int w = 0; w < RS_THREADS / 32; ++w) { f &= sfits[w]; a = min(a, sdlo[w]); b = max(b, sdhi[w]); }
     res[3 * MAXV] = f;
     if (P.gmask) {
       const bool over = a < INT32_MIN || b > INT32_MAX;

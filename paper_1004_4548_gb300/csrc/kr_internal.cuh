@@ -417,12 +417,26 @@ cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const i
 // flight.
 constexpr int64_t COMPACT_ONE_PASS_MAX = 1024;
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
+// Decoded outputs written by the compaction itself (one dense polynomial
+// product whose caller's output arrays are in device memory): term q's
+// exponents to exps[k * ld + q], its code to codes[q], its coefficient to
+// coef[q], for q < cap; coef == nullptr: none.
+struct DirectOut {
+  int32_t* exps = nullptr;
+  int64_t* codes = nullptr;
+  uint64_t* coef = nullptr;
+  int64_t ld = 0;
+  int64_t cap = 0;
+};
 // cstat: nchunks zeroed words of scan state; sync: two zeroed int64 (a
 // ticket counter, then an error flag set when a bounded wait gave up); scan:
-// scan_scratch_entries(nchunks) int64 for the two-pass form.
+// scan_scratch_entries(nchunks) int64 for the two-pass form.  With one
+// product compacted in one pass, the CTA of the last chunk also records the
+// product's count and status (no finishing launch); returns the launches made.
 cudaError_t launch_compact(Prod* dprods, int nprod, const int64_t* dchunk_begin, int64_t nchunks,
                            int64_t* dcounts, uint64_t* dcstat, int64_t* dsync, int64_t* dscan,
-                           uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s);
+                           uint64_t* okey, uint64_t* oval, int64_t cap, cudaStream_t s,
+                           const DirectOut& direct, int* launches);
 // exclusive scan of d[0, n) in place, *dtotal = sum; long arrays use several
 // CTAs and scratch of scan_scratch_entries(n) int64 (null: one CTA)
 int64_t scan_scratch_entries(int64_t n);
