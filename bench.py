@@ -433,10 +433,28 @@ def main():
         if sel("poisson_cfg4") or sel("poisson_cfg4_hash") or sel("poisson_cfg4_truncated"):
             f4, g4 = workload_cfg4()
             if sel("poisson_cfg4"):
-                paths["poisson_cfg4"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3, hbm_gbs=hbm)
+                p4 = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3, hbm_gbs=hbm)
+                # second denominator: random float64 adds into a key-indexed array of
+                # 2^32 8-byte slots (34 GB; the product's array is 46.6 GB), two per pair
+                upd = 2 * p4["term_products"]
+                ceil = kron.kr_probe_table_update_rate(32, min(p4["output_terms"], (7 << 32) // 10), upd, 2,
+                                                       local, 3)
+                p4["roofline"]["ceiling_random_f64_add_per_s"] = ceil
+                p4["roofline"]["frac_of_update_ceiling"] = (upd / (p4["kernel_ms"] * 1e-3)) / ceil \
+                    if ceil > 0 else None
+                paths["poisson_cfg4"] = p4
             if sel("poisson_cfg4_hash"):
-                paths["poisson_cfg4_hash"] = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3,
-                                                          path=kron.KR_PATH_HASH, hbm_gbs=hbm)
+                p4h = time_pseries(kron, ctx, f4, g4, dev, stream, flush, 3, path=kron.KR_PATH_HASH,
+                                   hbm_gbs=hbm)
+                # second denominator: random insert-or-adds (the insert routine, as the
+                # polynomial kernel issues them) into 2^30 16-byte slots, two per pair
+                upd = 2 * p4h["term_products"]
+                ceil = kron.kr_probe_table_update_rate(30, min(p4h["output_terms"], (7 << 30) // 10), upd, 0,
+                                                       local, 3)
+                p4h["roofline"]["ceiling_insert_per_s"] = ceil
+                p4h["roofline"]["frac_of_insert_ceiling"] = (upd / (p4h["kernel_ms"] * 1e-3)) / ceil \
+                    if ceil > 0 else None
+                paths["poisson_cfg4_hash"] = p4h
             if sel("poisson_cfg4_truncated"):
                 # Sec. 3's truncation of a Poisson product: pairs with |C_f C_g| >= 1e-38 (about 14%
                 # of them; the magnitudes fall with the exponents and multipliers) and terms of

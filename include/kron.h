@@ -406,10 +406,13 @@ double kr_probe_smem_accumulate_rate(int32_t device, int32_t reps);
  * of the value, issued as the polynomial hash kernel issues them) or of plain
  * atomic adds into each key's home slot (mode 1), with keys drawn at random
  * from `distinct` values, into a zeroed table of 2^log2_slots 16-byte slots in
- * device memory, on CUDA device `device`: best of `reps` launches, in updates
- * per second; < 0 on failure or bad arguments (log2_slots in [10, 30],
- * distinct at most 0.7 of the slots).  Allocates and frees the table;
- * synchronises the device's default stream. */
+ * device memory; mode 2: float64 atomic adds into a zeroed array of
+ * 2^log2_slots 8-byte slots at each key's hashed index (the Poisson dense
+ * path's key-indexed array), on CUDA device `device`: best of `reps` launches,
+ * in updates per second; < 0 on failure or bad arguments (log2_slots in
+ * [10, 30], in [10, 33] for mode 2; distinct at most 0.7 of the slots).
+ * Allocates and frees the table (up to 64 GiB in mode 2); synchronises the
+ * device's default stream. */
 double kr_probe_table_update_rate(int32_t device, int32_t log2_slots, int64_t distinct, int64_t updates,
                                   int32_t mode, int32_t reps);
 

@@ -276,7 +276,9 @@ def kr_probe_smem_atomic_rate(device: int = 0, f64: bool = False, reps: int = 5)
 def kr_probe_table_update_rate(log2_slots: int, distinct: int, updates: int, mode: int = 0,
                                device: int = 0, reps: int = 5) -> float:
     """Random insert-or-adds (mode 0) or plain adds (mode 1) per second into a
-    table of 2^log2_slots 16-byte slots (the hash path's ceiling)."""
+    table of 2^log2_slots 16-byte slots (the hash path's ceiling), or float64
+    adds (mode 2) into an array of 2^log2_slots 8-byte slots (the Poisson dense
+    path's ceiling)."""
     return float(load().kr_probe_table_update_rate(device, log2_slots, distinct, updates, mode, reps))
 
 

@@ -872,9 +872,16 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
         ctx->launches += 5;
       } else if (r.prod.kspan <= ORDER_BITMAP_MAX) {
         ck(ctx, order_by_bitmap(k, v, k2, v2, r.n, r.prod.kspan, Z.bins, s), "output order");
-        ck(ctx, cudaMemcpyAsync(k, k2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
-        ck(ctx, cudaMemcpyAsync(v, v2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
         ctx->launches += 4;
+        if (nlive == 1) {
+          // the only product: its ordered terms stay in the second arrays (context
+          // scratch, kept until the next call like the first)
+          r.key = k2;
+          r.val = v2;
+        } else {
+          ck(ctx, cudaMemcpyAsync(k, k2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
+          ck(ctx, cudaMemcpyAsync(v, v2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
+        }
       } else if (order_bins(r.prod.kspan) <= ORDER_MAX_BINS) {
         ck(ctx, order_by_bins(k, v, k2, v2, r.n, r.prod.kspan, Z.bins, s), "output order");
         ctx->launches += 4;
@@ -883,7 +890,10 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
         bool in_tmp = false;
         ck(ctx, radix_sort_pairs(k, v, k2, v2, r.n, bits, Z.scan, s, &in_tmp), "output sort");
         ctx->launches += 3 * ((bits + 7) / 8);
-        if (in_tmp) {
+        if (in_tmp && nlive == 1) {
+          r.key = k2;
+          r.val = v2;
+        } else if (in_tmp) {
           ck(ctx, cudaMemcpyAsync(k, k2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
           ck(ctx, cudaMemcpyAsync(v, v2, 8 * (size_t)r.n, cudaMemcpyDeviceToDevice, s), "copy");
         }

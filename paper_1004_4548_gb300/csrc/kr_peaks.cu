@@ -237,18 +237,37 @@ extern "C" double kr_probe_smem_atomic_rate(int32_t device, int32_t f64, int32_t
 // into a hash table; here an open-addressing table in device memory): random
 // insert-or-adds at a given table size and key count, in the insert routine
 // of the polynomial kernel, with nothing else in the loop.
+// Random float64 atomic adds into a key-indexed array of 8-byte slots (the
+// Poisson dense path's accumulation): update u adds 1.0 at the hashed index
+// of a key drawn from [0, distinct), four updates per thread in flight.
+__global__ void __launch_bounds__(256) k_probe_array_add(double* __restrict__ a, uint64_t mask,
+                                                         int64_t distinct, int64_t updates, uint64_t seed) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t u0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; u0 < updates; u0 += stride) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t u = u0 + r;
+      if (u < updates) {
+        const uint64_t key = mix64(seed ^ (uint64_t)(u + 1)) % (uint64_t)distinct;
+        atomicAdd(a + (mix64(key) & mask), 1.0);
+      }
+    }
+  }
+}
+
 extern "C" double kr_probe_table_update_rate(int32_t device, int32_t log2_slots, int64_t distinct,
                                              int64_t updates, int32_t mode, int32_t reps) {
-  if (log2_slots < 10 || log2_slots > 30 || distinct < 1 || updates < 1 || (mode != 0 && mode != 1) ||
-      distinct > (int64_t(1) << log2_slots) * 7 / 10)
+  if (log2_slots < 10 || log2_slots > (mode == 2 ? 33 : 30) || distinct < 1 || updates < 1 ||
+      mode < 0 || mode > 2 || distinct > (int64_t(1) << log2_slots) * 7 / 10)
     return -1.0;
   int prev = 0;
   cudaGetDevice(&prev);
   if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return -1.0; }
   const uint64_t slots = uint64_t(1) << log2_slots;
+  const uint64_t bytes = slots * (mode == 2 ? 8 : 16);
   uint64_t* table = nullptr;
   unsigned long long* fails = nullptr;
-  if (cudaMalloc(&table, slots * 16) != cudaSuccess || cudaMalloc(&fails, 8) != cudaSuccess) {
+  if (cudaMalloc(&table, bytes) != cudaSuccess || cudaMalloc(&fails, 8) != cudaSuccess) {
     cudaGetLastError();
     if (table) cudaFree(table);
     cudaSetDevice(prev);
@@ -260,10 +279,18 @@ extern "C" double kr_probe_table_update_rate(int32_t device, int32_t log2_slots,
   cudaEventCreate(&b);
   unsigned long long hf = 0;
   for (int r = 0; r < (reps > 0 ? reps : 5) + 1; ++r) {
-    cudaMemset(table, 0, slots * 16);
+    cudaMemset(table, 0, bytes);
     cudaMemset(fails, 0, 8);
     cudaEventRecord(a, 0);
-    launch_probe_table_update(table, slots, distinct, updates, mode, fails, 0);
+    if (mode == 2) {
+      int sms = 0, per = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_probe_array_add, 256, 0);
+      k_probe_array_add<<<sms * (per > 0 ? per : 1), 256>>>((double*)table, slots - 1, distinct, updates,
+                                                           0x5eed5eedull);
+    } else {
+      launch_probe_table_update(table, slots, distinct, updates, mode, fails, 0);
+    }
     cudaEventRecord(b, 0);
     cudaEventSynchronize(b);
     float ms = 0.f;

@@ -327,6 +327,11 @@ def test_peak_probes_report_rates(kron):
     add = kron.kr_probe_table_update_rate(22, 1 << 20, 1 << 23, 1, 0, 2)
     assert ins > 1e9 and add > 1e9
     assert kron.kr_probe_table_update_rate(22, 1 << 22, 1 << 23, 0, 0, 1) < 0   # load above 0.7 refused
+    # float64 adds into an 8-byte-slot array (the Poisson dense path's ceiling); 2^31 slots
+    # only in this mode, and no fourth mode
+    assert kron.kr_probe_table_update_rate(24, 1 << 22, 1 << 23, 2, 0, 2) > 1e9
+    assert kron.kr_probe_table_update_rate(31, 1 << 20, 1 << 20, 0, 0, 1) < 0
+    assert kron.kr_probe_table_update_rate(22, 1 << 20, 1 << 20, 3, 0, 1) < 0
     # multiply-add rates: the 32 x 32 -> 64-bit form no slower than the 64-bit one
     r0, r1, r2 = (kron.kr_probe_alu_rate(k, 0, 2) for k in (0, 1, 2))
     assert min(r0, r1, r2) > 1e11 and r1 > 0.8 * r0
