@@ -26,7 +26,10 @@
  *     of every term, row stride n, or the output capacity for outputs).
  *   - Pointers may address device memory or host memory (pageable or pinned);
  *     the library detects which with cudaPointerGetAttributes and stages host
- *     data through device scratch.  The caller owns every buffer it passes.
+ *     data through device scratch, except that the terms of a dense
+ *     polynomial product may be written by the GPU straight into pinned host
+ *     outputs through their device mapping.  The caller owns every buffer it
+ *     passes.
  *   - Every call is issued on the given stream.  Calls that return a term count
  *     synchronise that stream before returning; device outputs are complete
  *     when the call returns KR_OK only after a later synchronisation of the

@@ -43,8 +43,8 @@ struct kr_ctx {
   // then stays on the device until the decode (ProdResult::n = -1)
   bool allow_deferred = false;
   // a deferred dense polynomial product whose caller's outputs are all in
-  // device memory: the compaction decodes its terms there (direct_done), and
-  // the output step only reads the count
+  // device memory or pinned host memory: the compaction decodes its terms
+  // there (direct_done), and the output step only reads the count
   DirectOut direct{};
   bool direct_done = false;
   // split histogram (kron_split_hist): the pipeline stops after phase B1 and
@@ -158,6 +158,21 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// A pointer through which this device's kernels may write p: p itself for
+// device or managed memory, the mapped device address of pinned (page-locked)
+// host memory, nullptr for pageable host memory.
+void* device_view(void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  return nullptr;
 }
 
 // Records a stage boundary when profiling is on.
@@ -954,19 +969,25 @@ kr_status emit_poly(kr_ctx* ctx, kr_poly_out* h, cudaStream_t s) {
     h->omin[P.gvar] = P.gvar_min;
     h->omax[P.gvar] = P.gvar_max;
   }
+  if (n < 0 && ctx->direct_done) {
+    // the compaction has decoded the terms into the caller's arrays (device
+    // memory or pinned host memory): read the count and report it
+    const kr_status st = settle_deferred(ctx, s);
+    h->nterms = st == KR_OK ? ctx->res_n : 0;
+    if (st != KR_OK) return st;
+    return ctx->res_n > h->capacity ? KR_ERR_CAPACITY : KR_OK;
+  }
   if (n < 0) {
     const bool exps_dev = !h->exps || is_device_ptr(h->exps);
     const bool codes_dev = !h->codes || is_device_ptr(h->codes);
     if (exps_dev && codes_dev && is_device_ptr(h->coef)) {
-      // deferred count, device outputs: decode up to the capacity (unless the
-      // compaction has decoded into these arrays), read the count, then report it
-      if (!ctx->direct_done) {
-        ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->capacity, h->codes, s,
-                                   true, ctx->res_val, (uint64_t*)h->coef),
-           "decode");
-        ctx->launches += 1;
-        mark(ctx, s, "decode");
-      }
+      // deferred count, device outputs: decode up to the capacity, read the
+      // count, then report it
+      ck(ctx, launch_decode_poly(ctx->res_dprod, 0, ctx->res_key, h->capacity, h->exps, h->capacity, h->codes, s,
+                                 true, ctx->res_val, (uint64_t*)h->coef),
+         "decode");
+      ctx->launches += 1;
+      mark(ctx, s, "decode");
       const kr_status st = settle_deferred(ctx, s);
       h->nterms = st == KR_OK ? ctx->res_n : 0;
       if (st != KR_OK) return st;
@@ -1353,13 +1374,19 @@ kr_status poly_mul(kr_ctx* ctx, const kr_poly* f, const kr_poly* g, kr_poly_out*
     ctx->allow_deferred = true;
     ctx->direct = DirectOut{};
     ctx->direct_done = false;
-    if (h->capacity > 0 && is_device_ptr(h->coef) && (!h->exps || is_device_ptr(h->exps)) &&
-        (!h->codes || is_device_ptr(h->codes))) {
-      ctx->direct.exps = h->exps;
-      ctx->direct.codes = h->codes;
-      ctx->direct.coef = (uint64_t*)h->coef;
-      ctx->direct.ld = h->capacity;
-      ctx->direct.cap = h->capacity;
+    if (h->capacity > 0) {
+      // device memory, or pinned host memory through its device mapping (the
+      // GPU writes the terms across the host link; no copies afterwards)
+      void* cf = device_view(h->coef);
+      void* ex = h->exps ? device_view(h->exps) : nullptr;
+      void* cd = h->codes ? device_view(h->codes) : nullptr;
+      if (cf && (!h->exps || ex) && (!h->codes || cd)) {
+        ctx->direct.exps = (int32_t*)ex;
+        ctx->direct.codes = (int64_t*)cd;
+        ctx->direct.coef = (uint64_t*)cf;
+        ctx->direct.ld = h->capacity;
+        ctx->direct.cap = h->capacity;
+      }
     }
     try {
       run_pipeline(ctx, {in}, s, res);

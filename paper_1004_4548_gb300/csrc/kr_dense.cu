@@ -254,6 +254,8 @@ struct ChunkTable {
 #define KR_TILE_R 8
 #endif
 constexpr int TILE_R = KR_TILE_R;
+static_assert(TILE_R >= 1 && (TILE_R & (TILE_R - 1)) == 0 && 32 % TILE_R == 0,
+              "tiles end at warp boundaries");
 #ifndef KR_DENSE_Q
 #define KR_DENSE_Q 2
 #endif
@@ -388,19 +390,22 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
       const int nent = min(ACC_THREADS, kept - r0);
       const int ent = threadIdx.x;
       int32_t cnt = 0, l32 = 0, r = 0;
-      if (ent < nent) {
-        const int32_t off = ct.fc[ent].x;
-        const int32_t wid = off >> sh;   // floor: tiles stay within aligned windows of 2^sh codes
-        const bool owner = ent == 0 || wid != (ct.fc[ent - 1].x >> sh) || (ent & (TILE_R - 1)) == 0;
-        if (owner) {
-          r = 1;
-          while (r < TILE_R && ent + r < nent && (ct.fc[ent + r].x >> sh) == wid && ((ent + r) & (TILE_R - 1)) != 0)
-            ++r;
-          int64_t l, h;
-          g_lower_bound2(G, ng, GX, gn, gsh, -(int64_t)ct.fc[ent + r - 1].x, lim - off, &l, &h);
-          l32 = (int32_t)l;
-          cnt = (int32_t)(h - l);
-        }
+      const bool valid = ent < nent;
+      const int32_t off = valid ? ct.fc[ent].x : 0;
+      const int32_t wid = off >> sh;   // floor: tiles stay within aligned windows of 2^sh codes
+      const bool owner = valid && (ent == 0 || wid != (ct.fc[ent - 1].x >> sh) || (ent & (TILE_R - 1)) == 0);
+      // a tile runs to the next owner (every TILE_R-th entry is one, and
+      // TILE_R divides 32, so a warp's last tile ends at the warp's end) or
+      // to the table's end
+      const unsigned om = __ballot_sync(FULL, owner);
+      if (owner) {
+        const unsigned above = lane == 31 ? 0u : (om >> (lane + 1));
+        const int next = above ? lane + __ffs((int)above) : 32;
+        r = min(32 * warp + next, nent) - ent;
+        int64_t l, h;
+        g_lower_bound2(G, ng, GX, gn, gsh, -(int64_t)ct.fc[ent + r - 1].x, lim - off, &l, &h);
+        l32 = (int32_t)l;
+        cnt = (int32_t)(h - l);
       }
       ct.lo[ent] = l32;
       ct.run[ent] = (int16_t)r;
@@ -416,13 +421,17 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
         // k = the window of this lane's first slot (the last k with
         // excl[k] <= p); p < excl[ACC_THREADS] keeps k + 1 <= ACC_THREADS below
         int32_t p = pb + lane;
-        int k = 0, hi_k = ACC_THREADS;
+        // the window of the warp's first slot: the last k with excl[k] <= pb,
+        // by two ballots over the ascending excl (16 entries a lane, then 16
+        // lanes over one lane's entries); each lane then advances to its own
+        // slot's window in the walk below
+        int k;
         {
-          const int32_t ps = min(p, pe - 1);
-          while (hi_k - k > 1) {
-            const int mid = (k + hi_k) >> 1;
-            if (ct.excl[mid] <= ps) k = mid; else hi_k = mid;
-          }
+          constexpr int STEP = ACC_THREADS / 32;
+          const unsigned le = __ballot_sync(FULL, ct.excl[lane * STEP] <= pb);   // lane 0: excl[0] = 0
+          const int base = (31 - __clz((int)le)) * STEP;
+          const unsigned le2 = __ballot_sync(FULL, lane < STEP && ct.excl[base + (lane < STEP ? lane : 0)] <= pb);
+          k = base + 31 - __clz((int)le2);
         }
         int32_t e0 = ct.excl[k], e1 = ct.excl[k + 1];
         const int32_t lim32 = (int32_t)lim;
@@ -491,6 +500,36 @@ __device__ __forceinline__ void dense_task_body(const Prod& P, const DenseTask& 
   }
 }
 
+// int64 sums: four slots per thread and step, their low and high words read
+// by two 16-byte shared loads (the slice's halves start 16-byte aligned, S
+// being a multiple of 32); a single task's block is written with 16-byte
+// stores where the array is 16-byte aligned.
+__device__ __forceinline__ void dense_flush_i64(const Prod& P, const DenseTask& tk, const Slice<int64_t>& acc) {
+  const int64_t S = P.S;
+  const int64_t B = tk.block * S;   // relative to the window
+  const int64_t lim = min(S, P.kspan - B);
+  unsigned long long* out = (unsigned long long*)P.dense + B;
+  const bool v16 = (((uintptr_t)out) & 15) == 0;
+  for (int64_t s = 4 * (int64_t)threadIdx.x; s < lim; s += 4 * (int64_t)blockDim.x) {
+    const uint4 lo = *reinterpret_cast<const uint4*>(acc.lo + s);
+    const uint4 hi = *reinterpret_cast<const uint4*>(acc.hi + s);
+    const unsigned long long v[4] = {((unsigned long long)hi.x << 32) | lo.x, ((unsigned long long)hi.y << 32) | lo.y,
+                                     ((unsigned long long)hi.z << 32) | lo.z, ((unsigned long long)hi.w << 32) | lo.w};
+    if (tk.single && v16 && s + 4 <= lim) {
+      *reinterpret_cast<ulonglong2*>(out + s) = make_ulonglong2(v[0], v[1]);
+      *reinterpret_cast<ulonglong2*>(out + s + 2) = make_ulonglong2(v[2], v[3]);
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (s + i < lim) {
+        if (tk.single) out[s + i] = v[i];   // the block's only task: every slot, zeros included
+        else if (v[i] != 0) atomicAdd(&out[s + i], v[i]);
+      }
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void dense_flush(const Prod& P, const DenseTask& tk, const Slice<T>& acc) {
   const int64_t S = P.S;
@@ -524,8 +563,8 @@ __global__ void __launch_bounds__(ACC_THREADS, KR_ACC_MIN_BLOCKS) k_dense_accum(
     if (P.status) continue;
     const int64_t S = P.S;
     // zero the slice (8 bytes per code for both types)
-    int64_t* z = (int64_t*)smem_raw;
-    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) z[s] = 0;
+    uint4* z = (uint4*)smem_raw;   // S * 8 bytes, S a multiple of 32
+    for (int64_t s = threadIdx.x; s < S / 2; s += blockDim.x) z[s] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     if (P.f64) {
       const Slice<double> sl(smem_raw, S);
@@ -537,7 +576,7 @@ __global__ void __launch_bounds__(ACC_THREADS, KR_ACC_MIN_BLOCKS) k_dense_accum(
       if (P.coef32) dense_task_body<int64_t, true>(P, tk, sl, ct);
       else dense_task_body<int64_t, false>(P, tk, sl, ct);
       __syncthreads();
-      dense_flush<int64_t>(P, tk, sl);
+      dense_flush_i64(P, tk, sl);
     }
     __syncthreads();
   }

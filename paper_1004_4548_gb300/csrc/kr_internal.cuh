@@ -418,7 +418,8 @@ cudaError_t launch_hash_insert(Prod* dprods, const int32_t* dhash_prods, const i
 constexpr int64_t COMPACT_ONE_PASS_MAX = 1024;
 // Writes at most cap terms; products whose terms end beyond cap get ST_OUTCAP.
 // Decoded outputs written by the compaction itself (one dense polynomial
-// product whose caller's output arrays are in device memory): term q's
+// product whose caller's output arrays are in device memory or in pinned
+// host memory, through its device mapping): term q's
 // exponents to exps[k * ld + q], its code to codes[q], its coefficient to
 // coef[q], for q < cap; coef == nullptr: none.
 struct DirectOut {

@@ -1,0 +1,91 @@
+"""Where the library writes a product's terms, against the oracle (bit-exact):
+device arrays, pinned host arrays (written by the GPU through their device
+mapping), pageable host arrays (staged through device scratch), with and
+without the code array, and with a capacity below the term count (the call
+reports KR_ERR_CAPACITY and kron_fetch_poly then fills larger arrays).
+Through the C ABI, as a caller of include/kron.h would."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_compare import assert_poly_equal
+from workloads import workload_cfg1, workload_cfg2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1004_4548_gb300 as k
+    from paper_1004_4548_gb300 import binding as B
+    L = k.load()
+    return k, B, L, k.Context(0)
+
+
+def buffers(kind, nv, cap, codes):
+    import torch
+    kw = {"cuda": dict(device="cuda:0"), "pinned": dict(pin_memory=True), "pageable": dict()}[kind]
+    ex = torch.empty((nv, cap), dtype=torch.int32, **kw)
+    cf = torch.empty((cap,), dtype=torch.int64, **kw)
+    cd = torch.empty((cap,), dtype=torch.int64, **kw) if codes else None
+    return ex, cf, cd
+
+
+def mul(env, f, g, kind, cap, codes):
+    import torch
+    k, B, L, ctx = env
+    fe, fc = torch.from_numpy(f.exps).cuda(), torch.from_numpy(f.coef).cuda()
+    ge, gc = torch.from_numpy(g.exps).cuda(), torch.from_numpy(g.coef).cuda()
+    nv = f.exps.shape[0]
+    F = B.kr_poly(nv, f.n, fe.data_ptr(), fc.data_ptr(), B.KR_I64)
+    G = B.kr_poly(nv, g.n, ge.data_ptr(), gc.data_ptr(), B.KR_I64)
+    ex, cf, cd = buffers(kind, nv, cap, codes)
+    H = B.kr_poly_out(nv, cap, 0, ex.data_ptr(), cf.data_ptr(), cd.data_ptr() if codes else None)
+    O = B.kr_opts()
+    st = L.poly_mul(ctx.h, ctypes.byref(F), ctypes.byref(G), ctypes.byref(H), ctypes.byref(O), None)
+    if st == k.KR_ERR_CAPACITY:
+        n = int(H.nterms)
+        assert n > cap
+        ex, cf, cd = buffers(kind, nv, n, codes)
+        H = B.kr_poly_out(nv, n, 0, ex.data_ptr(), cf.data_ptr(), cd.data_ptr() if codes else None)
+        st = L.kron_fetch_poly(ctx.h, ctypes.byref(H), None)
+    assert st == 0, L.kr_last_error(ctx.h).decode()
+    torch.cuda.synchronize()
+    n = int(H.nterms)
+    ld = ex.shape[1]
+    exps = ex.cpu().numpy()[:, :n] if ld >= n else None
+    return exps, cf.cpu().numpy()[:n], (cd.cpu().numpy()[:n] if codes else None), n
+
+
+@pytest.mark.parametrize("kind", ["cuda", "pinned", "pageable"])
+@pytest.mark.parametrize("codes", [False, True])
+@pytest.mark.parametrize("short", [False, True])
+def test_outputs(env, kind, codes, short):
+    f, g = workload_cfg2() if not short else workload_cfg1()
+    r = oracle.poly_mul(f, g, nthreads=8)
+    m = r.coef.shape[0]
+    cap = m // 3 if short else m + 17   # below the count: a capacity retry; above: spare room
+    exps, coef, cd, n = mul(env, f, g, kind, cap, codes)
+    assert n == m
+    assert_poly_equal(exps, coef, r, f"{kind} codes={codes} cap={cap}")
+    if codes:
+        # the codes ascend and decode to the exponents: variable 0 least significant
+        # over the output box of widths w_k
+        assert (np.diff(cd) > 0).all()
+        lo = r.exps.min(axis=1).astype(np.int64)
+        w = (r.exps.max(axis=1) - r.exps.min(axis=1) + 1).astype(np.int64)
+        # the library's box is the sum of the operand boxes; take its widths
+        fw = f.exps.max(axis=1).astype(np.int64) - f.exps.min(axis=1) + g.exps.max(axis=1) - g.exps.min(axis=1) + 1
+        flo = f.exps.min(axis=1).astype(np.int64) + g.exps.min(axis=1)
+        c = np.zeros(n, dtype=np.int64)
+        mult = 1
+        for k in range(exps.shape[0]):
+            c += (exps[k].astype(np.int64) - flo[k]) * mult
+            mult *= int(fw[k])
+        assert np.array_equal(c, cd)
+        assert (lo >= flo).all() and (w <= fw).all()
