@@ -115,6 +115,11 @@ kr_status from_cuda(cudaError_t e) {
 }
 
 // Bump allocation over a base pointer; base == nullptr measures only.
+// pinned host inputs of at most this many values are read in place
+#ifndef KR_ZERO_COPY_MAX
+#define KR_ZERO_COPY_MAX (int64_t(1) << 18)
+#endif
+
 struct Bump {
   char* base;
   size_t off = 0;
@@ -256,7 +261,16 @@ struct JobIn {
 template <typename T>
 const T* stage(kr_ctx* ctx, Bump& b, const T* src, int64_t count, cudaStream_t s) {
   if (!src || count <= 0) return src;
-  if (is_device_ptr(src)) return src;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, src) != cudaSuccess) {
+    cudaGetLastError();
+    a.type = cudaMemoryTypeUnregistered;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return src;
+  // a small operand in pinned host memory is read by the kernels through its
+  // device mapping (across the host link), with no staging copy
+  if (a.type == cudaMemoryTypeHost && a.devicePointer && count <= KR_ZERO_COPY_MAX)
+    return (const T*)a.devicePointer;
   T* dst = b.take<T>(count);
   if (b.base) ck(ctx, cudaMemcpyAsync(dst, src, (size_t)count * sizeof(T), cudaMemcpyHostToDevice, s),
                  "stage input");

@@ -1,6 +1,7 @@
-"""Where the library writes a product's terms, against the oracle (bit-exact):
-device arrays, pinned host arrays (written by the GPU through their device
-mapping), pageable host arrays (staged through device scratch), with and
+"""Where the library reads a product's operands and writes its terms, against
+the oracle (bit-exact): device arrays, pinned host arrays (read and written by
+the GPU through their device mapping), pageable host arrays (staged through
+device scratch), with and
 without the code array, and with a capacity below the term count (the call
 reports KR_ERR_CAPACITY and kron_fetch_poly then fills larger arrays).
 Through the C ABI, as a caller of include/kron.h would."""
@@ -36,11 +37,23 @@ def buffers(kind, nv, cap, codes):
     return ex, cf, cd
 
 
+def inputs(kind, p):
+    """The operand's arrays where the outputs go: device, pinned host (read by
+    the kernels in place) or pageable host (staged)."""
+    import torch
+    e, c = torch.from_numpy(np.ascontiguousarray(p.exps)), torch.from_numpy(np.ascontiguousarray(p.coef))
+    if kind == "cuda":
+        return e.cuda(), c.cuda()
+    if kind == "pinned":
+        return e.pin_memory(), c.pin_memory()
+    return e, c
+
+
 def mul(env, f, g, kind, cap, codes):
     import torch
     k, B, L, ctx = env
-    fe, fc = torch.from_numpy(f.exps).cuda(), torch.from_numpy(f.coef).cuda()
-    ge, gc = torch.from_numpy(g.exps).cuda(), torch.from_numpy(g.coef).cuda()
+    fe, fc = inputs(kind, f)
+    ge, gc = inputs(kind, g)
     nv = f.exps.shape[0]
     F = B.kr_poly(nv, f.n, fe.data_ptr(), fc.data_ptr(), B.KR_I64)
     G = B.kr_poly(nv, g.n, ge.data_ptr(), gc.data_ptr(), B.KR_I64)
