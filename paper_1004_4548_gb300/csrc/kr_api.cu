@@ -807,6 +807,8 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
     DirectOut direct{};
     if (deferred && ctx->direct.coef) {
       const Prod& P0 = plans[live_ids[0]].p;
+      // polynomials only: on the Poisson product's 596 M terms a decode pass per
+      // chunk slowed the compaction more than the separate decode costs
       if (P0.path == PATH_DENSE && P0.nt == 0) {
         direct = ctx->direct;
         ctx->direct_done = true;
@@ -1458,6 +1460,8 @@ kr_status poisson_mul(kr_ctx* ctx, const kr_pseries* f, const kr_pseries* g, kr_
     ctx->allow_deferred = is_device_ptr(h->coef) && (!h->exps || is_device_ptr(h->exps)) &&
                           (!h->trig || is_device_ptr(h->trig)) && (!h->kind || is_device_ptr(h->kind)) &&
                           (!h->codes || is_device_ptr(h->codes));
+    ctx->direct = DirectOut{};
+    ctx->direct_done = false;
     try {
       run_pipeline(ctx, {in}, s, res);
     } catch (...) {

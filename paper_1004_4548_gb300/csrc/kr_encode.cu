@@ -597,26 +597,12 @@ __global__ void __launch_bounds__(256) k_decode_pseries(const Prod* __restrict__
                                                         uint64_t* __restrict__ coef) {
   const Prod& P = prods[prod];
   if (dev_count) n = P.status ? 0 : min(n, P.nout);
-  const int64_t per_kind = P.T2 * P.Wp;
-  const int64_t half = P.T2 - 1;   // sum_k c_k R_k
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t key = (int64_t)okey[q] + P.klo;   // keys are relative to the key window
     if (codes) codes[q] = key;
     if (coef) coef[q] = vals[q];
-    const int64_t kd = key >= per_kind ? 1 : 0;   // keys lie below 2 * per_kind
-    int64_t pc;
-    const int64_t T = divmod_nn(key - kd * per_kind, P.Wp, &pc);
-    if (kind) kind[q] = (uint8_t)kd;
-    if (exps) decode_poly_part(P, pc, exps, ld, q);
-    if (trig) {
-      int64_t u = T + half;
-      for (int k = 0; k < P.nt; ++k) {
-        int64_t d = u;
-        if (k + 1 < P.nt) u = divmod_nn(u, P.w[P.np + k], &d);
-        trig[(int64_t)k * ld + q] = (int32_t)(d + P.omin[P.np + k]);
-      }
-    }
+    decode_pseries_term(P, key, exps, trig, kind, ld, q);
   }
 }
 

@@ -294,6 +294,28 @@ __device__ __forceinline__ void decode_poly_part(const Prod& P, int64_t pc, int3
   exps[(int64_t)P.gvar * ld + q] = (int32_t)(pc + P.omin[P.gvar] - deg_rest);
 }
 
+// Exponents, multipliers and kind of an output key of a Poisson product
+// (key = (kind * T2 + tcode) * Wp + pcode, the tcode balanced over the
+// symmetric multiplier box) to term q of the output arrays (row stride ld).
+__device__ __forceinline__ void decode_pseries_term(const Prod& P, int64_t key, int32_t* __restrict__ exps,
+                                                    int32_t* __restrict__ trig, uint8_t* __restrict__ kind,
+                                                    int64_t ld, int64_t q) {
+  const int64_t per_kind = P.T2 * P.Wp;
+  const int64_t kd = key >= per_kind ? 1 : 0;   // keys lie below 2 * per_kind
+  int64_t pc;
+  const int64_t T = divmod_nn(key - kd * per_kind, P.Wp, &pc);
+  if (kind) kind[q] = (uint8_t)kd;
+  if (exps) decode_poly_part(P, pc, exps, ld, q);
+  if (trig) {
+    int64_t u = T + (P.T2 - 1);   // T2 - 1 = sum_k c_k R_k
+    for (int k = 0; k < P.nt; ++k) {
+      int64_t d = u;
+      if (k + 1 < P.nt) u = divmod_nn(u, P.w[P.np + k], &d);
+      trig[(int64_t)k * ld + q] = (int32_t)(d + P.omin[P.np + k]);
+    }
+  }
+}
+
 // int64 accumulate into shared memory as two 32-bit words (the low word at
 // shared address a, the high word hi_dist bytes further): a 32-bit atomic add
 // of the low half returning the old value, its carry by add-with-carry, and a
