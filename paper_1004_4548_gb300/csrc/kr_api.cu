@@ -508,7 +508,7 @@ void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
       max_hash_out = std::max(max_hash_out, pl.out_cap);
       const int64_t nb = order_bins(pl.p.kspan);
       if (order_buckets(pl.p.kspan) <= ORDER_MAX_BUCKETS)
-        bins_total = std::max(bins_total, order_buckets_scratch(pl.p.kspan));
+        bins_total = std::max(bins_total, order_buckets_scratch(pl.p.kspan, pl.out_cap));
       if (pl.p.kspan <= ORDER_BITMAP_MAX)
         bins_total = std::max(bins_total, (order_bitmap_bytes(pl.p.kspan) + 7) / 8);
       else if (nb <= ORDER_MAX_BINS) bins_total = std::max(bins_total, order_bins_scratch(pl.p.kspan));

@@ -490,14 +490,16 @@ cudaError_t order_by_bitmap(const uint64_t* key, const uint64_t* val, uint64_t* 
 cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
                           int64_t krange, int64_t* bins, cudaStream_t s);
 // Large outputs over code ranges whose one-bit-per-code bitmap would not stay
-// in L2 (above 2^30 codes, 128 MB): terms bucketed by 2^20 codes, then ranked
-// in each bucket by a shared-memory bitmap; sorted in place (key2/val2: n
-// terms of scratch; bins: order_buckets_scratch(krange) int64).
+// in L2 (above 2^30 codes, 128 MB): terms partitioned by the high digits of
+// their code in two tile-sorted passes into buckets of about 2048 terms, each
+// then ranked by a shared-memory bitmap (or, past 2^36 codes, bucketed by
+// 2^20 codes and ranked there); sorted in place (key2/val2: n terms of
+// scratch; bins: order_buckets_scratch(krange, n_max) int64 for up to n_max terms).
 constexpr int64_t ORDER_BUCKET_MIN_N = int64_t(1) << 20;
 constexpr int64_t ORDER_BUCKET_MIN_RANGE = int64_t(1) << 30;
 constexpr int64_t ORDER_MAX_BUCKETS = int64_t(1) << 22;
 int64_t order_buckets(int64_t krange);
-int64_t order_buckets_scratch(int64_t krange);
+int64_t order_buckets_scratch(int64_t krange, int64_t n_max);
 cudaError_t order_by_buckets(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
                              int64_t krange, int64_t* bins, cudaStream_t s);
 

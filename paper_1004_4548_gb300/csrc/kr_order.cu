@@ -128,9 +128,347 @@ constexpr int BK_WORDS = (int)(BK_CODES / 64);    // 16384 bitmap words: 128 KB,
 constexpr int BK_THREADS = 1024;
 
 int64_t order_buckets(int64_t krange) { return (krange + BK_CODES - 1) / BK_CODES; }
-int64_t order_buckets_scratch(int64_t krange) {
+
+// the contiguous slice of n terms of this CTA
+__device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  *a = min(n, (int64_t)blockIdx.x * per);
+  *b = min(n, *a + per);
+}
+
+// ---------------------------------------------------------------------------
+// partition ordering (the first choice for large outputs over wide code
+// ranges): the terms are partitioned by the high digits of their fine bucket
+// (2^F consecutive codes, F chosen for about 2048 terms a bucket) in two
+// passes, each pass sorting a tile of PT_TILE terms by digit in shared memory
+// so that the tile goes out as one contiguous run per digit:
+//   1. super-buckets of 256 fine buckets: the counts, then a scatter of every
+//      CTA's slice in tiles to its reserved range of each super-bucket;
+//   2. one CTA per super-bucket: its 256 fine counts and offsets, then the
+//      same tile scatter by fine bucket (back into the first arrays);
+//   3. each fine bucket ranked by a bitmap of its 2^F codes in shared memory
+//      and written back in order from a shared-memory copy (a bucket above
+//      PT_SMAX terms is ranked into the second arrays and copied back).
+// The result is in place.
+// ---------------------------------------------------------------------------
+#ifndef KR_ORDER_PARTITION
+#define KR_ORDER_PARTITION 1
+#endif
+constexpr int PT_THREADS = 512;
+constexpr int PT_TILE = 8192;                   // terms per tile: 128 KB of (key, val) in shared memory
+constexpr int PT_PER = PT_TILE / PT_THREADS;    // 16 terms per thread
+constexpr int PT_FINE_LOG2 = 8;                 // fine buckets per super-bucket: 256
+constexpr int PT_FINE = 1 << PT_FINE_LOG2;
+constexpr int64_t PT_MAX_SUPERS = 2048;
+constexpr int PT_F_MIN = 10, PT_F_MAX = 17;     // fine buckets of 2^F codes: bitmaps of at most 16 KB
+constexpr int PT_SMAX = 4096;                   // a fine bucket is sorted in shared memory up to this
+
+struct PtPlan {
+  int F = 0;
+  int64_t nfb = 0, nsup = 0;
+  bool ok = false;
+};
+
+static PtPlan pt_plan(int64_t n, int64_t krange) {
+  PtPlan pl;
+  if (n < 2 || krange < 1) return pl;
+  int F = 0;
+  while (F < PT_F_MAX && (double)(int64_t(1) << (F + 1)) * (double)n <= 2048.0 * (double)krange) ++F;
+  if (F < PT_F_MIN) F = PT_F_MIN;
+  pl.F = F;
+  pl.nfb = (krange + (int64_t(1) << F) - 1) >> F;
+  pl.nsup = (pl.nfb + PT_FINE - 1) >> PT_FINE_LOG2;
+  pl.ok = pl.nsup <= PT_MAX_SUPERS;
+  return pl;
+}
+
+int64_t order_buckets_scratch(int64_t krange, int64_t n_max) {
   const int64_t nb = order_buckets(krange);
-  return 3 * (nb + 1) + scan_scratch_entries(nb);
+  int64_t need = 3 * (nb + 1) + scan_scratch_entries(nb);
+  // partition ordering for any count up to n_max: fewer terms make larger
+  // fine buckets, so n_max gives the most of them
+  const PtPlan pl = pt_plan(n_max, krange);
+  if (pl.ok) need = std::max(need, 2 * (pl.nsup + 1) + (pl.nfb + 1) + scan_scratch_entries(pl.nsup));
+  return need;
+}
+
+// Exclusive scan of cnt[0, m) into ofs[0, m) by the whole CTA (m <= 4 * PT_THREADS);
+// wsum: PT_THREADS / 32 words of scratch.
+__device__ __forceinline__ void pt_scan(const uint32_t* cnt, uint32_t* ofs, int m, uint32_t* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (m + PT_THREADS - 1) / PT_THREADS;   // consecutive entries per thread
+  const int a = min(m, tid * per), b = min(m, a + per);
+  uint32_t t = 0;
+  for (int i = a; i < b; ++i) t += cnt[i];
+  uint32_t x = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < PT_THREADS / 32 ? wsum[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < PT_THREADS / 32) wsum[lane] = v;
+  }
+  __syncthreads();
+  uint32_t run = (warp > 0 ? wsum[warp - 1] : 0u) + x - t;
+  for (int i = a; i < b; ++i) {
+    const uint32_t c = cnt[i];
+    ofs[i] = run;
+    run += c;
+  }
+  __syncthreads();
+}
+
+// Tile scatter shared by passes 1 and 2: the terms [t0, t1) (at most PT_TILE)
+// of (key, val) go to (okey, oval) grouped by digit dig(key) in [0, m): the
+// terms of digit d to base[d] + cur[d] onwards, as one run.  tcnt, tofs: m
+// words; stage: PT_TILE keys then PT_TILE values.
+template <typename Dig>
+__device__ __forceinline__ void pt_tile(const uint64_t* __restrict__ key, const uint64_t* __restrict__ val,
+                                        int64_t t0, int64_t t1, int m, Dig dig, const int64_t* base,
+                                        uint32_t* cur, uint32_t* tcnt, uint32_t* tofs, uint64_t* stage,
+                                        uint32_t* wsum, uint64_t* __restrict__ okey,
+                                        uint64_t* __restrict__ oval) {
+  const int tid = threadIdx.x;
+  for (int d = tid; d < m; d += PT_THREADS) tcnt[d] = 0;
+  __syncthreads();
+  uint64_t k[PT_PER];
+  uint32_t r[PT_PER];
+#pragma unroll
+  for (int q = 0; q < PT_PER; ++q) {
+    const int64_t i = t0 + (int64_t)q * PT_THREADS + tid;
+    k[q] = 0;
+    r[q] = 0;
+    if (i < t1) {
+      k[q] = key[i];
+      r[q] = atomicAdd(&tcnt[dig(k[q])], 1u);
+    }
+  }
+  __syncthreads();
+  pt_scan(tcnt, tofs, m, wsum);
+#pragma unroll
+  for (int q = 0; q < PT_PER; ++q) {
+    const int64_t i = t0 + (int64_t)q * PT_THREADS + tid;
+    if (i < t1) {
+      const uint32_t pos = tofs[dig(k[q])] + r[q];
+      stage[pos] = k[q];
+      stage[PT_TILE + pos] = val[i];
+    }
+  }
+  __syncthreads();
+  const int nt = (int)(t1 - t0);
+  for (int j = tid; j < nt; j += PT_THREADS) {
+    const uint64_t kk = stage[j];
+    const int d = dig(kk);
+    const int64_t g = base[d] + (int64_t)cur[d] + (j - (int64_t)tofs[d]);
+    okey[g] = kk;
+    oval[g] = stage[PT_TILE + j];
+  }
+  __syncthreads();
+  for (int d = tid; d < m; d += PT_THREADS) cur[d] += tcnt[d];
+  __syncthreads();
+}
+
+// The super-bucket of a key (keys lie below the code range, so the clamp
+// only keeps a broken input's terms inside the arrays).
+__device__ __forceinline__ int pt_sup(uint64_t k, int sh, int nsup) {
+  const uint64_t d = k >> sh;
+  return d < (uint64_t)nsup ? (int)d : nsup - 1;
+}
+
+// Pass 1 counts: super-bucket histograms of every CTA's slice.
+__global__ void __launch_bounds__(PT_THREADS) k_pt_count(const uint64_t* __restrict__ key, int64_t n, int F,
+                                                        int nsup, unsigned long long* __restrict__ cnt) {
+  extern __shared__ uint32_t ph[];
+  for (int d = threadIdx.x; d < nsup; d += blockDim.x) ph[d] = 0;
+  __syncthreads();
+  int64_t a, e;
+  bk_slice(n, &a, &e);
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) atomicAdd(&ph[pt_sup(key[i], F + PT_FINE_LOG2, nsup)], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < nsup; d += blockDim.x)
+    if (ph[d]) atomicAdd(&cnt[d], (unsigned long long)ph[d]);
+}
+
+// Pass 1: each CTA reserves its slice's share of every super-bucket, then
+// scatters the slice tile by tile into (key2, val2).
+__global__ void __launch_bounds__(PT_THREADS) k_pt_super(const uint64_t* __restrict__ key,
+                                                        const uint64_t* __restrict__ val, int64_t n, int F,
+                                                        int nsup, const int64_t* __restrict__ soff,
+                                                        unsigned long long* __restrict__ scur,
+                                                        uint64_t* __restrict__ key2, uint64_t* __restrict__ val2) {
+  extern __shared__ __align__(16) unsigned char pt_smem[];
+  uint64_t* stage = (uint64_t*)pt_smem;                                 // 2 * PT_TILE
+  int64_t* base = (int64_t*)(pt_smem + 16 * PT_TILE);                  // [nsup]
+  uint32_t* cur = (uint32_t*)(base + nsup);                             // [nsup]
+  uint32_t* tcnt = cur + nsup;                                          // [nsup]
+  uint32_t* tofs = tcnt + nsup;                                         // [nsup]
+  __shared__ uint32_t wsum[PT_THREADS / 32];
+  const int tid = threadIdx.x;
+  const int sh = F + PT_FINE_LOG2;
+  int64_t a, e;
+  bk_slice(n, &a, &e);
+  for (int d = tid; d < nsup; d += PT_THREADS) tcnt[d] = 0;
+  __syncthreads();
+  for (int64_t i = a + tid; i < e; i += PT_THREADS) atomicAdd(&tcnt[pt_sup(key[i], sh, nsup)], 1u);
+  __syncthreads();
+  for (int d = tid; d < nsup; d += PT_THREADS) {
+    base[d] = soff[d] + (tcnt[d] ? (int64_t)atomicAdd(&scur[d], (unsigned long long)tcnt[d]) : 0);
+    cur[d] = 0;
+  }
+  __syncthreads();
+  auto dig = [sh, nsup](uint64_t k) -> int { return pt_sup(k, sh, nsup); };
+  for (int64_t t0 = a; t0 < e; t0 += PT_TILE)
+    pt_tile(key, val, t0, min(e, t0 + PT_TILE), nsup, dig, base, cur, tcnt, tofs, stage, wsum, key2, val2);
+}
+
+// Pass 2: one CTA per super-bucket: its fine counts and offsets (foff, the
+// fine buckets' first positions), then the tile scatter by fine bucket from
+// (key2, val2) back into (key, val).
+__global__ void __launch_bounds__(PT_THREADS) k_pt_fine(const uint64_t* __restrict__ key2,
+                                                       const uint64_t* __restrict__ val2, int64_t n, int F,
+                                                       int64_t nfb, const int64_t* __restrict__ soff,
+                                                       int64_t* __restrict__ foff, uint64_t* __restrict__ key,
+                                                       uint64_t* __restrict__ val) {
+  extern __shared__ __align__(16) unsigned char pt_smem[];
+  uint64_t* stage = (uint64_t*)pt_smem;
+  __shared__ int64_t base[PT_FINE];
+  __shared__ uint32_t cur[PT_FINE], tcnt[PT_FINE], tofs[PT_FINE];
+  __shared__ uint32_t wsum[PT_THREADS / 32];
+  const int tid = threadIdx.x;
+  const int64_t d = blockIdx.x;
+  const int64_t s0 = soff[d], s1 = soff[d + 1];
+  for (int f = tid; f < PT_FINE; f += PT_THREADS) tcnt[f] = 0;
+  __syncthreads();
+  for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) atomicAdd(&tcnt[(key2[i] >> F) & (PT_FINE - 1)], 1u);
+  __syncthreads();
+  pt_scan(tcnt, tofs, PT_FINE, wsum);
+  for (int f = tid; f < PT_FINE; f += PT_THREADS) {
+    base[f] = s0 + tofs[f];
+    cur[f] = 0;
+    const int64_t fb = d * PT_FINE + f;
+    if (fb < nfb) foff[fb] = s0 + tofs[f];
+  }
+  if (d == gridDim.x - 1 && tid == 0) foff[nfb] = n;
+  __syncthreads();
+  auto dig = [F](uint64_t k) -> int { return (int)((k >> F) & (PT_FINE - 1)); };
+  for (int64_t t0 = s0; t0 < s1; t0 += PT_TILE)
+    pt_tile(key2, val2, t0, min(s1, t0 + PT_TILE), PT_FINE, dig, base, cur, tcnt, tofs, stage, wsum, key, val);
+}
+
+// Pass 3: fine buckets in ticket order; bucket b holds the terms
+// [foff[b], foff[b+1]) of (key, val), codes in [b << F, (b + 1) << F).
+__global__ void __launch_bounds__(PT_THREADS) k_pt_rank(uint64_t* __restrict__ key, uint64_t* __restrict__ val,
+                                                       int F, int64_t nfb, const int64_t* __restrict__ foff,
+                                                       unsigned long long* __restrict__ ticket,
+                                                       uint64_t* __restrict__ key2, uint64_t* __restrict__ val2) {
+  extern __shared__ __align__(16) unsigned char pt_smem[];
+  uint64_t* stage = (uint64_t*)pt_smem;                                       // 2 * PT_SMAX
+  unsigned long long* bits = (unsigned long long*)(pt_smem + 16 * PT_SMAX);   // [2^(F-6)]
+  const int nw = 1 << (F - 6);
+  uint32_t* pre = (uint32_t*)(bits + nw);                                     // [2^(F-6)]
+  __shared__ uint32_t wsum[PT_THREADS / 32];
+  __shared__ int64_t s_b;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_b = (int64_t)atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int64_t b = s_b;
+    __syncthreads();
+    if (b >= nfb) break;
+    const int64_t s0 = foff[b], s1 = foff[b + 1];
+    const int64_t m = s1 - s0;
+    if (m < 2) continue;   // uniform across the CTA
+    for (int w = tid; w < nw; w += PT_THREADS) bits[w] = 0ull;
+    __syncthreads();
+    const uint64_t lo = (uint64_t)b << F;
+    const uint64_t span = uint64_t(1) << F;
+    for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) {
+      const uint64_t c = key[i] - lo;   // < 2^F for the bucket's keys
+      if (c < span) atomicOr(&bits[c >> 6], 1ull << (c & 63));
+    }
+    __syncthreads();
+    // word prefix counts (nw <= 2048: at most 4 words per thread)
+    for (int w = tid; w < nw; w += PT_THREADS) pre[w] = (uint32_t)__popcll(bits[w]);
+    __syncthreads();
+    pt_scan(pre, pre, nw, wsum);   // in place: each thread reads its entries before writing them
+    if (m <= PT_SMAX) {
+      for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) {
+        const uint64_t k = key[i];
+        const uint64_t c = k - lo;
+        if (c >= span) continue;
+        const uint32_t rank = pre[c >> 6] + (uint32_t)__popcll(bits[c >> 6] & ((1ull << (c & 63)) - 1ull));
+        stage[rank] = k;
+        stage[PT_SMAX + rank] = val[i];
+      }
+      __syncthreads();
+      for (int64_t j = tid; j < m; j += PT_THREADS) {
+        key[s0 + j] = stage[j];
+        val[s0 + j] = stage[PT_SMAX + j];
+      }
+    } else {
+      for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) {
+        const uint64_t k = key[i];
+        const uint64_t c = k - lo;
+        if (c >= span) continue;
+        const uint32_t rank = pre[c >> 6] + (uint32_t)__popcll(bits[c >> 6] & ((1ull << (c & 63)) - 1ull));
+        key2[s0 + rank] = k;
+        val2[s0 + rank] = val[i];
+      }
+      __syncthreads();   // this CTA's writes to (key2, val2) are visible to it
+      for (int64_t j = s0 + tid; j < s1; j += PT_THREADS) {
+        key[j] = key2[j];
+        val[j] = val2[j];
+      }
+    }
+    __syncthreads();   // bits, pre and stage are reused by the next bucket
+  }
+}
+
+static cudaError_t order_by_partition(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
+                                      const PtPlan& pl, int64_t* bins, cudaStream_t s) {
+  const int nsup = (int)pl.nsup;
+  int64_t* soff = bins;                                                   // [nsup + 1]
+  unsigned long long* scur = (unsigned long long*)(bins + nsup + 1);      // [nsup], then the ticket
+  int64_t* foff = bins + 2 * (nsup + 1);                                  // [nfb + 1]
+  int64_t* scan = foff + pl.nfb + 1;
+  cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(int64_t) * 2 * (nsup + 1), s);
+  if (e != cudaSuccess) return e;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (n + 4 * PT_TILE - 1) / (4 * PT_TILE);   // slices of at least four tiles
+  if (grid > sms) grid = sms;                              // one CTA per SM (128 KB of staging each)
+  if (grid < 1) grid = 1;
+  const size_t csm = (size_t)nsup * 4;
+  const size_t ssm = (size_t)16 * PT_TILE + (size_t)nsup * 20;
+  const size_t fsm = (size_t)16 * PT_TILE;
+  const size_t rsm = (size_t)16 * PT_SMAX + ((size_t)1 << (pl.F - 6)) * 12;
+  if ((e = raise_smem_limit((const void*)k_pt_count, csm)) != cudaSuccess ||
+      (e = raise_smem_limit((const void*)k_pt_super, ssm)) != cudaSuccess ||
+      (e = raise_smem_limit((const void*)k_pt_fine, fsm)) != cudaSuccess ||
+      (e = raise_smem_limit((const void*)k_pt_rank, rsm)) != cudaSuccess)
+    return e;
+  k_pt_count<<<(unsigned)grid, PT_THREADS, csm, s>>>(key, n, pl.F, nsup, (unsigned long long*)soff);
+  if ((e = launch_scan_exclusive(soff, nsup, soff + nsup, scan, s)) != cudaSuccess) return e;
+  k_pt_super<<<(unsigned)grid, PT_THREADS, ssm, s>>>(key, val, n, pl.F, nsup, soff, scur, key2, val2);
+  k_pt_fine<<<(unsigned)nsup, PT_THREADS, fsm, s>>>(key2, val2, n, pl.F, pl.nfb, soff, foff, key, val);
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pt_rank, PT_THREADS, rsm) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  k_pt_rank<<<(unsigned)(sms * per), PT_THREADS, rsm, s>>>(key, val, pl.F, pl.nfb, foff, scur + nsup, key2,
+                                                         val2);
+  return cudaGetLastError();
 }
 
 // Counting and scatter by bucket, each CTA over one contiguous slice of the
@@ -141,11 +479,6 @@ int64_t order_buckets_scratch(int64_t krange) {
 constexpr int BK_CTA_THREADS = 512;
 constexpr int BK_MAX_SMEM_BUCKETS = 8192;   // histogram in shared memory up to this many buckets
 
-__device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
-  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  *a = min(n, (int64_t)blockIdx.x * per);
-  *b = min(n, *a + per);
-}
 
 __global__ void __launch_bounds__(BK_CTA_THREADS) k_bk_count(const uint64_t* __restrict__ key, int64_t n,
                                                              int64_t nb, unsigned long long* __restrict__ cnt) {
@@ -277,6 +610,10 @@ __global__ void __launch_bounds__(BK_THREADS) k_bk_rank(const uint64_t* __restri
 cudaError_t order_by_buckets(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t* val2, int64_t n,
                              int64_t krange, int64_t* bins, cudaStream_t s) {
   if (n <= 1) return cudaSuccess;
+#if KR_ORDER_PARTITION
+  const PtPlan pl = pt_plan(n, krange);
+  if (pl.ok) return order_by_partition(key, val, key2, val2, n, pl, bins, s);
+#endif
   const int64_t nb = order_buckets(krange);
   int64_t* off = bins;                                               // [nb + 1]
   unsigned long long* cur = (unsigned long long*)(bins + nb + 1);    // [nb + 1]
