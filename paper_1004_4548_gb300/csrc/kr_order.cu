@@ -154,9 +154,12 @@ __device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
 #ifndef KR_ORDER_PARTITION
 #define KR_ORDER_PARTITION 1
 #endif
-constexpr int PT_THREADS = 512;
+#ifndef KR_PT_THREADS
+#define KR_PT_THREADS 1024
+#endif
+constexpr int PT_THREADS = KR_PT_THREADS;
 constexpr int PT_TILE = 8192;                   // terms per tile: 128 KB of (key, val) in shared memory
-constexpr int PT_PER = PT_TILE / PT_THREADS;    // 16 terms per thread
+constexpr int PT_PER = PT_TILE / PT_THREADS;    // terms per thread and tile
 constexpr int PT_FINE_LOG2 = 8;                 // fine buckets per super-bucket: 256
 constexpr int PT_FINE = 1 << PT_FINE_LOG2;
 constexpr int64_t PT_MAX_SUPERS = 2048;
@@ -192,11 +195,12 @@ int64_t order_buckets_scratch(int64_t krange, int64_t n_max) {
   return need;
 }
 
-// Exclusive scan of cnt[0, m) into ofs[0, m) by the whole CTA (m <= 4 * PT_THREADS);
-// wsum: PT_THREADS / 32 words of scratch.
+// Exclusive scan of cnt[0, m) into ofs[0, m) by the whole CTA of NT threads;
+// wsum: NT / 32 words of scratch.
+template <int NT = PT_THREADS>
 __device__ __forceinline__ void pt_scan(const uint32_t* cnt, uint32_t* ofs, int m, uint32_t* wsum) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (m + PT_THREADS - 1) / PT_THREADS;   // consecutive entries per thread
+  const int per = (m + NT - 1) / NT;   // consecutive entries per thread
   const int a = min(m, tid * per), b = min(m, a + per);
   uint32_t t = 0;
   for (int i = a; i < b; ++i) t += cnt[i];
@@ -209,13 +213,13 @@ __device__ __forceinline__ void pt_scan(const uint32_t* cnt, uint32_t* ofs, int 
   if (lane == 31) wsum[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    uint32_t v = lane < PT_THREADS / 32 ? wsum[lane] : 0u;
+    uint32_t v = lane < NT / 32 ? wsum[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += y;
     }
-    if (lane < PT_THREADS / 32) wsum[lane] = v;
+    if (lane < NT / 32) wsum[lane] = v;
   }
   __syncthreads();
   uint32_t run = (warp > 0 ? wsum[warp - 1] : 0u) + x - t;
@@ -226,6 +230,8 @@ __device__ __forceinline__ void pt_scan(const uint32_t* cnt, uint32_t* ofs, int 
   }
   __syncthreads();
 }
+
+constexpr int PR_THREADS = 512;   // the ranking pass: several CTAs per SM
 
 // Tile scatter shared by passes 1 and 2: the terms [t0, t1) (at most PT_TILE)
 // of (key, val) go to (okey, oval) grouped by digit dig(key) in [0, m): the
@@ -240,17 +246,22 @@ __device__ __forceinline__ void pt_tile(const uint64_t* __restrict__ key, const 
   const int tid = threadIdx.x;
   for (int d = tid; d < m; d += PT_THREADS) tcnt[d] = 0;
   __syncthreads();
-  uint64_t k[PT_PER];
+  uint64_t k[PT_PER], v[PT_PER];
   uint32_t r[PT_PER];
+#pragma unroll
+  for (int q = 0; q < PT_PER; ++q) {   // every load of the tile issued before any is used
+    const int64_t i = t0 + (int64_t)q * PT_THREADS + tid;
+    k[q] = 0;
+    v[q] = 0;
+    if (i < t1) {
+      k[q] = key[i];
+      v[q] = val[i];
+    }
+  }
 #pragma unroll
   for (int q = 0; q < PT_PER; ++q) {
     const int64_t i = t0 + (int64_t)q * PT_THREADS + tid;
-    k[q] = 0;
-    r[q] = 0;
-    if (i < t1) {
-      k[q] = key[i];
-      r[q] = atomicAdd(&tcnt[dig(k[q])], 1u);
-    }
+    r[q] = i < t1 ? atomicAdd(&tcnt[dig(k[q])], 1u) : 0u;
   }
   __syncthreads();
   pt_scan(tcnt, tofs, m, wsum);
@@ -260,7 +271,7 @@ __device__ __forceinline__ void pt_tile(const uint64_t* __restrict__ key, const 
     if (i < t1) {
       const uint32_t pos = tofs[dig(k[q])] + r[q];
       stage[pos] = k[q];
-      stage[PT_TILE + pos] = val[i];
+      stage[PT_TILE + pos] = v[q];
     }
   }
   __syncthreads();
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_fine(const uint64_t* __restri
 
 // Pass 3: fine buckets in ticket order; bucket b holds the terms
 // [foff[b], foff[b+1]) of (key, val), codes in [b << F, (b + 1) << F).
-__global__ void __launch_bounds__(PT_THREADS) k_pt_rank(uint64_t* __restrict__ key, uint64_t* __restrict__ val,
+__global__ void __launch_bounds__(PR_THREADS) k_pt_rank(uint64_t* __restrict__ key, uint64_t* __restrict__ val,
                                                        int F, int64_t nfb, const int64_t* __restrict__ foff,
                                                        unsigned long long* __restrict__ ticket,
                                                        uint64_t* __restrict__ key2, uint64_t* __restrict__ val2) {
@@ -375,7 +386,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_rank(uint64_t* __restrict__ k
   unsigned long long* bits = (unsigned long long*)(pt_smem + 16 * PT_SMAX);   // [2^(F-6)]
   const int nw = 1 << (F - 6);
   uint32_t* pre = (uint32_t*)(bits + nw);                                     // [2^(F-6)]
-  __shared__ uint32_t wsum[PT_THREADS / 32];
+  __shared__ uint32_t wsum[PR_THREADS / 32];
   __shared__ int64_t s_b;
   const int tid = threadIdx.x;
   for (;;) {
@@ -387,21 +398,21 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_rank(uint64_t* __restrict__ k
     const int64_t s0 = foff[b], s1 = foff[b + 1];
     const int64_t m = s1 - s0;
     if (m < 2) continue;   // uniform across the CTA
-    for (int w = tid; w < nw; w += PT_THREADS) bits[w] = 0ull;
+    for (int w = tid; w < nw; w += PR_THREADS) bits[w] = 0ull;
     __syncthreads();
     const uint64_t lo = (uint64_t)b << F;
     const uint64_t span = uint64_t(1) << F;
-    for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) {
+    for (int64_t i = s0 + tid; i < s1; i += PR_THREADS) {
       const uint64_t c = key[i] - lo;   // < 2^F for the bucket's keys
       if (c < span) atomicOr(&bits[c >> 6], 1ull << (c & 63));
     }
     __syncthreads();
-    // word prefix counts (nw <= 2048: at most 4 words per thread)
-    for (int w = tid; w < nw; w += PT_THREADS) pre[w] = (uint32_t)__popcll(bits[w]);
+    // word prefix counts (nw <= 2048 words)
+    for (int w = tid; w < nw; w += PR_THREADS) pre[w] = (uint32_t)__popcll(bits[w]);
     __syncthreads();
-    pt_scan(pre, pre, nw, wsum);   // in place: each thread reads its entries before writing them
+    pt_scan<PR_THREADS>(pre, pre, nw, wsum);   // in place: each thread reads its entries before writing them
     if (m <= PT_SMAX) {
-      for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) {
+      for (int64_t i = s0 + tid; i < s1; i += PR_THREADS) {
         const uint64_t k = key[i];
         const uint64_t c = k - lo;
         if (c >= span) continue;
@@ -410,12 +421,12 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_rank(uint64_t* __restrict__ k
         stage[PT_SMAX + rank] = val[i];
       }
       __syncthreads();
-      for (int64_t j = tid; j < m; j += PT_THREADS) {
+      for (int64_t j = tid; j < m; j += PR_THREADS) {
         key[s0 + j] = stage[j];
         val[s0 + j] = stage[PT_SMAX + j];
       }
     } else {
-      for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) {
+      for (int64_t i = s0 + tid; i < s1; i += PR_THREADS) {
         const uint64_t k = key[i];
         const uint64_t c = k - lo;
         if (c >= span) continue;
@@ -424,7 +435,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_rank(uint64_t* __restrict__ k
         val2[s0 + rank] = val[i];
       }
       __syncthreads();   // this CTA's writes to (key2, val2) are visible to it
-      for (int64_t j = s0 + tid; j < s1; j += PT_THREADS) {
+      for (int64_t j = s0 + tid; j < s1; j += PR_THREADS) {
         key[j] = key2[j];
         val[j] = val2[j];
       }
@@ -462,11 +473,11 @@ static cudaError_t order_by_partition(uint64_t* key, uint64_t* val, uint64_t* ke
   k_pt_super<<<(unsigned)grid, PT_THREADS, ssm, s>>>(key, val, n, pl.F, nsup, soff, scur, key2, val2);
   k_pt_fine<<<(unsigned)nsup, PT_THREADS, fsm, s>>>(key2, val2, n, pl.F, pl.nfb, soff, foff, key, val);
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pt_rank, PT_THREADS, rsm) != cudaSuccess || per < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pt_rank, PR_THREADS, rsm) != cudaSuccess || per < 1) {
     cudaGetLastError();
     per = 1;
   }
-  k_pt_rank<<<(unsigned)(sms * per), PT_THREADS, rsm, s>>>(key, val, pl.F, pl.nfb, foff, scur + nsup, key2,
+  k_pt_rank<<<(unsigned)(sms * per), PR_THREADS, rsm, s>>>(key, val, pl.F, pl.nfb, foff, scur + nsup, key2,
                                                          val2);
   return cudaGetLastError();
 }
