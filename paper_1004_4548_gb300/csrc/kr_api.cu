@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <chrono>
@@ -42,6 +43,8 @@ struct kr_ctx {
   // host depends on them (no hash table to size or regrow); its term count
   // then stays on the device until the decode (ProdResult::n = -1)
   bool allow_deferred = false;
+  // pointer attributes queried during the current call's staging
+  std::unordered_map<const void*, cudaPointerAttributes> attr_memo;
   // a deferred dense polynomial product whose caller's outputs are all in
   // device memory or pinned host memory: the compaction decodes its terms
   // there (direct_done), and the output step only reads the count
@@ -261,11 +264,18 @@ struct JobIn {
 template <typename T>
 const T* stage(kr_ctx* ctx, Bump& b, const T* src, int64_t count, cudaStream_t s) {
   if (!src || count <= 0) return src;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, src) != cudaSuccess) {
-    cudaGetLastError();
-    a.type = cudaMemoryTypeUnregistered;
+  // one query per pointer and call (the layout passes stage every input twice)
+  auto it = ctx->attr_memo.find((const void*)src);
+  if (it == ctx->attr_memo.end()) {
+    cudaPointerAttributes q;
+    if (cudaPointerGetAttributes(&q, src) != cudaSuccess) {
+      cudaGetLastError();
+      q.type = cudaMemoryTypeUnregistered;
+      q.devicePointer = nullptr;
+    }
+    it = ctx->attr_memo.emplace((const void*)src, q).first;
   }
+  const cudaPointerAttributes& a = it->second;
   if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return src;
   // a small operand in pinned host memory is read by the kernels through its
   // device mapping (across the host link), with no staging copy
@@ -285,6 +295,7 @@ const T* stage(kr_ctx* ctx, Bump& b, const T* src, int64_t count, cudaStream_t s
 // A product whose table fills up is retried from B2 with a larger table.
 void run_pipeline(kr_ctx* ctx, const std::vector<JobIn>& ins, cudaStream_t s,
                   std::vector<ProdResult>& res) {
+  ctx->attr_memo.clear();
   const int nprod = (int)ins.size();
   res.assign(nprod, ProdResult());
   const int nops = 2 * nprod;

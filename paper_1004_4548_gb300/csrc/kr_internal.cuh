@@ -492,7 +492,7 @@ cudaError_t order_by_bins(uint64_t* key, uint64_t* val, uint64_t* key2, uint64_t
 // Large outputs over code ranges whose one-bit-per-code bitmap would not stay
 // in L2 (above 2^30 codes, 128 MB): terms partitioned by the high digits of
 // their code in two tile-sorted passes into buckets of about 2048 terms, each
-// then ranked by a shared-memory bitmap (or, past 2^36 codes, bucketed by
+// then ranked by a shared-memory bitmap (or, past 2^37 codes, bucketed by
 // 2^20 codes and ranked there); sorted in place (key2/val2: n terms of
 // scratch; bins: order_buckets_scratch(krange, n_max) int64 for up to n_max terms).
 constexpr int64_t ORDER_BUCKET_MIN_N = int64_t(1) << 20;

@@ -142,9 +142,9 @@ __device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
 // (2^F consecutive codes, F chosen for about 2048 terms a bucket) in two
 // passes, each pass sorting a tile of PT_TILE terms by digit in shared memory
 // so that the tile goes out as one contiguous run per digit:
-//   1. super-buckets of 256 fine buckets: the counts, then a scatter of every
+//   1. super-buckets of 512 fine buckets: the counts, then a scatter of every
 //      CTA's slice in tiles to its reserved range of each super-bucket;
-//   2. one CTA per super-bucket: its 256 fine counts and offsets, then the
+//   2. one CTA per super-bucket: its 512 fine counts and offsets, then the
 //      same tile scatter by fine bucket (back into the first arrays);
 //   3. each fine bucket ranked by a bitmap of its 2^F codes in shared memory
 //      and written back in order from a shared-memory copy (a bucket above
@@ -160,7 +160,7 @@ __device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
 constexpr int PT_THREADS = KR_PT_THREADS;
 constexpr int PT_TILE = 8192;                   // terms per tile: 128 KB of (key, val) in shared memory
 constexpr int PT_PER = PT_TILE / PT_THREADS;    // terms per thread and tile
-constexpr int PT_FINE_LOG2 = 8;                 // fine buckets per super-bucket: 256
+constexpr int PT_FINE_LOG2 = 9;                 // fine buckets per super-bucket: 512
 constexpr int PT_FINE = 1 << PT_FINE_LOG2;
 constexpr int64_t PT_MAX_SUPERS = 2048;
 constexpr int PT_F_MIN = 10, PT_F_MAX = 17;     // fine buckets of 2^F codes: bitmaps of at most 16 KB
