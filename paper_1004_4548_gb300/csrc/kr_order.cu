@@ -142,9 +142,10 @@ __device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
 // (2^F consecutive codes, F chosen for about 2048 terms a bucket) in two
 // passes, each pass sorting a tile of PT_TILE terms by digit in shared memory
 // so that the tile goes out as one contiguous run per digit:
-//   1. super-buckets of 512 fine buckets: the counts, then a scatter of every
+//   1. super-buckets of 2^fbits fine buckets (512, or fewer when that leaves
+//      under 256 super-buckets): the counts, then a scatter of every
 //      CTA's slice in tiles to its reserved range of each super-bucket;
-//   2. one CTA per super-bucket: its 512 fine counts and offsets, then the
+//   2. one CTA per super-bucket: its fine counts and offsets, then the
 //      same tile scatter by fine bucket (back into the first arrays);
 //   3. each fine bucket ranked by a bitmap of its 2^F codes in shared memory
 //      and written back in order from a shared-memory copy (a bucket above
@@ -160,14 +161,17 @@ __device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
 constexpr int PT_THREADS = KR_PT_THREADS;
 constexpr int PT_TILE = 8192;                   // terms per tile: 128 KB of (key, val) in shared memory
 constexpr int PT_PER = PT_TILE / PT_THREADS;    // terms per thread and tile
-constexpr int PT_FINE_LOG2 = 9;                 // fine buckets per super-bucket: 512
-constexpr int PT_FINE = 1 << PT_FINE_LOG2;
+constexpr int PT_FINE_LOG2 = 9;                 // fine buckets per super-bucket: at most 512,
+constexpr int PT_FINE = 1 << PT_FINE_LOG2;      // fewer when that leaves under PT_MIN_SUPERS
+constexpr int PT_FINE_LOG2_MIN = 4;
+constexpr int64_t PT_MIN_SUPERS = 256;          // CTAs of the fine pass
 constexpr int64_t PT_MAX_SUPERS = 2048;
 constexpr int PT_F_MIN = 10, PT_F_MAX = 17;     // fine buckets of 2^F codes: bitmaps of at most 16 KB
 constexpr int PT_SMAX = 4096;                   // a fine bucket is sorted in shared memory up to this
 
 struct PtPlan {
   int F = 0;
+  int fbits = PT_FINE_LOG2;   // fine buckets per super-bucket: 2^fbits
   int64_t nfb = 0, nsup = 0;
   bool ok = false;
 };
@@ -180,7 +184,12 @@ static PtPlan pt_plan(int64_t n, int64_t krange) {
   if (F < PT_F_MIN) F = PT_F_MIN;
   pl.F = F;
   pl.nfb = (krange + (int64_t(1) << F) - 1) >> F;
-  pl.nsup = (pl.nfb + PT_FINE - 1) >> PT_FINE_LOG2;
+  // narrower fine digits for outputs of few fine buckets, so that the fine
+  // pass (one CTA per super-bucket) still spreads over the GPU
+  int fb = PT_FINE_LOG2;
+  while (fb > PT_FINE_LOG2_MIN && ((pl.nfb + (int64_t(1) << fb) - 1) >> fb) < PT_MIN_SUPERS) --fb;
+  pl.fbits = fb;
+  pl.nsup = (pl.nfb + (int64_t(1) << fb) - 1) >> fb;
   pl.ok = pl.nsup <= PT_MAX_SUPERS;
   return pl;
 }
@@ -190,8 +199,10 @@ int64_t order_buckets_scratch(int64_t krange, int64_t n_max) {
   int64_t need = 3 * (nb + 1) + scan_scratch_entries(nb);
   // partition ordering for any count up to n_max: fewer terms make larger
   // fine buckets, so n_max gives the most of them
+  // (the super-bucket count depends on the count too: room for the most)
   const PtPlan pl = pt_plan(n_max, krange);
-  if (pl.ok) need = std::max(need, 2 * (pl.nsup + 1) + (pl.nfb + 1) + scan_scratch_entries(pl.nsup));
+  if (pl.ok)
+    need = std::max(need, 2 * (PT_MAX_SUPERS + 1) + (pl.nfb + 1) + scan_scratch_entries(PT_MAX_SUPERS));
   return need;
 }
 
@@ -296,14 +307,14 @@ __device__ __forceinline__ int pt_sup(uint64_t k, int sh, int nsup) {
 }
 
 // Pass 1 counts: super-bucket histograms of every CTA's slice.
-__global__ void __launch_bounds__(PT_THREADS) k_pt_count(const uint64_t* __restrict__ key, int64_t n, int F,
+__global__ void __launch_bounds__(PT_THREADS) k_pt_count(const uint64_t* __restrict__ key, int64_t n, int sh,
                                                         int nsup, unsigned long long* __restrict__ cnt) {
   extern __shared__ uint32_t ph[];
   for (int d = threadIdx.x; d < nsup; d += blockDim.x) ph[d] = 0;
   __syncthreads();
   int64_t a, e;
   bk_slice(n, &a, &e);
-  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) atomicAdd(&ph[pt_sup(key[i], F + PT_FINE_LOG2, nsup)], 1u);
+  for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) atomicAdd(&ph[pt_sup(key[i], sh, nsup)], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < nsup; d += blockDim.x)
     if (ph[d]) atomicAdd(&cnt[d], (unsigned long long)ph[d]);
@@ -312,7 +323,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_count(const uint64_t* __restr
 // Pass 1: each CTA reserves its slice's share of every super-bucket, then
 // scatters the slice tile by tile into (key2, val2).
 __global__ void __launch_bounds__(PT_THREADS) k_pt_super(const uint64_t* __restrict__ key,
-                                                        const uint64_t* __restrict__ val, int64_t n, int F,
+                                                        const uint64_t* __restrict__ val, int64_t n, int sh,
                                                         int nsup, const int64_t* __restrict__ soff,
                                                         unsigned long long* __restrict__ scur,
                                                         uint64_t* __restrict__ key2, uint64_t* __restrict__ val2) {
@@ -324,7 +335,6 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_super(const uint64_t* __restr
   uint32_t* tofs = tcnt + nsup;                                         // [nsup]
   __shared__ uint32_t wsum[PT_THREADS / 32];
   const int tid = threadIdx.x;
-  const int sh = F + PT_FINE_LOG2;
   int64_t a, e;
   bk_slice(n, &a, &e);
   for (int d = tid; d < nsup; d += PT_THREADS) tcnt[d] = 0;
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_super(const uint64_t* __restr
 // (key2, val2) back into (key, val).
 __global__ void __launch_bounds__(PT_THREADS) k_pt_fine(const uint64_t* __restrict__ key2,
                                                        const uint64_t* __restrict__ val2, int64_t n, int F,
-                                                       int64_t nfb, const int64_t* __restrict__ soff,
+                                                       int fbits, int64_t nfb, const int64_t* __restrict__ soff,
                                                        int64_t* __restrict__ foff, uint64_t* __restrict__ key,
                                                        uint64_t* __restrict__ val) {
   extern __shared__ __align__(16) unsigned char pt_smem[];
@@ -355,24 +365,25 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt_fine(const uint64_t* __restri
   __shared__ uint32_t cur[PT_FINE], tcnt[PT_FINE], tofs[PT_FINE];
   __shared__ uint32_t wsum[PT_THREADS / 32];
   const int tid = threadIdx.x;
+  const int nfine = 1 << fbits;   // at most PT_FINE
   const int64_t d = blockIdx.x;
   const int64_t s0 = soff[d], s1 = soff[d + 1];
-  for (int f = tid; f < PT_FINE; f += PT_THREADS) tcnt[f] = 0;
+  for (int f = tid; f < nfine; f += PT_THREADS) tcnt[f] = 0;
   __syncthreads();
-  for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) atomicAdd(&tcnt[(key2[i] >> F) & (PT_FINE - 1)], 1u);
+  for (int64_t i = s0 + tid; i < s1; i += PT_THREADS) atomicAdd(&tcnt[(key2[i] >> F) & (nfine - 1)], 1u);
   __syncthreads();
-  pt_scan(tcnt, tofs, PT_FINE, wsum);
-  for (int f = tid; f < PT_FINE; f += PT_THREADS) {
+  pt_scan(tcnt, tofs, nfine, wsum);
+  for (int f = tid; f < nfine; f += PT_THREADS) {
     base[f] = s0 + tofs[f];
     cur[f] = 0;
-    const int64_t fb = d * PT_FINE + f;
+    const int64_t fb = d * nfine + f;
     if (fb < nfb) foff[fb] = s0 + tofs[f];
   }
   if (d == gridDim.x - 1 && tid == 0) foff[nfb] = n;
   __syncthreads();
-  auto dig = [F](uint64_t k) -> int { return (int)((k >> F) & (PT_FINE - 1)); };
+  auto dig = [F, nfine](uint64_t k) -> int { return (int)((k >> F) & (nfine - 1)); };
   for (int64_t t0 = s0; t0 < s1; t0 += PT_TILE)
-    pt_tile(key2, val2, t0, min(s1, t0 + PT_TILE), PT_FINE, dig, base, cur, tcnt, tofs, stage, wsum, key, val);
+    pt_tile(key2, val2, t0, min(s1, t0 + PT_TILE), nfine, dig, base, cur, tcnt, tofs, stage, wsum, key, val);
 }
 
 // Pass 3: fine buckets in ticket order; bucket b holds the terms
@@ -468,10 +479,11 @@ static cudaError_t order_by_partition(uint64_t* key, uint64_t* val, uint64_t* ke
       (e = raise_smem_limit((const void*)k_pt_fine, fsm)) != cudaSuccess ||
       (e = raise_smem_limit((const void*)k_pt_rank, rsm)) != cudaSuccess)
     return e;
-  k_pt_count<<<(unsigned)grid, PT_THREADS, csm, s>>>(key, n, pl.F, nsup, (unsigned long long*)soff);
+  const int sh = pl.F + pl.fbits;   // a key's super-bucket: key >> sh
+  k_pt_count<<<(unsigned)grid, PT_THREADS, csm, s>>>(key, n, sh, nsup, (unsigned long long*)soff);
   if ((e = launch_scan_exclusive(soff, nsup, soff + nsup, scan, s)) != cudaSuccess) return e;
-  k_pt_super<<<(unsigned)grid, PT_THREADS, ssm, s>>>(key, val, n, pl.F, nsup, soff, scur, key2, val2);
-  k_pt_fine<<<(unsigned)nsup, PT_THREADS, fsm, s>>>(key2, val2, n, pl.F, pl.nfb, soff, foff, key, val);
+  k_pt_super<<<(unsigned)grid, PT_THREADS, ssm, s>>>(key, val, n, sh, nsup, soff, scur, key2, val2);
+  k_pt_fine<<<(unsigned)nsup, PT_THREADS, fsm, s>>>(key2, val2, n, pl.F, pl.fbits, pl.nfb, soff, foff, key, val);
   int per = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pt_rank, PR_THREADS, rsm) != cudaSuccess || per < 1) {
     cudaGetLastError();
