@@ -102,3 +102,30 @@ def test_outputs(env, kind, codes, short):
             mult *= int(fw[k])
         assert np.array_equal(c, cd)
         assert (lo >= flo).all() and (w <= fw).all()
+
+
+@pytest.mark.parametrize("kind", ["cuda", "pinned", "pageable"])
+def test_poisson_operands_in_each_memory(env, kind):
+    """A Poisson product whose operands (exponents, multipliers, kinds,
+    coefficients) are device arrays, pinned host arrays read in place, or
+    pageable host arrays staged by copies; outputs in device memory."""
+    import torch
+    from gpu_compare import assert_pseries_close
+    from workloads import PSeries, random_pseries
+    k = env[0]
+    f = random_pseries(2, 3, 700, 3, 4, 8201)
+    g = random_pseries(2, 3, 900, 3, 4, 8202)
+    r = oracle.poisson_mul(f, g, nthreads=8, keep_zero=True)
+
+    def put(p):
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)) for a in (p.exps, p.trig, p.kind, p.coef)]
+        if kind == "cuda":
+            arrs = [a.cuda() for a in arrs]
+        elif kind == "pinned":
+            arrs = [a.pin_memory() for a in arrs]
+        return PSeries(*arrs)
+
+    out = k.poisson_mul(put(f), put(g))
+    torch.cuda.synchronize()
+    got = tuple(a.cpu().numpy() for a in out[:4])
+    assert_pseries_close(got, r, 1e-12, f"poisson operands {kind}")
