@@ -197,12 +197,13 @@ static PtPlan pt_plan(int64_t n, int64_t krange) {
 int64_t order_buckets_scratch(int64_t krange, int64_t n_max) {
   const int64_t nb = order_buckets(krange);
   int64_t need = 3 * (nb + 1) + scan_scratch_entries(nb);
-  // partition ordering for any count up to n_max: fewer terms make larger
-  // fine buckets, so n_max gives the most of them
-  // (the super-bucket count depends on the count too: room for the most)
-  const PtPlan pl = pt_plan(n_max, krange);
-  if (pl.ok)
-    need = std::max(need, 2 * (PT_MAX_SUPERS + 1) + (pl.nfb + 1) + scan_scratch_entries(PT_MAX_SUPERS));
+  // partition ordering for any count n <= n_max that the plan accepts: fewer
+  // terms make larger fine buckets, so n_max gives the most of them, and an
+  // accepted plan has at most PT_MAX_SUPERS super-buckets of at most PT_FINE
+  // fine buckets (whether or not n_max's own plan is accepted)
+  const PtPlan pl = pt_plan(std::max<int64_t>(n_max, 2), krange);
+  const int64_t nfb = std::min<int64_t>(pl.nfb, PT_MAX_SUPERS * PT_FINE);
+  need = std::max(need, 2 * (PT_MAX_SUPERS + 1) + (nfb + 1) + scan_scratch_entries(PT_MAX_SUPERS));
   return need;
 }
 
