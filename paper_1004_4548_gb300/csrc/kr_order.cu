@@ -149,7 +149,9 @@ __device__ __forceinline__ void bk_slice(int64_t n, int64_t* a, int64_t* b) {
 //      same tile scatter by fine bucket (back into the first arrays);
 //   3. each fine bucket ranked by a bitmap of its 2^F codes in shared memory
 //      and written back in order from a shared-memory copy (a bucket above
-//      PT_SMAX terms is ranked into the second arrays and copied back).
+//      PT_SMAX terms is ranked into the second arrays and copied back; one
+//      of at most PT_CMP_MAX terms is ranked by comparisons instead, whose
+//      cost follows its terms rather than its codes).
 // The result is in place.
 // ---------------------------------------------------------------------------
 #ifndef KR_ORDER_PARTITION
@@ -168,6 +170,7 @@ constexpr int64_t PT_MIN_SUPERS = 256;          // CTAs of the fine pass
 constexpr int64_t PT_MAX_SUPERS = 2048;
 constexpr int PT_F_MIN = 10, PT_F_MAX = 17;     // fine buckets of 2^F codes: bitmaps of at most 16 KB
 constexpr int PT_SMAX = 4096;                   // a fine bucket is sorted in shared memory up to this
+constexpr int PT_CMP_MAX = 256;                 // and ranked by comparisons, not a bitmap, up to this
 
 struct PtPlan {
   int F = 0;
@@ -410,6 +413,24 @@ __global__ void __launch_bounds__(PR_THREADS) k_pt_rank(uint64_t* __restrict__ k
     const int64_t s0 = foff[b], s1 = foff[b + 1];
     const int64_t m = s1 - s0;
     if (m < 2) continue;   // uniform across the CTA
+    if (m <= PT_CMP_MAX) {
+      // a small bucket: ranks by comparison (each term's rank is the number of
+      // the bucket's keys below it; keys are distinct), from a shared copy
+      for (int64_t j = tid; j < m; j += PR_THREADS) {
+        stage[j] = key[s0 + j];
+        stage[PT_SMAX + j] = val[s0 + j];
+      }
+      __syncthreads();
+      for (int64_t j = tid; j < m; j += PR_THREADS) {
+        const uint64_t k = stage[j];
+        int64_t rank = 0;
+        for (int64_t u = 0; u < m; ++u) rank += stage[u] < k ? 1 : 0;
+        key[s0 + rank] = k;
+        val[s0 + rank] = stage[PT_SMAX + j];
+      }
+      __syncthreads();   // stage is reused by the next bucket
+      continue;
+    }
     for (int w = tid; w < nw; w += PR_THREADS) bits[w] = 0ull;
     __syncthreads();
     const uint64_t lo = (uint64_t)b << F;
