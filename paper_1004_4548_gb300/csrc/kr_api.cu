@@ -117,12 +117,12 @@ kr_status from_cuda(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? KR_ERR_OOM : KR_ERR_CUDA;
 }
 
-// Bump allocation over a base pointer; base == nullptr measures only.
 // pinned host inputs of at most this many values are read in place
 #ifndef KR_ZERO_COPY_MAX
 #define KR_ZERO_COPY_MAX (int64_t(1) << 18)
 #endif
 
+// Bump allocation over a base pointer; base == nullptr measures only.
 struct Bump {
   char* base;
   size_t off = 0;
