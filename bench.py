@@ -246,8 +246,10 @@ def reference_arm(args):
             vals.append(cb["value"])
     v = statistics.median(vals)
     cb["value"] = v
+    # each step times a bounded sample; ms_per_step is the time the whole workload
+    # (all f x g term-products) takes at the measured rate
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f.n * g.n / (v * 1e6) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": cb,
