@@ -134,7 +134,11 @@ struct Result {
 KeyLess poly_order(int nv) {
   KeyLess L;
   L.len = nv;
+#if ORC_PLANT == 15
+  for (int t = 0; t < nv; ++t) L.order[t] = t;   // planted: variable 0 most significant
+#else
   for (int t = 0; t < nv; ++t) L.order[t] = nv - 1 - t;
+#endif
   return L;
 }
 
@@ -144,8 +148,13 @@ KeyLess poisson_order(int np, int nt) {
   L.len = 1 + nt + np;
   int t = 0;
   L.order[t++] = 0;
+#if ORC_PLANT == 17
+  for (int k = np - 1; k >= 0; --k) L.order[t++] = 1 + nt + k;   // planted: polynomial part before trig
+  for (int k = nt - 1; k >= 0; --k) L.order[t++] = 1 + k;
+#else
   for (int k = nt - 1; k >= 0; --k) L.order[t++] = 1 + k;
   for (int k = np - 1; k >= 0; --k) L.order[t++] = 1 + nt + k;
+#endif
   return L;
 }
 
@@ -285,7 +294,9 @@ Result* poly_mul(int nv, int64_t nf, const int32_t* ef, const void* cfv, int64_t
       __int128 v = (__int128)kv.second.s;
       if (v > (__int128)INT64_MAX || v < (__int128)INT64_MIN) R->overflow = 1;
       int64_t w = (int64_t)(uint64_t)kv.second.s;
-      if (w == 0 && !keep_zero) continue;
+#if ORC_PLANT != 16
+      if (w == 0 && !keep_zero) continue;   // (planted 16: zero sums kept)
+#endif
       R->keys.push_back(kv.first);
       R->ci.push_back(w);
     }
@@ -325,6 +336,9 @@ int canonicalise(Key& key, int nt) {
   if (last < 0) return key.c[0] == 1 ? 0 : 1;
   if (key.c[1 + last] > 0) return 1;
   for (int k = 0; k < nt; ++k) key.c[1 + k] = -key.c[1 + k];
+#if ORC_PLANT == 18
+  return 1;   // planted: a negated sine keeps its sign
+#endif
   return key.c[0] == 1 ? -1 : 1;
 }
 
@@ -380,6 +394,10 @@ void poisson_slice(int np, int nt, const PSIn& F, const PSIn& G, int64_t i0, int
 #endif
       for (int k = 0; k < np; ++k)
         key.c[1 + nt + k] = F.e[(int64_t)k * F.n + i] + G.e[(int64_t)k * G.n + j];
+#if ORC_PLANT == 19
+      for (int k = 0; k < np; ++k)   // planted: the difference term's polynomial exponents subtracted
+        key.c[1 + nt + k] = F.e[(int64_t)k * F.n + i] - G.e[(int64_t)k * G.n + j];
+#endif
       // difference term: trig(f) - trig(g)
       key.c[0] = kd;
       for (int k = 0; k < nt; ++k)

@@ -201,6 +201,85 @@ def pin_mod_p(plant=0):
     return errs
 
 
+def _table1_rows():
+    return [tuple(map(int, l.split())) for l in open(os.path.join(GOLDEN, "table1_codes.txt"))
+            if l.strip() and not l.startswith("#")]
+
+
+def _box(v, hi, shift, dt):
+    """Every monomial of the box [shift, shift + hi]^v, coefficient 1."""
+    e = np.array(np.meshgrid(*[np.arange(hi + 1)] * v, indexing="ij")).reshape(v, -1) + shift
+    return Poly(e.astype(np.int32), np.ones(e.shape[1], np.int64 if dt == "i64" else np.float64))
+
+
+def pin_order(plant=0):
+    """Output order (Sec. 2, Table 1): ascending Kronecker code, variable 0
+    varying fastest.  The product of the boxes [0, 1]^3 and [0, 2]^3 fills
+    [0, 3]^3 with positive coefficients, so its 64 terms must come out in the
+    order of Table 1's codes (c = (1, 4, 16)): Table 1's rows at their code's
+    position, and every term at position x + 4 y + 16 z; the same with the
+    box shifted to negative exponents, float64 coefficients and the f terms
+    split over three threads.  Poisson series: cosines before sines, then
+    the multiplier vectors and then the polynomial exponents, each compared
+    from the highest-index variable down (the ascending order of the coding
+    that puts the kind above the trig part above the polynomial part)."""
+    errs = []
+    rows = _table1_rows()
+    for shift, nth, dt in ((0, 1, "i64"), (-2, 3, "i64"), (-1, 3, "f64")):
+        f, g = _box(3, 1, shift, dt), _box(3, 2, 0, dt)
+        r = oracle.poly_mul(f, g, nthreads=nth, plant=plant)
+        if r.coef.shape[0] != 64:
+            errs.append(f"box product shift={shift}: {r.coef.shape[0]} terms, want 64")
+            continue
+        x, y, z = (r.exps.astype(np.int64) - shift)
+        if not np.array_equal(x + 4 * y + 16 * z, np.arange(64)):
+            errs.append(f"box product shift={shift} threads={nth} {dt}: not in Table 1's code order")
+        for zz, yy, xx, code in rows:
+            if (int(x[code]), int(y[code]), int(z[code])) != (xx, yy, zz):
+                errs.append(f"Table 1 row ({zz}, {yy}, {xx}) not at position {code} (shift={shift})")
+                break
+    for nth in (1, 3):
+        f = random_pseries(2, 3, 70, 2, 3, 2501)
+        g = random_pseries(2, 3, 75, 2, 3, 2502)
+        h = oracle.poisson_mul(f, g, nthreads=nth, plant=plant)
+        keys = [(int(h.kind[i]),) + tuple(int(t) for t in h.trig[::-1, i])
+                + tuple(int(e) for e in h.exps[::-1, i]) for i in range(h.coef.shape[0])]
+        if any(a >= b for a, b in zip(keys, keys[1:])):
+            errs.append(f"Poisson output not strictly ascending (kind, trig, poly) threads={nth}")
+    return errs
+
+
+def pin_cancellation(plant=0):
+    """Terms whose contributions cancel leave the output, worked by hand:
+    (x - y)(x + y) = x^2 - y^2, (x + 1/x)(x - 1/x) = x^2 - x^-2 (Laurent),
+    and 3 cos y (2 cos 3y - 2 cos y) = -3 + 3 cos 4y (Eq. 6 with the 1/2: the
+    two contributions to cos 2y cancel); kept as zeros only on request."""
+    errs = []
+    cases = [((np.array([[1, 0], [0, 1]]), [1, -1]), (np.array([[1, 0], [0, 1]]), [1, 1]),
+              {(2, 0): 1, (0, 2): -1}, {(1, 1): 0}),
+             ((np.array([[1, -1]]), [1, 1]), (np.array([[1, -1]]), [1, -1]),
+              {(2,): 1, (-2,): -1}, {(0,): 0})]
+    for (ef, cf), (eg, cg), want, zeros in cases:
+        for dt in ("i64", "f64"):
+            typ = np.int64 if dt == "i64" else np.float64
+            f = Poly(ef.astype(np.int32), np.array(cf, typ))
+            g = Poly(eg.astype(np.int32), np.array(cg, typ))
+            for keep in (False, True):
+                r = oracle.poly_mul(f, g, plant=plant, keep_zero=keep)
+                w = {**want, **zeros} if keep else want
+                if as_dict(r.exps, r.coef) != w:
+                    errs.append(f"cancellation {dt} keep_zero={keep}: {as_dict(r.exps, r.coef)}, want {w}")
+    f = PSeries(np.zeros((1, 2), np.int32), np.array([[3, 1]], np.int32), np.zeros(2, np.uint8),
+                np.array([2.0, -2.0]))
+    g = PSeries(np.zeros((1, 1), np.int32), np.array([[1]], np.int32), np.zeros(1, np.uint8),
+                np.array([3.0]))
+    r = oracle.poisson_mul(f, g, plant=plant)
+    got = {(int(r.trig[0, i]), int(r.kind[i])): float(r.coef[i]) for i in range(r.coef.shape[0])}
+    if got != {(0, 0): -3.0, (4, 0): 3.0}:
+        errs.append(f"cancelling Poisson product: {got}")
+    return errs
+
+
 # ---------------------------------------------------------------------------
 # the pins, run on the oracle
 # ---------------------------------------------------------------------------
@@ -236,6 +315,14 @@ def test_oracle_canonical_output():
 
 def test_oracle_mod_p_small():
     assert pin_mod_p() == []
+
+
+def test_oracle_output_order_table1():
+    assert pin_order() == []
+
+
+def test_oracle_cancellation():
+    assert pin_cancellation() == []
 
 
 def test_oracle_cfg1_bruteforce():
@@ -538,6 +625,11 @@ PLANTS = {
     12: "coefficient bound applied after the product-to-sum 1/2",
     13: "harmonic order bound applied as < N instead of <= N",
     14: "harmonic order counts every trig variable, ignoring the mask",
+    15: "polynomial output ordered with variable 0 most significant",
+    16: "zero int64 sums kept in the output",
+    17: "Poisson output ordered by the polynomial part before the trig part",
+    18: "a negated sine keeps its sign",
+    19: "the difference term's polynomial exponents subtracted",
 }
 
 
@@ -545,5 +637,6 @@ PLANTS = {
 def test_planted_mistake_is_caught(plant):
     caught = (pin_werner(plant) + pin_canonical(plant) + pin_random_angles(plant)
               + pin_bruteforce(plant) + pin_mod_p(plant) + pin_truncation(plant)
-              + pin_mass(plant) + pin_coef_truncation(plant) + pin_harmonic_truncation(plant))
+              + pin_mass(plant) + pin_coef_truncation(plant) + pin_harmonic_truncation(plant)
+              + pin_order(plant) + pin_cancellation(plant))
     assert caught, f"planted mistake {plant} ({PLANTS[plant]}) escaped every pin"
