@@ -107,7 +107,11 @@ struct AccF {
     mass = m + o.mass;
 #endif
   }
+#if ORC_PLANT == 20
+  double value() const { return s; }   // planted: the compensation dropped
+#else
   double value() const { return s + comp; }
+#endif
 };
 
 uint64_t fnv1a(const Key& k, int len) {

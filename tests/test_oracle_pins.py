@@ -280,6 +280,33 @@ def pin_cancellation(plant=0):
     return errs
 
 
+def pin_compensated(plant=0):
+    """float64 sums are compensated (Neumaier 1974), so a sum whose exact value
+    is a double comes out exact however its parts cancel: in
+    (1e16 + x - 1e16 x^2)(x^2 + x + 1) the x^2 coefficient gathers 1e16, 1 and
+    -1e16 (exactly 1; an uncompensated running sum gives 0 or 2, since 1e16 + 1
+    is not a double), on one thread and with the three f terms on three
+    threads (the partial sums then meet in the merge); likewise for a Poisson
+    series, where each contribution carries the 1/2 of Eq. 6."""
+    errs = []
+    f = Poly(np.array([[0, 1, 2]], np.int32), np.array([1e16, 1.0, -1e16]))
+    g = Poly(np.array([[2, 1, 0]], np.int32), np.array([1.0, 1.0, 1.0]))
+    for nth in (1, 3):
+        r = oracle.poly_mul(f, g, nthreads=nth, plant=plant)
+        got = as_dict(r.exps, r.coef)
+        if got.get((2,)) != 1.0:
+            errs.append(f"compensated sum threads={nth}: x^2 coefficient {got.get((2,))}, want 1.0")
+    z = lambda n: np.zeros((1, n), np.int32)
+    F = PSeries(np.array([[0, 1, 2]], np.int32), z(3), np.zeros(3, np.uint8), np.array([2e16, 2.0, -2e16]))
+    G = PSeries(np.array([[2, 1, 0]], np.int32), z(3), np.zeros(3, np.uint8), np.array([1.0, 1.0, 1.0]))
+    for nth in (1, 3):
+        r = oracle.poisson_mul(F, G, nthreads=nth, plant=plant)
+        got = {int(r.exps[0, i]): float(r.coef[i]) for i in range(r.coef.shape[0])}
+        if got.get(2) != 2.0:   # cos 0 cos 0 = 1/2 + 1/2: each pair gives C D in two halves
+            errs.append(f"compensated Poisson sum threads={nth}: x^2 coefficient {got.get(2)}, want 2.0")
+    return errs
+
+
 # ---------------------------------------------------------------------------
 # the pins, run on the oracle
 # ---------------------------------------------------------------------------
@@ -323,6 +350,10 @@ def test_oracle_output_order_table1():
 
 def test_oracle_cancellation():
     assert pin_cancellation() == []
+
+
+def test_oracle_compensated_sums():
+    assert pin_compensated() == []
 
 
 def test_oracle_cfg1_bruteforce():
@@ -630,6 +661,7 @@ PLANTS = {
     17: "Poisson output ordered by the polynomial part before the trig part",
     18: "a negated sine keeps its sign",
     19: "the difference term's polynomial exponents subtracted",
+    20: "the compensation dropped from the float64 sums",
 }
 
 
@@ -638,5 +670,5 @@ def test_planted_mistake_is_caught(plant):
     caught = (pin_werner(plant) + pin_canonical(plant) + pin_random_angles(plant)
               + pin_bruteforce(plant) + pin_mod_p(plant) + pin_truncation(plant)
               + pin_mass(plant) + pin_coef_truncation(plant) + pin_harmonic_truncation(plant)
-              + pin_order(plant) + pin_cancellation(plant))
+              + pin_order(plant) + pin_cancellation(plant) + pin_compensated(plant))
     assert caught, f"planted mistake {plant} ({PLANTS[plant]}) escaped every pin"
