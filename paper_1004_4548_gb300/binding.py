@@ -175,6 +175,27 @@ def _ptr_len(a, dtype):
     return arr.ctypes.data, arr
 
 
+def _out_ptr(out, shape, dtype):
+    """Pointer of a caller-supplied output array.  It must already have the
+    dtype, the shape and a contiguous layout: a converted copy would take the
+    result in its place and the caller's array would never see it."""
+    shape = tuple(int(x) for x in shape)
+    ok = False
+    try:
+        torch = _torch()
+        if isinstance(out, torch.Tensor):
+            tdt = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+            if out.dtype == tdt and out.is_contiguous() and tuple(out.shape) == shape:
+                return out.data_ptr()
+    except ImportError:
+        pass
+    if isinstance(out, np.ndarray):
+        ok = out.dtype == np.dtype(dtype) and out.flags.c_contiguous and out.shape == shape
+        if ok:
+            return out.ctypes.data
+    raise ValueError(f"out must be a contiguous {np.dtype(dtype).name} array of shape {shape}")
+
+
 def _stream_ptr(stream):
     if stream is None:
         torch = _torch()
@@ -321,7 +342,7 @@ def kron_encode(exps, emin, emax, ctx: Context | None = None, stream=None, out=N
     emax = np.ascontiguousarray(emax, dtype=np.int32)
     if out is None:
         out = _alloc((n,), np.int64, ctx.device, host=False)
-    po, ko = _ptr_len(out, np.int64)
+    po = _out_ptr(out, (n,), np.int64)
     st = ctx.L.kron_encode(ctx.h, pe, n, nv, emin.ctypes.data, emax.ctypes.data, po, _stream_ptr(stream))
     _check(ctx.L, ctx.h, st, "kron_encode")
     return out
@@ -336,7 +357,7 @@ def kron_decode(codes, emin, emax, ctx: Context | None = None, stream=None, out=
     pc, kc = _ptr_len(codes, np.int64)
     if out is None:
         out = _alloc((nv, n), np.int32, ctx.device, host=False)
-    po, ko = _ptr_len(out, np.int32)
+    po = _out_ptr(out, (nv, n), np.int32)
     st = ctx.L.kron_decode(ctx.h, pc, n, nv, emin.ctypes.data, emax.ctypes.data, po, _stream_ptr(stream))
     _check(ctx.L, ctx.h, st, "kron_decode")
     return out

@@ -124,3 +124,23 @@ def test_ctypes_structures_match_the_header(tmp_path):
         assert int(got[n]) == ctypes.sizeof(st), n
         for fname, _ in st._fields_:
             assert int(got[f"{n}.{fname}"]) == getattr(st, fname).offset, f"{n}.{fname}"
+
+
+def test_caller_outputs_are_used_as_given_or_rejected():
+    """A caller-supplied output of another dtype, shape or layout would be
+    replaced by a converted copy that alone receives the result: the binding
+    refuses it instead (no device call is made here)."""
+    import torch
+    good = np.zeros((3, 5), np.int32)
+    assert binding._out_ptr(good, (3, 5), np.int32) == good.ctypes.data
+    t = torch.zeros(7, dtype=torch.int64)
+    assert binding._out_ptr(t, (7,), np.int64) == t.data_ptr()
+    bad = [(np.zeros((3, 5), np.int64), (3, 5), np.int32),           # dtype
+           (np.zeros((5, 3), np.int32).T, (3, 5), np.int32),         # layout
+           (np.zeros((3, 6), np.int32), (3, 5), np.int32),           # shape
+           (torch.zeros(7, dtype=torch.int32), (7,), np.int64),
+           (torch.zeros(14, dtype=torch.int64)[::2], (7,), np.int64),
+           ([0] * 7, (7,), np.int64)]
+    for out, shape, dt in bad:
+        with pytest.raises(ValueError):
+            binding._out_ptr(out, shape, dt)
