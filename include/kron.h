@@ -234,13 +234,16 @@ kr_status kron_plan(const int32_t* emin, const int32_t* emax, int32_t nvars,
 
 /* codes_out[i] = sum_k c_k (exps[k][i] - emin[k]) for the box [emin, emax]
  * (host arrays).  exps: [nvars][n]; codes_out: [n].  KR_ERR_RANGE when a
- * term lies outside the box.  Synchronises the stream. */
+ * term lies outside the box; KR_ERR_OVERFLOW as for kron_plan, and also when
+ * some width w_k exceeds 2^31 - 1 (checked on the host before any device
+ * work).  Synchronises the stream. */
 kr_status kron_encode(kr_ctx* ctx, const int32_t* exps, int64_t n, int32_t nvars,
                       const int32_t* emin, const int32_t* emax, int64_t* codes_out,
                       kr_stream stream);
 
 /* Inverse of kron_encode: exps_out[k][i] = (codes[i] / c_k) mod w_k + emin[k].
- * KR_ERR_RANGE when a code lies outside [0, W).  Synchronises the stream. */
+ * KR_ERR_RANGE when a code lies outside [0, W); KR_ERR_OVERFLOW as for
+ * kron_encode.  Synchronises the stream. */
 kr_status kron_decode(kr_ctx* ctx, const int64_t* codes, int64_t n, int32_t nvars,
                       const int32_t* emin, const int32_t* emax, int32_t* exps_out,
                       kr_stream stream);

@@ -1296,12 +1296,22 @@ kr_status kron_plan(const int32_t* emin, const int32_t* emax, int32_t nvars, int
   return KR_OK;
 }
 
+// The standalone coding kernels keep each variable's width and offset in 32
+// bits, as the product path's output boxes do: every w_k must be at most
+// 2^31 - 1.
+static bool widths_fit_int32(const int32_t* emin, const int32_t* emax, int32_t nvars) {
+  for (int k = 0; k < nvars; ++k)
+    if ((int64_t)emax[k] - (int64_t)emin[k] + 1 > (int64_t)INT32_MAX) return false;
+  return true;
+}
+
 kr_status kron_encode(kr_ctx* ctx, const int32_t* exps, int64_t n, int32_t nvars, const int32_t* emin,
                       const int32_t* emax, int64_t* codes_out, kr_stream stream) {
   if (n < 0 || (n > 0 && (!exps || !codes_out))) return KR_ERR_INVALID;
   int64_t c[KR_MAXV], W;
   kr_status st = kron_plan(emin, emax, nvars, c, &W);
   if (st != KR_OK) return st;
+  if (!widths_fit_int32(emin, emax, nvars)) return KR_ERR_OVERFLOW;
   if (n == 0) return KR_OK;
   return guarded(ctx, [&]() -> kr_status {
     cudaStream_t s = (cudaStream_t)stream;
@@ -1336,6 +1346,7 @@ kr_status kron_decode(kr_ctx* ctx, const int64_t* codes, int64_t n, int32_t nvar
   int64_t c[KR_MAXV], W;
   kr_status st = kron_plan(emin, emax, nvars, c, &W);
   if (st != KR_OK) return st;
+  if (!widths_fit_int32(emin, emax, nvars)) return KR_ERR_OVERFLOW;
   if (n == 0) return KR_OK;
   int32_t w[KR_MAXV];
   for (int k = 0; k < nvars; ++k) w[k] = emax[k] - emin[k] + 1;

@@ -144,3 +144,27 @@ def test_caller_outputs_are_used_as_given_or_rejected():
     for out, shape, dt in bad:
         with pytest.raises(ValueError):
             binding._out_ptr(out, shape, dt)
+
+
+def test_coding_entries_reject_boxes_wider_than_int32():
+    """A variable whose width exceeds 2^31 - 1 is a valid box for kron_plan
+    (W = 2^32 here) but not for the 32-bit coding kernels: kron_encode and
+    kron_decode refuse it on the host, before any device work (no context is
+    needed to reach that check)."""
+    L = kron.load()
+    lo = np.array([-(1 << 31)], np.int32)
+    hi = np.array([(1 << 31) - 1], np.int32)
+    c, W = kron.kron_plan(lo, hi)
+    assert W == 1 << 32
+    codes = np.zeros(1, np.int64)
+    exps = np.zeros((1, 1), np.int32)
+    st = L.kron_decode(None, codes.ctypes.data, 1, 1, lo.ctypes.data, hi.ctypes.data, exps.ctypes.data, None)
+    assert st == binding.KR_ERR_OVERFLOW
+    st = L.kron_encode(None, exps.ctypes.data, 1, 1, lo.ctypes.data, hi.ctypes.data, codes.ctypes.data, None)
+    assert st == binding.KR_ERR_OVERFLOW
+    # width exactly 2^31 - 1 passes the check; the call then stops at the
+    # missing context, still before any device work
+    lo2 = np.array([-(1 << 30)], np.int32)
+    hi2 = np.array([(1 << 30) - 2], np.int32)
+    st = L.kron_decode(None, codes.ctypes.data, 1, 1, lo2.ctypes.data, hi2.ctypes.data, exps.ctypes.data, None)
+    assert st == binding.KR_ERR_INVALID
